@@ -1,0 +1,357 @@
+"""Plain FP64 CPU oracle for the contour-integral (CI) generalized eigensolver.
+
+TEST INFRASTRUCTURE ONLY.  Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  It shares no code with the CUDA path (the GPU library never
+loads `liboracle.so`, and nothing here imports `paper_2511_01927_gb300`).
+
+What it computes (paper: arXiv 2511.01927, "Learning-Guided Integration Contours Construction
+for Fast Large-Scale Generalized Eigensolvers"):
+
+* the definition of the result, Eq. GEP (Section 3.1) restricted to the target range of
+  Algorithm 1: every eigenpair (lambda, x) of A x = lambda B x with lambda in [lo, hi]
+  (`eigpairs_dense`, `inertia_count`);
+* the CI method step by step in the paper's order (`ci_solve`): contours from the partition of
+  the range (Section 4.2 circle rule), trapezoid nodes on each circle (Section 4.2 N_q-point
+  trapezoid rule; Eq. quadrature_appendix), the shifted solves (z_j B - A) X_j = B V at every
+  node (Algorithm 1), the moment sums S_k (Appendix A.3.3, moment-based methods), orthonormal
+  basis, projection, reduced GEP, Ritz recovery and "keep lambda in I_k" (Algorithm 1), the
+  subspace iteration of FEAST (Appendix A.3.3, U_{i+1} = orth(P_k U_i)) until the residual
+  tolerance is met (Section 5.1 / Appendix B.2), and the merge/de-duplication across contours.
+
+Readings of points the paper leaves open (node placement, moment scaling, residual norm, basis
+orthonormalisation, dedup rule, eigenvector sign) are stated at each function.
+
+Notation: the paper's A, B are K (stiffness, symmetric) and M (mass, SPD) here.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.sparse as sp
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (strict IEEE double, no FMA contraction)."""
+    src = os.path.join(_HERE, "oracle.c")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-o", _SO, src, "-lm"])
+    return _SO
+
+
+def _L():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        lib.oracle_zband_lu_factor.argtypes = [i64, i64, i64, p, p]
+        lib.oracle_zband_lu_factor.restype = ctypes.c_int
+        lib.oracle_zband_lu_solve.argtypes = [i64, i64, i64, p, p, i64, p]
+        lib.oracle_zband_lu_solve.restype = None
+        lib.oracle_dband_ldlt_negcount.argtypes = [i64, i64, p, p]
+        lib.oracle_dband_ldlt_negcount.restype = i64
+        lib.oracle_jacobi_eig.argtypes = [i64, p, p, p, ctypes.c_double, ctypes.c_int]
+        lib.oracle_jacobi_eig.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+# ----------------------------------------------------------------------------- matrices
+
+def as_scipy(A):
+    """Accept a pencils.Csr-like object (n, rowptr, col, val) or a scipy matrix."""
+    if sp.issparse(A):
+        return sp.csr_matrix(A)
+    return sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+
+
+def bandwidth(*mats) -> int:
+    bw = 0
+    for A in mats:
+        A = sp.coo_matrix(as_scipy(A))
+        if A.nnz:
+            bw = max(bw, int(np.max(np.abs(A.row.astype(np.int64) - A.col))))
+    return bw
+
+
+def norm1(A) -> float:
+    """||A||_1 = max column absolute sum (= ||A||_inf for symmetric A)."""
+    A = as_scipy(A)
+    return float(np.max(np.asarray(abs(A).sum(axis=0)).ravel()))
+
+
+# ----------------------------------------------------------------------------- shifted solves
+
+class ShiftedSolver:
+    """Factorization of (z M - K) by complex banded Gaussian elimination with partial pivoting;
+    `solve(B)` returns X with (z M - K) X = B.  These are the shifted linear systems of
+    Eq. quadrature_appendix / Algorithm 1 ("Solve (z_j B - A) X_j = B V")."""
+
+    def __init__(self, K, M, z: complex, bw: int | None = None):
+        Ks, Ms = as_scipy(K), as_scipy(M)
+        n = Ks.shape[0]
+        kl = ku = bandwidth(Ks, Ms) if bw is None else bw
+        W = 2 * kl + ku + 1
+        A = (complex(z) * Ms.astype(np.complex128) - Ks.astype(np.complex128)).tocoo()
+        ab = np.zeros((n, W), dtype=np.complex128)
+        ab[A.row, A.col.astype(np.int64) - A.row + kl] += A.data
+        self.n, self.kl, self.ku, self.ab = n, kl, ku, ab
+        self.ipiv = np.zeros(n, dtype=np.int64)
+        info = _L().oracle_zband_lu_factor(n, kl, ku, _ptr(ab), _ptr(self.ipiv))
+        if info != 0:
+            raise np.linalg.LinAlgError(f"zero pivot in column {info - 1}")
+
+    def solve(self, B: np.ndarray) -> np.ndarray:
+        X = np.array(B, dtype=np.complex128, order="C", copy=True)
+        if X.ndim == 1:
+            X = X[:, None]
+        _L().oracle_zband_lu_solve(self.n, self.kl, self.ku, _ptr(self.ab), _ptr(self.ipiv),
+                                   X.shape[1], _ptr(X))
+        return X
+
+
+def shifted_apply(K, M, z: complex, P: np.ndarray) -> np.ndarray:
+    """Q = (z M - K) P: the operator of the shifted systems applied to a block (plain definition)."""
+    Ks, Ms = as_scipy(K), as_scipy(M)
+    return complex(z) * (Ms @ P) - Ks @ P
+
+
+# ----------------------------------------------------------------------------- counting
+
+def inertia_count(K, M, sigma: float) -> int:
+    """Number of eigenvalues of K x = lambda M x below sigma, as the number of negative pivots of
+    LDL^T(K - sigma M) (Sylvester's law of inertia; the eigenvalue counting the paper cites in
+    Sections 2.1 and 3.3).  Banded, no pivoting."""
+    Ks, Ms = as_scipy(K), as_scipy(M)
+    n = Ks.shape[0]
+    bw = bandwidth(Ks, Ms)
+    A = sp.tril(Ks - sigma * Ms).tocoo()
+    ab = np.zeros((n, bw + 1), dtype=np.float64)
+    ab[A.row, A.col.astype(np.int64) - A.row + bw] += A.data
+    nz = np.zeros(1, dtype=np.int64)
+    return int(_L().oracle_dband_ldlt_negcount(n, bw, _ptr(ab), _ptr(nz)))
+
+
+def count_in(K, M, lo: float, hi: float) -> int:
+    """Eigenvalues in [lo, hi] = #neg(hi) - #neg(lo)."""
+    return inertia_count(K, M, hi) - inertia_count(K, M, lo)
+
+
+# ----------------------------------------------------------------------------- dense symmetric
+
+def jacobi_eigh(A: np.ndarray, tol: float = 1e-15, maxsweep: int = 60):
+    """Eigen-decomposition of a dense symmetric matrix by cyclic Jacobi; ascending eigenvalues,
+    eigenvectors as columns."""
+    A = np.array(A, dtype=np.float64, order="C", copy=True)
+    p = A.shape[0]
+    w = np.zeros(p)
+    V = np.zeros((p, p))
+    if p == 0:
+        return w, V
+    _L().oracle_jacobi_eig(p, _ptr(A), _ptr(w), _ptr(V), tol, maxsweep)
+    order = np.argsort(w, kind="stable")
+    return w[order], np.ascontiguousarray(V[:, order])
+
+
+def fix_sign(Z: np.ndarray) -> np.ndarray:
+    """Sign convention for eigenvectors: the entry of largest magnitude is positive."""
+    Z = np.array(Z, dtype=np.float64, copy=True)
+    if Z.size == 0:
+        return Z
+    idx = np.argmax(np.abs(Z), axis=0)
+    s = np.sign(Z[idx, np.arange(Z.shape[1])])
+    s[s == 0] = 1.0
+    return Z * s
+
+
+def eigpairs_dense(K, M, lo: float = -np.inf, hi: float = np.inf):
+    """The definition of the result: all eigenpairs of K x = lambda M x with lambda in [lo, hi]
+    (Eq. GEP; Algorithm 1 ENSURE), by Cholesky reduction M = L L^T, C = L^-1 K L^-T, Jacobi on C,
+    x = L^-T y.  Eigenvectors are M-orthonormal with the `fix_sign` convention.  Dense: small n."""
+    Kd = as_scipy(K).toarray()
+    Md = as_scipy(M).toarray()
+    Lc = np.linalg.cholesky(Md)
+    Li = np.linalg.inv(Lc)
+    C = Li @ Kd @ Li.T
+    C = 0.5 * (C + C.T)
+    w, Y = jacobi_eigh(C)
+    X = Li.T @ Y
+    keep = (w >= lo) & (w <= hi)
+    return w[keep], fix_sign(X[:, keep])
+
+
+# ----------------------------------------------------------------------------- CI method
+
+def uniform_contours(lo: float, hi: float, ncontours: int, alpha: float = 0.0):
+    """Equal-width partition of [lo, hi]; each piece I_k = [s, e] becomes the circle with centre
+    (s+e)/2 and radius (1+alpha)(e-s)/2 (Section 4.2 circle rule).  Returns a list of
+    (c, R, s, e)."""
+    edges = np.linspace(lo, hi, ncontours + 1)
+    out = []
+    for k in range(ncontours):
+        s, e = float(edges[k]), float(edges[k + 1])
+        out.append((0.5 * (s + e), (1.0 + alpha) * 0.5 * (e - s), s, e))
+    return out
+
+
+def trapezoid_nodes(c: float, R: float, N: int):
+    """Upper-half nodes and weights of the N-point trapezoid rule on the circle |z - c| = R
+    (Section 4.2; Eq. quadrature_appendix).  Reading: theta_j = 2 pi (j - 1/2) / N, j = 1..N, so
+    no node lies on the real axis and nodes come in conjugate pairs; the weight folds in
+    dz/(2 pi i): omega_j = R e^{i theta_j} / N.  Only j = 1..N/2 (Im z > 0) are returned; the
+    lower half contributes the complex conjugate because K, M are real."""
+    if N % 2:
+        raise ValueError("N must be even")
+    j = np.arange(1, N // 2 + 1)
+    th = 2.0 * np.pi * (j - 0.5) / N
+    e = np.exp(1j * th)
+    return c + R * e, R * e / N
+
+
+def moments(X_nodes, z, w, c: float, R: float, m: int):
+    """Moment sums S_k = (1/2 pi i) oint s^k (z M - K)^-1 M V dz by the trapezoid rule, k = 0..m-1
+    (Appendix A.3.3, moment-based methods).  Reading: the power is of the normalised node
+    s_j = (z_j - c)/R instead of z_j (same span, better conditioned).  With upper-half nodes:
+    S_k = 2 Re sum_j omega_j s_j^k X_j."""
+    S = []
+    for k in range(m):
+        acc = np.zeros(X_nodes[0].shape, dtype=np.complex128)
+        for Xj, zj, wj in zip(X_nodes, z, w):
+            acc += wj * ((zj - c) / R) ** k * Xj
+        S.append(2.0 * acc.real)
+    return S
+
+
+def m_orthonormalize(Y: np.ndarray, M, drop: float = 1e-14):
+    """Orthonormal basis of span(Y) in the M inner product ("Orthonormalize Q <- orth(Y)",
+    Algorithm 1).  Reading: Gram matrix G = Y^T M Y, G = U diag(sigma) U^T by Jacobi, keep
+    sigma_i > drop * max sigma (rank truncation), Q = Y U_k diag(sigma_k)^-1/2."""
+    Ms = as_scipy(M)
+    G = Y.T @ (Ms @ Y)
+    G = 0.5 * (G + G.T)
+    sig, U = jacobi_eigh(G)
+    if sig.size == 0 or sig[-1] <= 0:
+        return Y[:, :0]
+    keep = sig > drop * sig[-1]
+    return Y @ (U[:, keep] / np.sqrt(sig[keep]))
+
+
+def rayleigh_ritz(K, M, Q: np.ndarray):
+    """Project and solve the reduced GEP (Algorithm 1): A_k = Q^T K Q, B_k = Q^T M Q,
+    A_k u = theta B_k u via Cholesky reduction of B_k and Jacobi; Ritz vectors Z = Q U."""
+    Ks, Ms = as_scipy(K), as_scipy(M)
+    Kh = Q.T @ (Ks @ Q)
+    Mh = Q.T @ (Ms @ Q)
+    Kh = 0.5 * (Kh + Kh.T)
+    Mh = 0.5 * (Mh + Mh.T)
+    Lc = np.linalg.cholesky(Mh)
+    Li = np.linalg.inv(Lc)
+    C = Li @ Kh @ Li.T
+    theta, Yc = jacobi_eigh(0.5 * (C + C.T))
+    U = Li.T @ Yc
+    return theta, Q @ U
+
+
+def residuals(K, M, theta: np.ndarray, Z: np.ndarray, normK1: float | None = None):
+    """Relative residual ||K z - theta M z||_2 / (||K||_1 ||z||_2) per Ritz pair (reading of the
+    paper's unspecified "residual tolerance", Section 5.1 / Appendix B.2)."""
+    Ks, Ms = as_scipy(K), as_scipy(M)
+    if normK1 is None:
+        normK1 = norm1(Ks)
+    R = Ks @ Z - (Ms @ Z) * theta
+    return np.linalg.norm(R, axis=0) / (normK1 * np.linalg.norm(Z, axis=0))
+
+
+def merge_dedup(theta, Z, res, cid, M, rtol: float = 1e-8):
+    """Merge the per-contour results and remove duplicates ("Merge and de-duplicate solutions
+    across k", Algorithm 1).  Reading: sort by value; two pairs are the same when
+    |theta - theta'| <= rtol max(1, |theta|) and |z^T M z'| > 0.5; the smaller residual wins."""
+    Ms = as_scipy(M)
+    order = np.argsort(theta, kind="stable")
+    theta, Z, res, cid = theta[order], Z[:, order], res[order], cid[order]
+    keep = []
+    for i in range(len(theta)):
+        dup = False
+        for k in range(len(keep) - 1, -1, -1):
+            j = keep[k]
+            if abs(theta[i] - theta[j]) > rtol * max(1.0, abs(theta[i])):
+                break
+            if abs(Z[:, i] @ (Ms @ Z[:, j])) > 0.5:
+                dup = True
+                if res[i] < res[j]:
+                    keep[k] = i
+                break
+        if not dup:
+            keep.append(i)
+    keep = np.array(sorted(keep, key=lambda i: theta[i]), dtype=np.int64)
+    return theta[keep], Z[:, keep], res[keep], cid[keep]
+
+
+def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, nodes: int = 16,
+             moments_m: int = 2, tol: float = 1e-10, max_outer: int = 10, alpha: float = 0.0,
+             contours=None, trace: dict | None = None):
+    """The CI eigensolver of Algorithm 1 with the moment method and FEAST outer iterations.
+
+    For each contour (c, R) enclosing I_k = [s, e]:
+      1. nodes/weights of the trapezoid rule (upper half);
+      2. iteration 0: Y = [S_0 .. S_{m-1}] from the solves (z_j M - K) X_j = M V;
+      3. Q = M-orthonormal basis of Y; Ritz pairs (theta, Z) of (Q^T K Q, Q^T M Q);
+      4. residual of each Ritz pair; the pairs with theta in I_k are kept when their residual
+         is <= tol;
+      5. if some theta in I_k still has residual > tol: next iteration with V <- Z (all Ritz
+         vectors), one moment (plain FEAST filter P_k Z), same factorizations; back to 3.
+    Then merge/dedup across contours.  V is the random block (n x L) drawn by the caller.
+    `trace`, if given, receives per-contour intermediates of iteration 0 (nodes, S, Q, theta).
+    Returns dict(evals, evecs, resid, contour_of, outer_iters, status)."""
+    Ks, Ms = as_scipy(K), as_scipy(M)
+    nK = norm1(Ks)
+    if contours is None:
+        contours = uniform_contours(lo, hi, ncontours, alpha)
+    bw = bandwidth(Ks, Ms)
+    all_t, all_z, all_r, all_c, iters, status = [], [], [], [], [], []
+    for k, (c, R, s, e) in enumerate(contours):
+        z, w = trapezoid_nodes(c, R, nodes)
+        solvers = [ShiftedSolver(Ks, Ms, zj, bw) for zj in z]
+        Vk = np.asarray(V, dtype=np.float64)
+        m = moments_m
+        ok = False
+        for it in range(max_outer):
+            B = Ms @ Vk
+            X = [sv.solve(B) for sv in solvers]
+            S = moments(X, z, w, c, R, m)
+            Y = np.concatenate(S, axis=1)
+            Q = m_orthonormalize(Y, Ms)
+            theta, Z = rayleigh_ritz(Ks, Ms, Q)
+            res = residuals(Ks, Ms, theta, Z, nK)
+            if trace is not None and it == 0:
+                trace.setdefault("contours", []).append(dict(z=z, w=w, S=S, Q=Q, theta=theta, res=res))
+            inside = (theta >= s) & (theta <= e)
+            if not np.any(inside & (res > tol)):
+                ok = True
+                break
+            Vk, m = Z, 1
+        iters.append(it + 1)
+        status.append(0 if ok else 1)
+        sel = inside & (res <= tol)
+        all_t.append(theta[sel]); all_z.append(Z[:, sel]); all_r.append(res[sel])
+        all_c.append(np.full(int(sel.sum()), k, dtype=np.int32))
+    theta = np.concatenate(all_t)
+    Z = np.concatenate(all_z, axis=1) if all_z else np.zeros((Ks.shape[0], 0))
+    res = np.concatenate(all_r)
+    cid = np.concatenate(all_c)
+    theta, Z, res, cid = merge_dedup(theta, Z, res, cid, Ms)
+    # M-normalise and fix the sign of each returned vector
+    Zn = Z / np.sqrt(np.einsum("ij,ij->j", Z, Ms @ Z))
+    return dict(evals=theta, evecs=fix_sign(Zn), resid=res, contour_of=cid,
+                outer_iters=max(iters) if iters else 0, status=status)
