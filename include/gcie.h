@@ -1,0 +1,217 @@
+/*
+ * gcie: contour-integral generalized eigensolver for GB300 (sm_103a), C ABI.
+ *
+ * Problem (paper arXiv 2511.01927, Eq. GEP in Section 3.1 and the REQUIRE/ENSURE lines of
+ * Algorithm 1): given a real symmetric sparse K (the paper's A) and a symmetric positive
+ * definite sparse M (the paper's B) and a target range [lo, hi], return every eigenpair
+ * (lambda, x) of K x = lambda M x with lambda in [lo, hi].
+ *
+ * Method: the contour-integral pipeline of Algorithm 1 with the moment method and FEAST
+ * subspace iteration of Appendix A.3.3 (Sakurai-Sugiura moments, U_{i+1} = orth(P_k U_i)),
+ * trapezoid quadrature on circles (Section 4.2), shifted systems (z_j M - K) X_j = M V at every
+ * node (Eq. quadrature_appendix), moments S_k, M-orthonormal basis, Rayleigh-Ritz, keep
+ * lambda in I_k, merge/de-duplicate.  The shifted solves run as batched COCG (conjugate
+ * orthogonal CG for complex symmetric systems) in FP32 complex with FP64 residual refinement,
+ * or in FP64 throughout; everything after the solves is FP64.
+ *
+ * Conventions for every call:
+ *   - return value 0 (GCIE_OK) on success, otherwise one of the GCIE_E* codes below; no call
+ *     throws or aborts; gcie_strerror() names a code and gcie_last_error() gives a message
+ *     for the calling thread's most recent failure.
+ *   - pointers named h_* / taking gcie_csr are HOST memory, borrowed for the duration of the
+ *     call (the library copies what it needs).  Pointers named d_* are DEVICE memory on the
+ *     context's device, owned by the caller, and must stay valid until the call returns.
+ *   - complex arrays are interleaved (re, im) pairs.
+ *   - a context is used by one host thread at a time; calls on it are ordered on its stream.
+ */
+#ifndef GCIE_H
+#define GCIE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status codes */
+enum {
+    GCIE_OK = 0,
+    GCIE_EINVAL = 1,      /* bad argument: CSR structure, sizes, lo >= hi, option out of range */
+    GCIE_ENOTSYM = 2,     /* K or M not symmetric (checked on every stored entry) */
+    GCIE_ENOTSPD = 3,     /* M has a non-positive diagonal entry, or a Gram matrix lost rank */
+    GCIE_ENOMEM = 4,      /* device or host allocation failed, or the budget is too small */
+    GCIE_ENOCONV = 5,     /* some contour did not reach the tolerance; converged pairs returned */
+    GCIE_EBREAKDOWN = 6,  /* COCG breakdown (p^T A p = 0) that refinement could not recover */
+    GCIE_ETIMEOUT = 7,    /* a bounded device-side wait expired */
+    GCIE_ECOUNT = 8,      /* returned count differs from a caller-supplied expected count */
+    GCIE_ECUDA = 9        /* CUDA runtime error */
+};
+
+enum { GCIE_MIXED = 0, GCIE_FP64 = 1 };   /* precision of the shifted solves */
+
+/* Sparse matrix in CSR form, host memory: 0-based, column indices sorted and unique within a
+ * row, both triangles stored, n >= 1, rowptr[0] = 0, rowptr[n] = nnz. */
+typedef struct {
+    int64_t n;
+    int64_t nnz;
+    const int64_t *rowptr;   /* n + 1 */
+    const int32_t *col;      /* nnz */
+    const double *val;       /* nnz */
+} gcie_csr;
+
+/* One contour: the circle |z - c| = r and the interval [lo, hi] whose eigenvalues it keeps
+ * (Algorithm 1: "keep lambda in I_k").  Section 4.2: c = (lo+hi)/2, r = (1+alpha)(hi-lo)/2. */
+typedef struct {
+    double c, r;
+    double lo, hi;
+} gcie_contour;
+
+typedef struct {
+    int32_t nodes;          /* trapezoid nodes N per circle, even, 2..64 (default 16) */
+    int32_t L;              /* columns of the random starting block V (default 32) */
+    int32_t moments;        /* moments m: basis [S_0 .. S_{m-1}] (default 2) */
+    int32_t max_outer;      /* FEAST iterations cap (default 8) */
+    int32_t max_iters;      /* COCG iteration cap per shifted solve (default 100000) */
+    int32_t precision;      /* GCIE_MIXED (default) or GCIE_FP64 */
+    double tol;             /* eigenpair tolerance on ||Kx - lambda Mx||_2 / (||K||_1 ||x||_2) (1e-10) */
+    double lin_tol;         /* shifted-solve target ||b - A x||_2 / ||b||_2 (default 1e-11) */
+    int32_t ncontours;      /* > 0: use contours[0..ncontours-1]; 0: nuniform equal-width pieces */
+    int32_t nuniform;       /* number of equal-width contours when ncontours == 0 (default 1) */
+    const gcie_contour *contours;   /* host, borrowed */
+    double alpha;           /* radius inflation for uniform contours (default 0) */
+    const double *h_V0;     /* host n x L row-major starting block, or NULL: library draws N(0,1) */
+    uint64_t seed;          /* seed for the library's own draw when h_V0 == NULL */
+    size_t hbm_budget_bytes;/* device memory the solve may use (0: 90% of free memory) */
+    int32_t expected_count; /* >= 0: return GCIE_ECOUNT if the merged count differs; -1: off */
+    int32_t profile;        /* 1: time every kernel launch with CUDA events (see gcie_stats) */
+} gcie_opts;
+
+/* Results: library-allocated host arrays, released by gcie_result_free. */
+typedef struct {
+    int64_t n;
+    int32_t count;              /* eigenpairs returned (converged, inside [lo, hi], de-duplicated) */
+    double *evals;              /* count, ascending */
+    double *evecs;              /* n x count, column j at evecs[j*n .. j*n+n), M-normalised, the
+                                   entry of largest magnitude positive */
+    double *resid;              /* count: ||Kx - lambda Mx||_2 / (||K||_1 ||x||_2) */
+    int32_t *contour_of;        /* count: index of the contour that produced the pair */
+    int32_t ncontours;
+    int32_t *status_per_contour;/* ncontours: GCIE_OK or GCIE_ENOCONV */
+    int32_t *iters_per_contour; /* ncontours: FEAST iterations used */
+    int32_t outer_iters;        /* max over contours */
+    int64_t cocg_iters;         /* COCG iterations summed over solve batches */
+    double norm_k1;             /* ||K||_1 used in the residual */
+} gcie_result;
+
+/* Per-kernel-class accounting since the last gcie_reset_stats (profile = 1 fills times). */
+enum { GCIE_K_SPMM_DIR = 0, GCIE_K_SPMM_UPD = 1, GCIE_K_REFINE = 2, GCIE_K_MOMENT = 3,
+       GCIE_K_DENSE = 4, GCIE_K_OTHER = 5, GCIE_K_NCLASS = 6 };
+typedef struct {
+    int64_t launches[GCIE_K_NCLASS];
+    double ms[GCIE_K_NCLASS];          /* summed CUDA-event durations of those launches */
+    double bytes[GCIE_K_NCLASS];       /* algorithmic DRAM bytes of those launches */
+    double flops[GCIE_K_NCLASS];
+    int64_t total_launches;            /* every kernel the library launched */
+} gcie_stats;
+
+typedef struct gcie_ctx gcie_ctx;
+typedef struct gcie_pencil gcie_pencil;
+
+/* ------------------------------------------------------------------ context */
+
+/* Create a context on CUDA device `device`.  stream: a cudaStream_t to order work on, or NULL
+ * for a stream the context creates and owns.  Errors: GCIE_EINVAL (bad device), GCIE_ECUDA. */
+int gcie_create(gcie_ctx **out, int device, void *stream);
+/* Release the context and everything it allocated (pencils must be destroyed first). */
+void gcie_destroy(gcie_ctx *ctx);
+
+/* Default options (the values in the comments above). */
+void gcie_default_opts(gcie_opts *o);
+const char *gcie_strerror(int code);
+/* Message of the calling thread's last failure ("" if none). */
+const char *gcie_last_error(void);
+int gcie_get_stats(gcie_ctx *ctx, gcie_stats *out);
+void gcie_reset_stats(gcie_ctx *ctx);
+/* Time every subsequent kernel launch of this context with CUDA events (on = 1) or not (0);
+ * gcie_solve_pencil also sets it from opts.profile. */
+void gcie_set_profile(gcie_ctx *ctx, int on);
+
+/* ------------------------------------------------------------------ pencil ingest (step a1)
+ * Validate K and M (structure, symmetry of every stored entry, positive diagonal of M), build
+ * the union sparsity pattern and upload FP64 and FP32 copies of both value arrays to the
+ * device.  The pencil stays resident until gcie_pencil_destroy.
+ * Errors: GCIE_EINVAL, GCIE_ENOTSYM, GCIE_ENOTSPD, GCIE_ENOMEM, GCIE_ECUDA. */
+int gcie_pencil_create(gcie_ctx *ctx, const gcie_csr *K, const gcie_csr *M, gcie_pencil **out);
+void gcie_pencil_destroy(gcie_pencil *p);
+int64_t gcie_pencil_n(const gcie_pencil *p);
+int64_t gcie_pencil_nnz(const gcie_pencil *p);   /* of the union pattern */
+
+/* ------------------------------------------------------------------ whole solve
+ * All eigenpairs of K x = lambda M x in [lo, hi] (Algorithm 1 ENSURE).  gcie_solve ingests K, M
+ * from the host, solves, and frees the device copy; gcie_solve_pencil reuses a resident pencil.
+ * On GCIE_ENOCONV the result still holds every pair that met the tolerance.
+ * Errors: those of gcie_pencil_create plus GCIE_ENOCONV, GCIE_EBREAKDOWN, GCIE_ECOUNT. */
+int gcie_solve(gcie_ctx *ctx, const gcie_csr *K, const gcie_csr *M, double lo, double hi,
+               const gcie_opts *opts, gcie_result *out);
+int gcie_solve_pencil(gcie_ctx *ctx, gcie_pencil *p, double lo, double hi, const gcie_opts *opts,
+                      gcie_result *out);
+void gcie_result_free(gcie_result *r);
+
+/* ------------------------------------------------------------------ steps of the path
+ * Device-pointer entry points for the individual steps, used by the parity tests and by
+ * callers that drive the pipeline themselves.  Each runs the same kernels as gcie_solve. */
+
+/* Nodes and weights of the N-point trapezoid rule on |z - c| = r, upper half only
+ * (Section 4.2; Eq. quadrature_appendix): theta_j = 2 pi (j - 1/2)/N, z_j = c + r e^{i theta_j},
+ * w_j = r e^{i theta_j} / N, j = 1..N/2.  h_z, h_w: host, N/2 complex each. */
+int gcie_trapezoid_nodes(double c, double r, int32_t N, double *h_z, double *h_w);
+
+/* Step a4 (fused multi-shift SpMM): for each shift s and column l,
+ *   Q[s][i][l] = z_s (M P[s])[i][l] - (K P[s])[i][l].
+ * d_P, d_Q: FP32 complex, nshift blocks of n x ncol row-major.  h_z: host, nshift complex. */
+int gcie_shifted_spmm_f32(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
+                          int32_t ncol, const float *d_P, float *d_Q);
+/* The same operator in FP64 (used by the refinement residual): d_P, d_Q FP64 complex. */
+int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
+                          int32_t ncol, const double *d_P, double *d_Q);
+
+/* Steps a4-a6 (shifted block solves): X[s] = (z_s M - K)^{-1} B for every shift s, by batched
+ * COCG (FP32 with FP64 refinement for GCIE_MIXED, FP64 for GCIE_FP64) to
+ * ||B - A X[s]||_2 / ||B||_2 <= lin_tol per column.
+ * d_B: FP64 real n x ncol row-major (shared by all shifts); d_X: FP64 complex, nshift blocks of
+ * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  h_iters (host, may be
+ * NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
+ * within max_iters (d_X then holds the best iterate). */
+int gcie_shifted_solve(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
+                       int32_t ncol, const double *d_B, double *d_X, int32_t x0, double lin_tol,
+                       int32_t max_iters, int32_t precision, int64_t *h_iters);
+
+/* Step a7 (moments): S_k += 2 Re( w_s ((z_s - c)/r)^k X[s] ), k = 0..m-1, summed over the nshift
+ * upper-half nodes.  d_X as in gcie_shifted_solve; d_S: FP64 n x (m*ncol) row-major, column
+ * k*ncol + l holds S_k[:, l]; accumulated into (zero it first for a fresh sum). */
+int gcie_moments(gcie_ctx *ctx, int64_t n, int32_t nshift, const double *h_z, const double *h_w,
+                 double c, double r, int32_t m, int32_t ncol, const double *d_X, double *d_S);
+
+/* Step a8 (M-orthonormal basis of span Y): G = Y^T M Y, G = U diag(s) U^T (Jacobi), keep
+ * s_i > drop * max s, Q = Y U_k diag(s_k)^-1/2; applied twice (the second pass restores
+ * orthonormality lost to rounding).  d_Y: FP64 n x p row-major; d_Q: FP64 n x p row-major
+ * (columns >= *h_rank are zero).  Errors: GCIE_ENOTSPD if the rank is 0. */
+int gcie_m_orthonormalize(gcie_ctx *ctx, gcie_pencil *p, int32_t ncolY, const double *d_Y,
+                          double drop, double *d_Q, int32_t *h_rank);
+
+/* Steps a9-a11 (Rayleigh-Ritz): Khat = Q^T K Q, Jacobi Khat = W diag(theta) W^T, Z = Q W,
+ * residual_i = ||K z_i - theta_i M z_i||_2 / (||K||_1 ||z_i||_2).  d_Q: FP64 n x q row-major,
+ * M-orthonormal; d_Z: FP64 n x q row-major; h_theta, h_res: host, q (theta ascending). */
+int gcie_rayleigh_ritz(gcie_ctx *ctx, gcie_pencil *p, int32_t q, const double *d_Q, double *d_Z,
+                       double *h_theta, double *h_res);
+
+/* Cyclic Jacobi on a dense symmetric p x p FP64 matrix on the device (the small-eigensolve
+ * kernel of steps a8 and a10).  d_A: row-major, destroyed; d_w: p eigenvalues ascending;
+ * d_V: p x p row-major, column j = eigenvector j. */
+int gcie_jacobi_eig(gcie_ctx *ctx, int32_t p, double *d_A, double *d_w, double *d_V);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GCIE_H */

@@ -1,0 +1,304 @@
+"""ctypes marshalling for libgcie.so (include/gcie.h).  No arithmetic of the method lives here."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libgcie.so")
+
+STATUS = {0: "GCIE_OK", 1: "GCIE_EINVAL", 2: "GCIE_ENOTSYM", 3: "GCIE_ENOTSPD", 4: "GCIE_ENOMEM",
+          5: "GCIE_ENOCONV", 6: "GCIE_EBREAKDOWN", 7: "GCIE_ETIMEOUT", 8: "GCIE_ECOUNT", 9: "GCIE_ECUDA"}
+MIXED, FP64 = 0, 1
+
+EXPORTED_SYMBOLS = [
+    "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
+    "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
+    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
+    "gcie_rayleigh_ritz", "gcie_jacobi_eig",
+]
+
+
+class GcieError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str = ""):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)} {msg}")
+
+
+class Csr(C.Structure):
+    _fields_ = [("n", C.c_int64), ("nnz", C.c_int64), ("rowptr", C.c_void_p), ("col", C.c_void_p), ("val", C.c_void_p)]
+
+
+class Contour(C.Structure):
+    _fields_ = [("c", C.c_double), ("r", C.c_double), ("lo", C.c_double), ("hi", C.c_double)]
+
+
+class Opts(C.Structure):
+    _fields_ = [("nodes", C.c_int32), ("L", C.c_int32), ("moments", C.c_int32), ("max_outer", C.c_int32),
+                ("max_iters", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double), ("lin_tol", C.c_double),
+                ("ncontours", C.c_int32), ("nuniform", C.c_int32), ("contours", C.c_void_p), ("alpha", C.c_double),
+                ("h_V0", C.c_void_p), ("seed", C.c_uint64), ("hbm_budget_bytes", C.c_size_t),
+                ("expected_count", C.c_int32), ("profile", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("n", C.c_int64), ("count", C.c_int32), ("evals", C.POINTER(C.c_double)),
+                ("evecs", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
+                ("contour_of", C.POINTER(C.c_int32)), ("ncontours", C.c_int32),
+                ("status_per_contour", C.POINTER(C.c_int32)), ("iters_per_contour", C.POINTER(C.c_int32)),
+                ("outer_iters", C.c_int32), ("cocg_iters", C.c_int64), ("norm_k1", C.c_double)]
+
+
+NCLASS = 6
+KERNEL_CLASSES = ["spmm_dir", "spmm_upd", "refine", "moment", "dense", "other"]
+
+
+class Stats(C.Structure):
+    _fields_ = [("launches", C.c_int64 * NCLASS), ("ms", C.c_double * NCLASS), ("bytes", C.c_double * NCLASS),
+                ("flops", C.c_double * NCLASS), ("total_launches", C.c_int64)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _SO
+
+
+def lib():
+    """Load libgcie.so (built in-tree by paper_2511_01927_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise RuntimeError(f"libgcie.so not built ({_SO}); run paper_2511_01927_gb300.build.build()")
+    L = C.CDLL(_SO)
+    vp, i32, i64, d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+    sig = {
+        "gcie_create": (C.c_int, [C.POINTER(vp), C.c_int, vp]),
+        "gcie_destroy": (None, [vp]),
+        "gcie_default_opts": (None, [C.POINTER(Opts)]),
+        "gcie_strerror": (C.c_char_p, [C.c_int]),
+        "gcie_last_error": (C.c_char_p, []),
+        "gcie_get_stats": (C.c_int, [vp, C.POINTER(Stats)]),
+        "gcie_reset_stats": (None, [vp]),
+        "gcie_set_profile": (None, [vp, C.c_int]),
+        "gcie_pencil_create": (C.c_int, [vp, C.POINTER(Csr), C.POINTER(Csr), C.POINTER(vp)]),
+        "gcie_pencil_destroy": (None, [vp]),
+        "gcie_pencil_n": (i64, [vp]),
+        "gcie_pencil_nnz": (i64, [vp]),
+        "gcie_solve": (C.c_int, [vp, C.POINTER(Csr), C.POINTER(Csr), d, d, C.POINTER(Opts), C.POINTER(Result)]),
+        "gcie_solve_pencil": (C.c_int, [vp, vp, d, d, C.POINTER(Opts), C.POINTER(Result)]),
+        "gcie_result_free": (None, [C.POINTER(Result)]),
+        "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
+        "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
+        "gcie_shifted_spmm_f64": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
+        "gcie_shifted_solve": (C.c_int, [vp, vp, i32, vp, i32, vp, vp, i32, d, i32, i32, C.POINTER(i64)]),
+        "gcie_moments": (C.c_int, [vp, i64, i32, vp, vp, d, d, i32, i32, vp, vp]),
+        "gcie_m_orthonormalize": (C.c_int, [vp, vp, i32, vp, d, vp, C.POINTER(i32)]),
+        "gcie_rayleigh_ritz": (C.c_int, [vp, vp, i32, vp, vp, vp, vp]),
+        "gcie_jacobi_eig": (C.c_int, [vp, i32, vp, vp, vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(rc: int, where: str, allow=()):
+    if rc != 0 and rc not in allow:
+        raise GcieError(rc, where, lib().gcie_last_error().decode())
+    return rc
+
+
+def _ptr(x) -> int:
+    """Address of a numpy array or a torch tensor (host or device)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return x.ctypes.data
+
+
+# ------------------------------------------------------------------ host structs
+
+class _HostCsr:
+    """Keeps the numpy arrays alive while the C struct points at them."""
+
+    def __init__(self, A):
+        self.rowptr = np.ascontiguousarray(A.rowptr, dtype=np.int64)
+        self.col = np.ascontiguousarray(A.col, dtype=np.int32)
+        self.val = np.ascontiguousarray(A.val, dtype=np.float64)
+        self.s = Csr(int(A.n), int(self.rowptr[-1]), self.rowptr.ctypes.data, self.col.ctypes.data,
+                     self.val.ctypes.data)
+
+
+def csr_struct(A) -> _HostCsr:
+    return _HostCsr(A)
+
+
+def default_opts(**kw) -> Opts:
+    o = Opts()
+    lib().gcie_default_opts(C.byref(o))
+    for k, v in kw.items():
+        if k in ("contours", "h_V0"):
+            continue
+        setattr(o, k, v)
+    return o
+
+
+class _OptsHolder:
+    def __init__(self, kw):
+        kw = dict(kw)
+        self.contours = kw.pop("contours", None)
+        V0 = kw.pop("V0", None)
+        self.o = default_opts(**kw)
+        if self.contours is not None:
+            arr = (Contour * len(self.contours))(*[Contour(*map(float, cc)) for cc in self.contours])
+            self._carr = arr
+            self.o.contours = C.cast(arr, C.c_void_p)
+            self.o.ncontours = len(self.contours)
+        if V0 is not None:
+            self.V0 = np.ascontiguousarray(V0, dtype=np.float64)
+            self.o.h_V0 = self.V0.ctypes.data
+            self.o.L = self.V0.shape[1]
+
+
+# ------------------------------------------------------------------ context / pencil
+
+def gcie_create(device: int = 0, stream: int | None = None):
+    h = C.c_void_p()
+    _check(lib().gcie_create(C.byref(h), int(device), C.c_void_p(stream) if stream else None), "gcie_create")
+    return h
+
+
+def gcie_destroy(ctx):
+    lib().gcie_destroy(ctx)
+
+
+def gcie_get_stats(ctx) -> dict:
+    s = Stats()
+    _check(lib().gcie_get_stats(ctx, C.byref(s)), "gcie_get_stats")
+    return {name: dict(launches=int(s.launches[i]), ms=float(s.ms[i]), bytes=float(s.bytes[i]), flops=float(s.flops[i]))
+            for i, name in enumerate(KERNEL_CLASSES)} | {"total_launches": int(s.total_launches)}
+
+
+def gcie_reset_stats(ctx):
+    lib().gcie_reset_stats(ctx)
+
+
+def gcie_set_profile(ctx, on: bool):
+    lib().gcie_set_profile(ctx, int(bool(on)))
+
+
+def gcie_pencil_create(ctx, K, M):
+    hk, hm = _HostCsr(K), _HostCsr(M)
+    h = C.c_void_p()
+    _check(lib().gcie_pencil_create(ctx, C.byref(hk.s), C.byref(hm.s), C.byref(h)), "gcie_pencil_create")
+    return h
+
+
+def gcie_pencil_destroy(p):
+    lib().gcie_pencil_destroy(p)
+
+
+def _take_result(r: Result) -> dict:
+    n, k = int(r.n), int(r.count)
+    out = dict(
+        evals=np.ctypeslib.as_array(r.evals, (k,)).copy() if k else np.zeros(0),
+        evecs=(np.ctypeslib.as_array(r.evecs, (k, n)).copy().T if k else np.zeros((n, 0))),
+        resid=np.ctypeslib.as_array(r.resid, (k,)).copy() if k else np.zeros(0),
+        contour_of=np.ctypeslib.as_array(r.contour_of, (k,)).copy() if k else np.zeros(0, np.int32),
+        status=[int(r.status_per_contour[i]) for i in range(r.ncontours)] if r.status_per_contour else [],
+        iters=[int(r.iters_per_contour[i]) for i in range(r.ncontours)] if r.iters_per_contour else [],
+        outer_iters=int(r.outer_iters), cocg_iters=int(r.cocg_iters), norm_k1=float(r.norm_k1))
+    lib().gcie_result_free(C.byref(r))
+    return out
+
+
+def gcie_solve(ctx, K, M, lo: float, hi: float, allow_noconv: bool = False, **opts) -> dict:
+    """All eigenpairs in [lo, hi] from host CSR matrices (pencils.Csr-like objects).  Keyword
+    options are the gcie_opts fields; `contours` = list of (c, r, lo, hi); `V0` = n x L block."""
+    hk, hm = _HostCsr(K), _HostCsr(M)
+    oh = _OptsHolder(opts)
+    r = Result()
+    rc = lib().gcie_solve(ctx, C.byref(hk.s), C.byref(hm.s), float(lo), float(hi), C.byref(oh.o), C.byref(r))
+    _check(rc, "gcie_solve", allow=(5,) if allow_noconv else ())
+    out = _take_result(r)
+    out["rc"] = rc
+    return out
+
+
+def gcie_solve_pencil(ctx, pencil, lo: float, hi: float, allow_noconv: bool = False, **opts) -> dict:
+    oh = _OptsHolder(opts)
+    r = Result()
+    rc = lib().gcie_solve_pencil(ctx, pencil, float(lo), float(hi), C.byref(oh.o), C.byref(r))
+    _check(rc, "gcie_solve_pencil", allow=(5,) if allow_noconv else ())
+    out = _take_result(r)
+    out["rc"] = rc
+    return out
+
+
+# ------------------------------------------------------------------ steps (device buffers)
+
+def gcie_trapezoid_nodes(c: float, r: float, N: int):
+    z = np.zeros(N // 2, dtype=np.complex128)
+    w = np.zeros(N // 2, dtype=np.complex128)
+    _check(lib().gcie_trapezoid_nodes(float(c), float(r), int(N), z.ctypes.data, w.ctypes.data), "gcie_trapezoid_nodes")
+    return z, w
+
+
+def _zarr(z):
+    return np.ascontiguousarray(np.asarray(z, dtype=np.complex128).ravel())
+
+
+def gcie_shifted_spmm_f32(ctx, pencil, z, ncol: int, d_P, d_Q):
+    zz = _zarr(z)
+    _check(lib().gcie_shifted_spmm_f32(ctx, pencil, len(zz), zz.ctypes.data, int(ncol), _ptr(d_P), _ptr(d_Q)),
+           "gcie_shifted_spmm_f32")
+
+
+def gcie_shifted_spmm_f64(ctx, pencil, z, ncol: int, d_P, d_Q):
+    zz = _zarr(z)
+    _check(lib().gcie_shifted_spmm_f64(ctx, pencil, len(zz), zz.ctypes.data, int(ncol), _ptr(d_P), _ptr(d_Q)),
+           "gcie_shifted_spmm_f64")
+
+
+def gcie_shifted_solve(ctx, pencil, z, ncol: int, d_B, d_X, x0: bool = False, lin_tol: float = 1e-11,
+                       max_iters: int = 100000, precision: int = MIXED, allow_noconv: bool = False):
+    zz = _zarr(z)
+    it = C.c_int64(0)
+    rc = lib().gcie_shifted_solve(ctx, pencil, len(zz), zz.ctypes.data, int(ncol), _ptr(d_B), _ptr(d_X), int(bool(x0)),
+                                  float(lin_tol), int(max_iters), int(precision), C.byref(it))
+    _check(rc, "gcie_shifted_solve", allow=(5,) if allow_noconv else ())
+    return int(it.value), rc
+
+
+def gcie_moments(ctx, n: int, z, w, c: float, r: float, m: int, ncol: int, d_X, d_S):
+    zz, ww = _zarr(z), _zarr(w)
+    _check(lib().gcie_moments(ctx, int(n), len(zz), zz.ctypes.data, ww.ctypes.data, float(c), float(r), int(m),
+                              int(ncol), _ptr(d_X), _ptr(d_S)), "gcie_moments")
+
+
+def gcie_m_orthonormalize(ctx, pencil, ncolY: int, d_Y, drop: float, d_Q) -> int:
+    rank = C.c_int32(0)
+    _check(lib().gcie_m_orthonormalize(ctx, pencil, int(ncolY), _ptr(d_Y), float(drop), _ptr(d_Q), C.byref(rank)),
+           "gcie_m_orthonormalize")
+    return int(rank.value)
+
+
+def gcie_rayleigh_ritz(ctx, pencil, q: int, d_Q, d_Z):
+    th = np.zeros(q)
+    rs = np.zeros(q)
+    _check(lib().gcie_rayleigh_ritz(ctx, pencil, int(q), _ptr(d_Q), _ptr(d_Z), th.ctypes.data, rs.ctypes.data),
+           "gcie_rayleigh_ritz")
+    return th, rs
+
+
+def gcie_jacobi_eig(ctx, p: int, d_A, d_w, d_V):
+    _check(lib().gcie_jacobi_eig(ctx, int(p), _ptr(d_A), _ptr(d_w), _ptr(d_V)), "gcie_jacobi_eig")

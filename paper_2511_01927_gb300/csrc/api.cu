@@ -1,0 +1,903 @@
+// C ABI of the gcie library: context, pencil ingest (step a1), the FEAST/CIRR driver
+// (Algorithm 1 with the moment method and subspace iteration of Appendix A.3.3), and the
+// per-step device-pointer entry points.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace gcie {
+
+static thread_local std::string g_err;
+void set_error(const std::string &msg) { g_err = msg; }
+
+// ------------------------------------------------------------------ launch accounting
+struct PendingEvent { cudaEvent_t a, b; int cls; };
+static thread_local std::vector<PendingEvent> t_pending;
+static thread_local std::vector<cudaEvent_t> t_free;
+
+static cudaEvent_t get_event()
+{
+    if (!t_free.empty()) { cudaEvent_t e = t_free.back(); t_free.pop_back(); return e; }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void flush_timing(Ctx *c)
+{
+    for (auto &pe : t_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) c->stats.ms[pe.cls] += ms;
+        t_free.push_back(pe.a);
+        t_free.push_back(pe.b);
+    }
+    t_pending.clear();
+    cudaGetLastError();
+}
+
+LaunchScope::LaunchScope(Ctx *ctx, int klass, double b, double f) : c(ctx), cls(klass), bytes(b), flops(f)
+{
+    if (c->profile) {
+        cudaEvent_t a = get_event();
+        cudaEventRecord(a, c->stream);
+        t_pending.push_back({a, nullptr, cls});
+    }
+}
+
+LaunchScope::~LaunchScope()
+{
+    c->stats.launches[cls] += 1;
+    c->stats.bytes[cls] += bytes;
+    c->stats.flops[cls] += flops;
+    c->stats.total_launches += 1;
+    if (c->profile && !t_pending.empty() && t_pending.back().b == nullptr) {
+        cudaEvent_t b = get_event();
+        cudaEventRecord(b, c->stream);
+        t_pending.back().b = b;
+        if (t_pending.size() > 4096) {
+            cudaEventSynchronize(b);
+            flush_timing(c);
+        }
+    }
+}
+
+int ctx_scratch(Ctx *c, size_t bytes, void **out)
+{
+    if (bytes > c->scratch_bytes) {
+        if (c->scratch) {
+            cudaStreamSynchronize(c->stream);
+            cudaFree(c->scratch);
+            c->scratch = nullptr;
+            c->scratch_bytes = 0;
+        }
+        size_t want = std::max(bytes, (size_t)1 << 20);
+        if (cudaMalloc(&c->scratch, want) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("scratch allocation failed");
+            return GCIE_ENOMEM;
+        }
+        c->scratch_bytes = want;
+    }
+    *out = c->scratch;
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ small helpers
+static void trapezoid(double c, double r, int N, std::vector<double2> &z, std::vector<double2> &w)
+{
+    z.resize(N / 2);
+    w.resize(N / 2);
+    for (int j = 1; j <= N / 2; ++j) {
+        const double th = 2.0 * M_PI * (j - 0.5) / N;
+        const double ct = std::cos(th), st = std::sin(th);
+        z[j - 1] = make_double2(c + r * ct, r * st);
+        w[j - 1] = make_double2(r * ct / N, r * st / N);
+    }
+}
+
+// SplitMix64 (Steele, Lea, Flood 2014) as a counter-based generator, Box-Muller for N(0, 1).
+static uint64_t splitmix64(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+static void draw_gaussian(uint64_t seed, int64_t count, double *out)
+{
+    for (int64_t e = 0; e < count; e += 2) {
+        const uint64_t a = splitmix64(seed * 0x100000001B3ull + (uint64_t)e);
+        const uint64_t b = splitmix64(a ^ 0xD1B54A32D192ED03ull);
+        const double u1 = ((a >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double u2 = ((b >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+        const double rad = std::sqrt(-2.0 * std::log(u1));
+        out[e] = rad * std::cos(2.0 * M_PI * u2);
+        if (e + 1 < count) out[e + 1] = rad * std::sin(2.0 * M_PI * u2);
+    }
+}
+
+static int check_csr(const gcie_csr *A, const char *name)
+{
+    if (!A || !A->rowptr || (!A->col && A->nnz) || (!A->val && A->nnz) || A->n < 1 || A->nnz < 0) {
+        set_error(std::string(name) + ": null pointer or bad size");
+        return GCIE_EINVAL;
+    }
+    if (A->rowptr[0] != 0 || A->rowptr[A->n] != A->nnz) { set_error(std::string(name) + ": rowptr ends"); return GCIE_EINVAL; }
+    if (A->nnz >= ((int64_t)1 << 31)) { set_error(std::string(name) + ": nnz >= 2^31"); return GCIE_EINVAL; }
+    for (int64_t i = 0; i < A->n; ++i) {
+        if (A->rowptr[i + 1] < A->rowptr[i]) { set_error(std::string(name) + ": rowptr decreasing"); return GCIE_EINVAL; }
+        for (int64_t k = A->rowptr[i]; k < A->rowptr[i + 1]; ++k) {
+            if (A->col[k] < 0 || A->col[k] >= A->n) { set_error(std::string(name) + ": column index out of range"); return GCIE_EINVAL; }
+            if (k > A->rowptr[i] && A->col[k] <= A->col[k - 1]) {
+                set_error(std::string(name) + ": column indices not sorted/unique in row " + std::to_string(i));
+                return GCIE_EINVAL;
+            }
+            if (!std::isfinite(A->val[k])) { set_error(std::string(name) + ": non-finite value"); return GCIE_EINVAL; }
+        }
+    }
+    return GCIE_OK;
+}
+
+// Locate (i, j) in a sorted CSR row; -1 if absent.
+static int64_t find_entry(const std::vector<int64_t> &rp, const std::vector<int32_t> &cl, int64_t i, int32_t j)
+{
+    auto b = cl.begin() + rp[i], e = cl.begin() + rp[i + 1];
+    auto it = std::lower_bound(b, e, j);
+    return (it != e && *it == j) ? (int64_t)(it - cl.begin()) : -1;
+}
+
+}  // namespace gcie
+
+using namespace gcie;
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *gcie_strerror(int code)
+{
+    switch (code) {
+    case GCIE_OK: return "ok";
+    case GCIE_EINVAL: return "invalid argument";
+    case GCIE_ENOTSYM: return "matrix not symmetric";
+    case GCIE_ENOTSPD: return "mass matrix not positive definite";
+    case GCIE_ENOMEM: return "out of memory";
+    case GCIE_ENOCONV: return "not converged";
+    case GCIE_EBREAKDOWN: return "COCG breakdown";
+    case GCIE_ETIMEOUT: return "device wait timed out";
+    case GCIE_ECOUNT: return "eigenvalue count mismatch";
+    case GCIE_ECUDA: return "CUDA error";
+    default: return "unknown status";
+    }
+}
+
+const char *gcie_last_error(void) { return g_err.c_str(); }
+
+void gcie_default_opts(gcie_opts *o)
+{
+    std::memset(o, 0, sizeof(*o));
+    o->nodes = 16;
+    o->L = 32;
+    o->moments = 2;
+    o->max_outer = 8;
+    o->max_iters = 100000;
+    o->precision = GCIE_MIXED;
+    o->tol = 1e-10;
+    o->lin_tol = 1e-11;
+    o->ncontours = 0;
+    o->nuniform = 1;
+    o->alpha = 0.0;
+    o->seed = 1;
+    o->expected_count = -1;
+}
+
+int gcie_create(gcie_ctx **out, int device, void *stream)
+{
+    if (!out) { set_error("gcie_create: out is NULL"); return GCIE_EINVAL; }
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        set_error("gcie_create: no such CUDA device");
+        return GCIE_EINVAL;
+    }
+    GCIE_CUDA_TRY(cudaSetDevice(device));
+    gcie_ctx *c = new gcie_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaGetDeviceProperties(&prop, device);
+    c->num_sms = prop.multiProcessorCount;
+    c->smem_optin = prop.sharedMemPerBlockOptin;
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            set_error("gcie_create: stream creation failed");
+            return GCIE_ECUDA;
+        }
+        c->own_stream = true;
+    }
+    *out = c;
+    return GCIE_OK;
+}
+
+void gcie_destroy(gcie_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    flush_timing(c);
+    if (c->scratch) cudaFree(c->scratch);
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+int gcie_get_stats(gcie_ctx *c, gcie_stats *out)
+{
+    if (!c || !out) return GCIE_EINVAL;
+    cudaStreamSynchronize(c->stream);
+    flush_timing(c);
+    *out = c->stats;
+    return GCIE_OK;
+}
+
+void gcie_set_profile(gcie_ctx *c, int on)
+{
+    if (c) c->profile = on != 0;
+}
+
+void gcie_reset_stats(gcie_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    flush_timing(c);
+    std::memset(&c->stats, 0, sizeof(c->stats));
+}
+
+int gcie_pencil_create(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, gcie_pencil **out)
+{
+    if (!c || !out) { set_error("gcie_pencil_create: null argument"); return GCIE_EINVAL; }
+    *out = nullptr;
+    GCIE_TRY(check_csr(K, "K"));
+    GCIE_TRY(check_csr(M, "M"));
+    if (K->n != M->n) { set_error("K and M differ in size"); return GCIE_EINVAL; }
+    const int64_t n = K->n;
+    gcie_pencil *p = new gcie_pencil();
+    p->ctx = c;
+    p->n = n;
+    // union pattern, row by row
+    std::vector<int64_t> &rp = p->h_rowptr;
+    std::vector<int32_t> &cl = p->h_col;
+    std::vector<double> &kv = p->h_k, &mv = p->h_m;
+    rp.assign(n + 1, 0);
+    cl.reserve(std::max(K->nnz, M->nnz));
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t a = K->rowptr[i], ae = K->rowptr[i + 1], b = M->rowptr[i], be = M->rowptr[i + 1];
+        while (a < ae || b < be) {
+            int32_t ja = a < ae ? K->col[a] : INT32_MAX, jb = b < be ? M->col[b] : INT32_MAX;
+            int32_t j = std::min(ja, jb);
+            cl.push_back(j);
+            kv.push_back(ja == j ? K->val[a++] : 0.0);
+            mv.push_back(jb == j ? M->val[b++] : 0.0);
+        }
+        rp[i + 1] = (int64_t)cl.size();
+    }
+    p->nnz = rp[n];
+    if (p->nnz >= ((int64_t)1 << 31)) { delete p; set_error("union pattern nnz >= 2^31"); return GCIE_EINVAL; }
+    // symmetry of every stored entry, then exact symmetrisation; diagonal of M; bandwidth; ||K||_1
+    std::vector<double> ks(kv.size()), ms(mv.size());
+    int bw = 0;
+    double nk = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        bool diag = false;
+        double rowsum = 0.0;
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const int32_t j = cl[k];
+            bw = std::max<int>(bw, (int)std::llabs((long long)(j - i)));
+            const int64_t t = find_entry(rp, cl, j, (int32_t)i);
+            if (t < 0) {
+                if (kv[k] != 0.0 || mv[k] != 0.0) { delete p; set_error("entry (" + std::to_string(i) + "," + std::to_string(j) + ") has no transpose"); return GCIE_ENOTSYM; }
+                ks[k] = 0.0; ms[k] = 0.0;
+                continue;
+            }
+            const double tolk = 1e-12 * std::max(std::fabs(kv[k]), std::fabs(kv[t]));
+            const double tolm = 1e-12 * std::max(std::fabs(mv[k]), std::fabs(mv[t]));
+            if (std::fabs(kv[k] - kv[t]) > tolk || std::fabs(mv[k] - mv[t]) > tolm) {
+                delete p;
+                set_error("asymmetric entry at (" + std::to_string(i) + "," + std::to_string(j) + ")");
+                return GCIE_ENOTSYM;
+            }
+            ks[k] = 0.5 * (kv[k] + kv[t]);
+            ms[k] = 0.5 * (mv[k] + mv[t]);
+            rowsum += std::fabs(ks[k]);
+            if (j == i) {
+                diag = true;
+                if (!(ms[k] > 0.0)) { delete p; set_error("M has a non-positive diagonal entry in row " + std::to_string(i)); return GCIE_ENOTSPD; }
+            }
+        }
+        if (!diag) { delete p; set_error("M has no diagonal entry in row " + std::to_string(i)); return GCIE_ENOTSPD; }
+        nk = std::max(nk, rowsum);
+    }
+    kv.swap(ks);
+    mv.swap(ms);
+    p->bw = bw;
+    p->norm_k1 = nk;
+    // device copies
+    std::vector<int> rp32(n + 1);
+    for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp[i];
+    std::vector<float> k32(p->nnz), m32(p->nnz);
+    for (int64_t k = 0; k < p->nnz; ++k) { k32[k] = (float)kv[k]; m32[k] = (float)mv[k]; }
+    cudaSetDevice(c->device);
+    const size_t nz = (size_t)p->nnz;
+    bool ok = cudaMalloc(&p->rowptr, sizeof(int) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&p->col, sizeof(int) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->k32, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->m32, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->k64, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->m64, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess;
+    if (!ok) { cudaGetLastError(); gcie_pencil_destroy(p); set_error("pencil: device allocation failed"); return GCIE_ENOMEM; }
+    cudaStream_t st = c->stream;
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaMemcpyAsync(p->rowptr, rp32.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->col, cl.data(), sizeof(int) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->k32, k32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->m32, m32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->k64, kv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->m64, mv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { gcie_pencil_destroy(p); set_error(std::string("pencil upload: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
+    *out = p;
+    return GCIE_OK;
+}
+
+void gcie_pencil_destroy(gcie_pencil *p)
+{
+    if (!p) return;
+    if (p->ctx) cudaStreamSynchronize(p->ctx->stream);
+    cudaFree(p->rowptr); cudaFree(p->col); cudaFree(p->k32); cudaFree(p->m32); cudaFree(p->k64); cudaFree(p->m64);
+    delete p;
+}
+
+int64_t gcie_pencil_n(const gcie_pencil *p) { return p ? p->n : -1; }
+int64_t gcie_pencil_nnz(const gcie_pencil *p) { return p ? p->nnz : -1; }
+
+int gcie_trapezoid_nodes(double c, double r, int32_t N, double *h_z, double *h_w)
+{
+    if (N < 2 || N % 2 || !h_z || !h_w || !(r > 0)) { set_error("trapezoid: N even >= 2, r > 0"); return GCIE_EINVAL; }
+    std::vector<double2> z, w;
+    trapezoid(c, r, N, z, w);
+    for (int j = 0; j < N / 2; ++j) {
+        h_z[2 * j] = z[j].x; h_z[2 * j + 1] = z[j].y;
+        h_w[2 * j] = w[j].x; h_w[2 * j + 1] = w[j].y;
+    }
+    return GCIE_OK;
+}
+
+static int upload_shifts(gcie_ctx *c, int nshift, const double *h_z, double2 **d_z)
+{
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)d_z, sizeof(double2) * std::max(nshift, 1), c->stream));
+    GCIE_CUDA_TRY(cudaMemcpyAsync(*d_z, h_z, sizeof(double2) * nshift, cudaMemcpyHostToDevice, c->stream));
+    return GCIE_OK;
+}
+
+int gcie_shifted_spmm_f32(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const float *d_P,
+                          float *d_Q)
+{
+    if (!c || !p || !h_z || !d_P || !d_Q || nshift < 0 || ncol <= 0) { set_error("spmm_f32: bad argument"); return GCIE_EINVAL; }
+    double2 *dz = nullptr;
+    GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
+    int rc = shifted_spmm_f32(c, p, nshift, dz, ncol, (const float2 *)d_P, (float2 *)d_Q);
+    cudaFreeAsync(dz, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+int gcie_shifted_spmm_f64(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const double *d_P,
+                          double *d_Q)
+{
+    if (!c || !p || !h_z || !d_P || !d_Q || nshift < 0 || ncol <= 0) { set_error("spmm_f64: bad argument"); return GCIE_EINVAL; }
+    double2 *dz = nullptr;
+    GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
+    int rc = shifted_spmm_f64(c, p, nshift, dz, ncol, (const double2 *)d_P, (double2 *)d_Q);
+    cudaFreeAsync(dz, c->stream);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const double *d_B,
+                       double *d_X, int32_t x0, double lin_tol, int32_t max_iters, int32_t precision, int64_t *h_iters)
+{
+    if (!c || !p || !h_z || !d_B || !d_X || nshift <= 0 || ncol <= 0 || !(lin_tol > 0) || max_iters < 0) {
+        set_error("shifted_solve: bad argument");
+        return GCIE_EINVAL;
+    }
+    if (precision != GCIE_MIXED && precision != GCIE_FP64) { set_error("shifted_solve: precision"); return GCIE_EINVAL; }
+    if (precision == GCIE_MIXED && ncol % 2) { set_error("shifted_solve: mixed precision needs an even ncol"); return GCIE_EINVAL; }
+    std::vector<int> rhs(nshift, 0);
+    SolveInfo info;
+    int rc = cocg_solve(c, p, nshift, h_z, rhs.data(), 1, ncol, d_B, (double2 *)d_X, x0 != 0, lin_tol, max_iters,
+                        precision, &info);
+    if (h_iters) *h_iters = info.iters;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+int gcie_moments(gcie_ctx *c, int64_t n, int32_t nshift, const double *h_z, const double *h_w, double cc, double r,
+                 int32_t m, int32_t ncol, const double *d_X, double *d_S)
+{
+    if (!c || !h_z || !h_w || !d_X || !d_S || n <= 0 || nshift <= 0 || m < 1 || m > 8 || ncol <= 0 || !(r > 0)) {
+        set_error("moments: bad argument");
+        return GCIE_EINVAL;
+    }
+    std::vector<double2> coef((size_t)nshift * m);
+    for (int s = 0; s < nshift; ++s) {
+        double2 zs = make_double2(h_z[2 * s], h_z[2 * s + 1]);
+        double2 ws = make_double2(h_w[2 * s], h_w[2 * s + 1]);
+        double2 sn = make_double2((zs.x - cc) / r, zs.y / r);
+        double2 pw = make_double2(1, 0);
+        for (int k = 0; k < m; ++k) {
+            coef[(size_t)s * m + k] = cmul(ws, pw);
+            pw = cmul(pw, sn);
+        }
+    }
+    int rc = moments(c, n, nshift, coef.data(), m, ncol, (const double2 *)d_X, d_S, m * ncol);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+int gcie_m_orthonormalize(gcie_ctx *c, gcie_pencil *p, int32_t ncolY, const double *d_Y, double drop, double *d_Q,
+                          int32_t *h_rank)
+{
+    if (!c || !p || !d_Y || !d_Q || ncolY <= 0 || ncolY > 256 || !(drop >= 0)) { set_error("m_orthonormalize: bad argument"); return GCIE_EINVAL; }
+    int rank = 0;
+    int rc = m_orthonormalize(c, p, p->n, ncolY, d_Y, drop, d_Q, &rank);
+    if (h_rank) *h_rank = rank;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+int gcie_rayleigh_ritz(gcie_ctx *c, gcie_pencil *p, int32_t q, const double *d_Q, double *d_Z, double *h_theta,
+                       double *h_res)
+{
+    if (!c || !p || !d_Q || !d_Z || !h_theta || !h_res || q <= 0 || q > 256) { set_error("rayleigh_ritz: bad argument"); return GCIE_EINVAL; }
+    return rayleigh_ritz(c, p, q, d_Q, d_Z, h_theta, h_res);
+}
+
+int gcie_jacobi_eig(gcie_ctx *c, int32_t p, double *d_A, double *d_w, double *d_V)
+{
+    if (!c || !d_A || !d_w || !d_V || p <= 0 || p > 1024) { set_error("jacobi: bad argument"); return GCIE_EINVAL; }
+    int rc = jacobi(c, 1, p, d_A, d_w, d_V);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
+    return rc;
+}
+
+}  // extern "C"
+
+// ====================================================================== the solver driver
+namespace gcie {
+
+// X0[s][i][l] = Z[i][l] / (z_s - theta_l): the filtered Ritz block as the first guess of the
+// shifted solves of a FEAST iteration (exact when the Ritz pairs are eigenpairs).
+__global__ void k_warm_start(int64_t n, int nshift, int ncol, int q, const double *__restrict__ Z,
+                             const double2 *__restrict__ coef, double2 *__restrict__ X)
+{
+    const int64_t total = (int64_t)nshift * n * ncol;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e % ncol);
+        const int64_t i = (e / ncol) % n;
+        const int s = (int)(e / ((int64_t)n * ncol));
+        double2 out = make_double2(0, 0);
+        if (l < q) {
+            const double zz = Z[i * q + l];
+            const double2 cf = coef[(int64_t)s * ncol + l];
+            out = make_double2(zz * cf.x, zz * cf.y);
+        }
+        X[e] = out;
+    }
+}
+
+// out[j*n + i] = Z[i*q + idx[j]]  (selected columns, column-major)
+__global__ void k_gather_cols(int64_t n, int q, int k, const int *__restrict__ idx, const double *__restrict__ Z,
+                              double *__restrict__ out)
+{
+    const int64_t total = n * k;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int j = (int)(e / n);
+        const int64_t i = e % n;
+        out[e] = Z[i * q + idx[j]];
+    }
+}
+
+// copy columns [0, k) of a row-major n x ld block into a row-major n x k block; padding columns
+// [k, kpad) are zeroed
+__global__ void k_copy_cols(int64_t n, int ld, int k, int kpad, const double *__restrict__ A, double *__restrict__ B)
+{
+    const int64_t total = n * kpad;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e % kpad);
+        const int64_t i = e / kpad;
+        B[e] = l < k ? A[i * ld + l] : 0.0;
+    }
+}
+
+static int grid_for(const Ctx *c, int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 32)); }
+
+struct ContourState {
+    double c, r, lo, hi;
+    int ncol = 0;          // columns of the current right-hand side block
+    int m = 0;             // moments this iteration
+    double *V = nullptr;   // device n x ncol (starting block of this iteration; owned when it > 0)
+    double *Z = nullptr;   // device n x q Ritz vectors of the last iteration
+    std::vector<double> theta;
+    int q = 0;
+    int iters = 0;
+    bool done = false;
+    int status = GCIE_OK;
+    // kept pairs
+    std::vector<double> kv, kr;
+    std::vector<double> kvec;   // column-major n x kept
+};
+
+static double dot_m(const Pencil *p, const double *x, const double *y)
+{
+    double s = 0.0;
+    for (int64_t i = 0; i < p->n; ++i) {
+        double mi = 0.0;
+        for (int64_t k = p->h_rowptr[i]; k < p->h_rowptr[i + 1]; ++k) mi += p->h_m[k] * y[p->h_col[k]];
+        s += x[i] * mi;
+    }
+    return s;
+}
+
+static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts *o, gcie_result *res)
+{
+    const int64_t n = p->n;
+    const int N = o->nodes, L0 = o->L, half = N / 2;
+    std::vector<ContourState> cs;
+    if (o->ncontours > 0) {
+        for (int k = 0; k < o->ncontours; ++k) {
+            ContourState s;
+            s.c = o->contours[k].c; s.r = o->contours[k].r; s.lo = o->contours[k].lo; s.hi = o->contours[k].hi;
+            cs.push_back(s);
+        }
+    } else {
+        for (int k = 0; k < o->nuniform; ++k) {
+            ContourState s;
+            s.lo = lo + (hi - lo) * k / o->nuniform;
+            s.hi = (k + 1 == o->nuniform) ? hi : lo + (hi - lo) * (k + 1) / o->nuniform;
+            s.c = 0.5 * (s.lo + s.hi);
+            s.r = (1.0 + o->alpha) * 0.5 * (s.hi - s.lo);
+            cs.push_back(s);
+        }
+    }
+    const int nc = (int)cs.size();
+    // starting block V (n x L0) and B0 = M V
+    std::vector<double> hV;
+    const double *srcV = o->h_V0;
+    if (!srcV) {
+        hV.resize((size_t)n * L0);
+        draw_gaussian(o->seed, (int64_t)n * L0, hV.data());
+        srcV = hV.data();
+    }
+    const int L = L0 + (L0 & 1);   // even width for the FP32 vector loads
+    double *dV0 = nullptr, *dB0 = nullptr;
+    GCIE_CUDA_TRY(cudaMalloc(&dV0, sizeof(double) * (size_t)n * L));
+    if (cudaMalloc(&dB0, sizeof(double) * (size_t)n * L) != cudaSuccess) { cudaFree(dV0); set_error("out of memory"); return GCIE_ENOMEM; }
+    int rc = GCIE_OK;
+    struct Guard { std::vector<void *> ptrs; ~Guard() { for (void *q : ptrs) cudaFree(q); } } guard;
+    guard.ptrs.push_back(dV0);
+    guard.ptrs.push_back(dB0);
+    GCIE_CUDA_TRY(cudaMemsetAsync(dV0, 0, sizeof(double) * (size_t)n * L, c->stream));
+    GCIE_CUDA_TRY(cudaMemcpy2DAsync(dV0, sizeof(double) * L, srcV, sizeof(double) * L0, sizeof(double) * L0, n,
+                                    cudaMemcpyHostToDevice, c->stream));
+    GCIE_TRY(spmm_real(c, p, 1, L, dV0, dB0));
+    for (auto &s : cs) { s.ncol = L; s.m = o->moments; }
+
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t budget = o->hbm_budget_bytes ? o->hbm_budget_bytes : (size_t)(0.85 * free_b);
+    const size_t esz = o->precision == GCIE_FP64 ? 16 : 8;
+    int64_t cocg_iters = 0;
+
+    for (int it = 0; it < o->max_outer; ++it) {
+        std::vector<int> act;
+        for (int k = 0; k < nc; ++k)
+            if (!cs[k].done) act.push_back(k);
+        if (act.empty()) break;
+        // batches of contours that fit the memory budget
+        size_t b0 = 0;
+        while (b0 < act.size()) {
+            int ncol = 0;
+            size_t b1 = b0;
+            while (b1 < act.size()) {
+                int nn = std::max(ncol, cs[act[b1]].ncol);
+                nn += nn & 1;
+                const size_t per = (size_t)half * n * nn * (4 * esz + 16) + (size_t)n * nn * 8 * 4;
+                if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
+                ncol = nn;
+                ++b1;
+            }
+            const int nb = (int)(b1 - b0);
+            const int nshift = nb * half;
+            std::vector<double> hz(2 * (size_t)nshift);
+            std::vector<int> rhs_of(nshift);
+            std::vector<std::vector<double2>> zw(nb), ww(nb);
+            for (int bi = 0; bi < nb; ++bi) {
+                ContourState &s = cs[act[b0 + bi]];
+                trapezoid(s.c, s.r, N, zw[bi], ww[bi]);
+                for (int j = 0; j < half; ++j) {
+                    hz[2 * (bi * half + j)] = zw[bi][j].x;
+                    hz[2 * (bi * half + j) + 1] = zw[bi][j].y;
+                    rhs_of[bi * half + j] = it == 0 ? 0 : bi;
+                }
+            }
+            // right-hand sides
+            double *dB = dB0;
+            int nrhs = 1;
+            double *dBb = nullptr;
+            double2 *dX = nullptr;
+            if (cudaMalloc(&dX, sizeof(double2) * (size_t)nshift * n * ncol) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("solution block allocation failed");
+                return GCIE_ENOMEM;
+            }
+            guard.ptrs.push_back(dX);
+            bool x0 = false;
+            if (it > 0) {
+                nrhs = nb;
+                GCIE_CUDA_TRY(cudaMalloc(&dBb, sizeof(double) * (size_t)nb * n * ncol));
+                guard.ptrs.push_back(dBb);
+                double *tmp = nullptr;
+                GCIE_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)n * ncol));
+                guard.ptrs.push_back(tmp);
+                for (int bi = 0; bi < nb; ++bi) {
+                    ContourState &s = cs[act[b0 + bi]];
+                    {
+                        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * ncol, 0);
+                        k_copy_cols<<<grid_for(c, n * ncol), 256, 0, c->stream>>>(n, s.q, s.q, ncol, s.Z, tmp);
+                        GCIE_CUDA_TRY(cudaGetLastError());
+                    }
+                    GCIE_TRY(spmm_real(c, p, 1, ncol, tmp, dBb + (size_t)bi * n * ncol));
+                    // warm start from the Ritz pairs
+                    std::vector<double2> coef((size_t)half * ncol, make_double2(0, 0));
+                    for (int j = 0; j < half; ++j)
+                        for (int l = 0; l < s.q; ++l) {
+                            double2 d = make_double2(zw[bi][j].x - s.theta[l], zw[bi][j].y);
+                            coef[(size_t)j * ncol + l] = cdiv(make_double2(1, 0), d);
+                        }
+                    double2 *dcoef = nullptr;
+                    GCIE_CUDA_TRY(cudaMalloc(&dcoef, sizeof(double2) * coef.size()));
+                    guard.ptrs.push_back(dcoef);
+                    GCIE_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, c->stream));
+                    {
+                        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * half * n * ncol, 0);
+                        k_warm_start<<<grid_for(c, (int64_t)half * n * ncol), 256, 0, c->stream>>>(
+                            n, half, ncol, s.q, s.Z, dcoef, dX + (size_t)bi * half * n * ncol);
+                        GCIE_CUDA_TRY(cudaGetLastError());
+                    }
+                }
+                dB = dBb;
+                x0 = true;
+            }
+            SolveInfo info;
+            int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
+                                 o->precision, &info);
+            cocg_iters += info.iters;
+            if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
+            // per contour: moments, basis, Rayleigh-Ritz, keep
+            for (int bi = 0; bi < nb; ++bi) {
+                ContourState &s = cs[act[b0 + bi]];
+                const int m = s.m;
+                const int pY = m * ncol;
+                if (pY > 256) { set_error("moments x columns > 256"); return GCIE_EINVAL; }
+                double *Y = nullptr, *Q = nullptr;
+                GCIE_CUDA_TRY(cudaMalloc(&Y, sizeof(double) * (size_t)n * pY));
+                guard.ptrs.push_back(Y);
+                GCIE_CUDA_TRY(cudaMalloc(&Q, sizeof(double) * (size_t)n * pY));
+                guard.ptrs.push_back(Q);
+                GCIE_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * pY, c->stream));
+                std::vector<double2> coef((size_t)half * m);
+                for (int j = 0; j < half; ++j) {
+                    double2 sn = make_double2((zw[bi][j].x - s.c) / s.r, zw[bi][j].y / s.r);
+                    double2 pw = make_double2(1, 0);
+                    for (int k = 0; k < m; ++k) { coef[(size_t)j * m + k] = cmul(ww[bi][j], pw); pw = cmul(pw, sn); }
+                }
+                GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Y, pY));
+                int rank = 0;
+                GCIE_TRY(m_orthonormalize(c, p, n, pY, Y, 1e-14, Q, &rank));
+                double *Qc = nullptr, *Z = nullptr;
+                GCIE_CUDA_TRY(cudaMalloc(&Qc, sizeof(double) * (size_t)n * rank));
+                guard.ptrs.push_back(Qc);
+                GCIE_CUDA_TRY(cudaMalloc(&Z, sizeof(double) * (size_t)n * rank));
+                {
+                    LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
+                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pY, rank, rank, Q, Qc);
+                    GCIE_CUDA_TRY(cudaGetLastError());
+                }
+                std::vector<double> th(rank), rs(rank);
+                rc = rayleigh_ritz(c, p, rank, Qc, Z, th.data(), rs.data());
+                if (rc) { cudaFree(Z); return rc; }
+                bool unconverged_inside = false;
+                std::vector<int> keep;
+                for (int l = 0; l < rank; ++l) {
+                    const bool inside = th[l] >= s.lo && th[l] <= s.hi;
+                    if (!inside) continue;
+                    if (rs[l] <= o->tol) keep.push_back(l);
+                    else unconverged_inside = true;
+                }
+                s.iters = it + 1;
+                const bool last = (it + 1 == o->max_outer);
+                if (!unconverged_inside || last) {
+                    // final: keep converged pairs
+                    if (!keep.empty()) {
+                        int *didx = nullptr;
+                        double *dout = nullptr;
+                        GCIE_CUDA_TRY(cudaMalloc(&didx, sizeof(int) * keep.size()));
+                        guard.ptrs.push_back(didx);
+                        GCIE_CUDA_TRY(cudaMalloc(&dout, sizeof(double) * (size_t)n * keep.size()));
+                        guard.ptrs.push_back(dout);
+                        GCIE_CUDA_TRY(cudaMemcpyAsync(didx, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, c->stream));
+                        {
+                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
+                            k_gather_cols<<<grid_for(c, n * (int64_t)keep.size()), 256, 0, c->stream>>>(n, rank, (int)keep.size(), didx, Z, dout);
+                            GCIE_CUDA_TRY(cudaGetLastError());
+                        }
+                        const size_t off = s.kvec.size();
+                        s.kvec.resize(off + (size_t)n * keep.size());
+                        GCIE_CUDA_TRY(cudaMemcpyAsync(s.kvec.data() + off, dout, sizeof(double) * (size_t)n * keep.size(),
+                                                      cudaMemcpyDeviceToHost, c->stream));
+                        GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+                        for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
+                    }
+                    s.done = true;
+                    s.status = unconverged_inside ? GCIE_ENOCONV : GCIE_OK;
+                    cudaFree(Z);
+                    if (s.Z) { cudaFree(s.Z); s.Z = nullptr; }
+                } else {
+                    // FEAST: next iteration filters all Ritz vectors, one moment
+                    if (s.Z) cudaFree(s.Z);
+                    s.Z = Z;
+                    s.q = rank;
+                    s.theta = th;
+                    s.ncol = rank;
+                    s.m = 1;
+                }
+            }
+            // release per-batch buffers now (the guard frees anything left on error paths)
+            GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            for (void *q : guard.ptrs)
+                if (q != dV0 && q != dB0) cudaFree(q);
+            guard.ptrs.assign({dV0, dB0});
+            b0 = b1;
+        }
+    }
+    for (auto &s : cs)
+        if (s.Z) { cudaFree(s.Z); s.Z = nullptr; }
+
+    // merge and de-duplicate across contours (Algorithm 1, last step)
+    struct Pair { double v, r; int k; const double *x; };
+    std::vector<Pair> all;
+    for (int k = 0; k < nc; ++k)
+        for (size_t j = 0; j < cs[k].kv.size(); ++j) all.push_back({cs[k].kv[j], cs[k].kr[j], k, cs[k].kvec.data() + j * n});
+    std::stable_sort(all.begin(), all.end(), [](const Pair &a, const Pair &b) { return a.v < b.v; });
+    std::vector<Pair> kept;
+    for (const Pair &pr : all) {
+        bool dup = false;
+        for (int t = (int)kept.size() - 1; t >= 0; --t) {
+            if (std::fabs(pr.v - kept[t].v) > 1e-8 * std::max(1.0, std::fabs(pr.v))) break;
+            if (std::fabs(dot_m(p, pr.x, kept[t].x)) > 0.5) {
+                dup = true;
+                if (pr.r < kept[t].r) kept[t] = pr;
+                break;
+            }
+        }
+        if (!dup) kept.push_back(pr);
+    }
+    res->n = n;
+    res->count = (int32_t)kept.size();
+    res->ncontours = nc;
+    res->evals = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, kept.size()));
+    res->resid = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, kept.size()));
+    res->contour_of = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(1, kept.size()));
+    res->evecs = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, (size_t)n * kept.size()));
+    res->status_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nc));
+    res->iters_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nc));
+    if (!res->evals || !res->resid || !res->contour_of || !res->evecs || !res->status_per_contour || !res->iters_per_contour) {
+        gcie_result_free(res);
+        set_error("result allocation failed");
+        return GCIE_ENOMEM;
+    }
+    for (size_t j = 0; j < kept.size(); ++j) {
+        res->evals[j] = kept[j].v;
+        res->resid[j] = kept[j].r;
+        res->contour_of[j] = kept[j].k;
+        double *dst = res->evecs + j * n;
+        const double *x = kept[j].x;
+        // Ritz vectors are M-orthonormal by construction (Q M-orthonormal, W orthogonal); only the
+        // sign is fixed here: the entry of largest magnitude is made positive
+        const double nm = 1.0;
+        int64_t im = 0;
+        for (int64_t i = 1; i < n; ++i)
+            if (std::fabs(x[i]) > std::fabs(x[im])) im = i;
+        const double sg = x[im] < 0 ? -1.0 : 1.0;
+        for (int64_t i = 0; i < n; ++i) dst[i] = sg * x[i] / nm;
+    }
+    int worst = GCIE_OK, outer = 0;
+    for (int k = 0; k < nc; ++k) {
+        res->status_per_contour[k] = cs[k].status;
+        res->iters_per_contour[k] = cs[k].iters;
+        outer = std::max(outer, cs[k].iters);
+        if (cs[k].status != GCIE_OK) worst = cs[k].status;
+    }
+    res->outer_iters = outer;
+    res->cocg_iters = cocg_iters;
+    res->norm_k1 = p->norm_k1;
+    if (worst != GCIE_OK) { set_error("some contours did not converge"); return worst; }
+    if (o->expected_count >= 0 && o->expected_count != res->count) {
+        set_error("count " + std::to_string(res->count) + " != expected " + std::to_string(o->expected_count));
+        return GCIE_ECOUNT;
+    }
+    return GCIE_OK;
+}
+
+}  // namespace gcie
+
+extern "C" {
+
+int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const gcie_opts *opts, gcie_result *out)
+{
+    if (!c || !p || !out) { set_error("solve: null argument"); return GCIE_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    gcie_opts o;
+    if (opts) o = *opts; else gcie_default_opts(&o);
+    if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) { set_error("solve: need finite lo < hi"); return GCIE_EINVAL; }
+    if (o.nodes < 2 || o.nodes > 64 || o.nodes % 2 || o.L < 1 || o.moments < 1 || o.moments > 8 || o.max_outer < 1 ||
+        o.max_iters < 1 || !(o.tol > 0) || !(o.lin_tol > 0) || (o.precision != GCIE_MIXED && o.precision != GCIE_FP64) ||
+        o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0) {
+        set_error("solve: option out of range");
+        return GCIE_EINVAL;
+    }
+    if (o.moments * (o.L + (o.L & 1)) > 256) { set_error("solve: moments x L must be <= 256"); return GCIE_EINVAL; }
+    for (int k = 0; k < o.ncontours; ++k)
+        if (!(o.contours[k].r > 0) || !(o.contours[k].lo <= o.contours[k].hi)) { set_error("solve: bad contour"); return GCIE_EINVAL; }
+    cudaSetDevice(c->device);
+    if (o.profile) c->profile = true;
+    int rc = solve_driver(c, p, lo, hi, &o, out);
+    cudaStreamSynchronize(c->stream);
+    if (c->profile) flush_timing(c);
+    return rc;
+}
+
+int gcie_solve(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, double lo, double hi, const gcie_opts *opts,
+               gcie_result *out)
+{
+    if (!c || !out) { set_error("solve: null argument"); return GCIE_EINVAL; }
+    std::memset(out, 0, sizeof(*out));
+    gcie_pencil *p = nullptr;
+    GCIE_TRY(gcie_pencil_create(c, K, M, &p));
+    int rc = gcie_solve_pencil(c, p, lo, hi, opts, out);
+    gcie_pencil_destroy(p);
+    return rc;
+}
+
+void gcie_result_free(gcie_result *r)
+{
+    if (!r) return;
+    std::free(r->evals); std::free(r->evecs); std::free(r->resid); std::free(r->contour_of);
+    std::free(r->status_per_contour); std::free(r->iters_per_contour);
+    std::memset(r, 0, sizeof(*r));
+}
+
+}  // extern "C"

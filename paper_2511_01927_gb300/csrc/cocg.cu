@@ -1,0 +1,617 @@
+// Batched shifted solves (steps a4-a6): (z_s M - K) X[s] = B for every quadrature node s.
+//
+// The paper computes the projector by quadrature, which reduces to solving the N_q shifted
+// systems (z_j B - A) Y_j = B V (Eq. quadrature_appendix) -- the dominant cost.  With real
+// symmetric K, M the matrices z M - K are complex symmetric, so each column is solved by COCG
+// (conjugate orthogonal CG: CG with the unconjugated bilinear form x^T y).
+//
+// Mixed precision: the COCG recurrences run in FP32 complex on a correction d for the FP64
+// iterate x64; "reliable updates" fold d into x64 and replace the FP32 residual by the true
+// FP64 residual b - (z M - K) x64 whenever the recursive residual has fallen by a factor delta
+// since the last update, or looks converged.  Convergence is decided on the FP64 residual only.
+// In FP64 mode the same recurrences run in FP64 (delta = 0: refinements happen only to confirm
+// convergence).
+//
+// One COCG iteration = two fused sweeps over the pencil rows (each reads every neighbour row of
+// the block through L1/L2):
+//   dir: p_new = r + beta p_old (formed at the neighbour rows on the fly), A p_new, and the
+//        partial sums of p_new^T (A p_new);                     reads r, p_old; writes p_new
+//   upd: A p_new again, d += alpha p_new, r -= alpha A p_new, partial sums of r^T r and |r|^2;
+//                                                                 reads p_new, d, r; writes d, r
+// so the block is streamed 8 times per iteration and A p is never stored.  Per-column scalars
+// (alpha, beta, rho) are formed by small kernels from per-CTA partial sums in a fixed order, so
+// the iteration is deterministic.  Converged columns freeze (alpha = beta = 0) and a node whose
+// columns have all converged drops out of the sweeps.
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace gcie {
+
+enum : int { F_ACTIVE = 1, F_CONV = 2, F_RESTART = 4 };
+
+template <typename T, int CPT> struct V2;
+template <> struct V2<float, 2> {
+    float2 v[2];
+    __device__ __forceinline__ void load(const float2 *p) {
+        float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+        v[0] = make_float2(t.x, t.y); v[1] = make_float2(t.z, t.w);
+    }
+    __device__ __forceinline__ void load_cg(const float2 *p) {   // coherent load (buffer written by this kernel)
+        float4 t = *reinterpret_cast<const float4 *>(p);
+        v[0] = make_float2(t.x, t.y); v[1] = make_float2(t.z, t.w);
+    }
+    __device__ __forceinline__ void store(float2 *p) const {
+        *reinterpret_cast<float4 *>(p) = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+    }
+};
+template <> struct V2<double, 1> {
+    double2 v[1];
+    __device__ __forceinline__ void load(const double2 *p) { v[0] = __ldg(p); }
+    __device__ __forceinline__ void load_cg(const double2 *p) { v[0] = *p; }
+    __device__ __forceinline__ void store(double2 *p) const { *p = v[0]; }
+};
+
+template <typename T> struct Acc;           // accumulator type of the per-thread partial sums
+template <> struct Acc<float> { using t = float; };
+template <> struct Acc<double> { using t = double; };
+
+// CTA reduction of per-thread complex partials (one per owned column) into partA[tile][col];
+// optional real partials into partB.  smem: threads * CPT * 3 doubles.
+template <int CPT, typename A>
+__device__ __forceinline__ void cta_partials(const A (&pa)[CPT][2], const A *pb, int ncol, int tpr, int t, int rsub,
+                                             int rpb, double2 *outA, double *outB)
+{
+    extern __shared__ double sred[];
+    double *sa = sred;                                   // [rpb][ncol][2]
+    double *sb = sred + (size_t)2 * rpb * ncol;          // [rpb][ncol]
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        int c = t * CPT + q;
+        sa[((size_t)rsub * ncol + c) * 2 + 0] = (double)pa[q][0];
+        sa[((size_t)rsub * ncol + c) * 2 + 1] = (double)pa[q][1];
+        if (pb) sb[(size_t)rsub * ncol + c] = (double)pb[q];
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double re = 0, im = 0, b = 0;
+        for (int r = 0; r < rpb; ++r) {
+            re += sa[((size_t)r * ncol + c) * 2 + 0];
+            im += sa[((size_t)r * ncol + c) * 2 + 1];
+            if (pb) b += sb[(size_t)r * ncol + c];
+        }
+        outA[c] = make_double2(re, im);
+        if (pb) outB[c] = b;
+    }
+}
+
+// ------------------------------------------------------------------ dir sweep
+template <typename T, int CPT>
+__global__ void __launch_bounds__(256) k_dir(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
+        const T *__restrict__ kv, const T *__restrict__ mv, const double2 *__restrict__ z, int ncol,
+        int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_active, const double2 *__restrict__ beta,
+        const typename cplx<T>::t *__restrict__ R, const typename cplx<T>::t *__restrict__ Pold,
+        typename cplx<T>::t *__restrict__ Pnew, double2 *__restrict__ partA)
+{
+    using C = typename cplx<T>::t;
+    using A = typename Acc<T>::t;
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!shift_active[s]) return;
+    const int tpr = ncol / CPT;
+    const int t = threadIdx.x % tpr, rsub = threadIdx.x / tpr, rpb = blockDim.x / tpr;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int64_t off = (int64_t)s * n * ncol + t * CPT;
+    const C *Rs = R + off;
+    const C *Ps = Pold + off;
+    C *Ns = Pnew + off;
+    const T zr = (T)z[s].x, zi = (T)z[s].y;
+    T br[CPT], bi[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        double2 b = beta[(int64_t)s * ncol + t * CPT + q];
+        br[q] = (T)b.x; bi[q] = (T)b.y;
+    }
+    A pa[CPT][2] = {};
+    for (int64_t i = r0 + rsub; i < r1; i += rpb) {
+        T am[CPT][2] = {}, ak[CPT][2] = {}, own[CPT][2] = {};
+        const int e1 = rowptr[i + 1];
+        for (int k = rowptr[i]; k < e1; ++k) {
+            const int j = __ldg(col + k);
+            const T a = __ldg(kv + k), b = __ldg(mv + k);
+            V2<T, CPT> rj, pj;
+            rj.load(Rs + (int64_t)j * ncol);
+            pj.load(Ps + (int64_t)j * ncol);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                // p_new(j) = r(j) + beta * p_old(j)
+                T xr = rj.v[q].x + br[q] * pj.v[q].x - bi[q] * pj.v[q].y;
+                T xi = rj.v[q].y + br[q] * pj.v[q].y + bi[q] * pj.v[q].x;
+                am[q][0] = fma(b, xr, am[q][0]); am[q][1] = fma(b, xi, am[q][1]);
+                ak[q][0] = fma(a, xr, ak[q][0]); ak[q][1] = fma(a, xi, ak[q][1]);
+                if (j == i) { own[q][0] = xr; own[q][1] = xi; }
+            }
+        }
+        V2<T, CPT> o;
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            T apr = zr * am[q][0] - zi * am[q][1] - ak[q][0];
+            T api = zr * am[q][1] + zi * am[q][0] - ak[q][1];
+            o.v[q].x = own[q][0]; o.v[q].y = own[q][1];
+            // sigma += p^T (A p), unconjugated
+            pa[q][0] += (A)(own[q][0] * apr - own[q][1] * api);
+            pa[q][1] += (A)(own[q][0] * api + own[q][1] * apr);
+        }
+        o.store(Ns + i * ncol);
+    }
+    cta_partials<CPT, A>(pa, nullptr, ncol, tpr, t, rsub, rpb, partA + ((int64_t)s * chunks + ch) * ncol, nullptr);
+}
+
+// ------------------------------------------------------------------ upd sweep
+template <typename T, int CPT>
+__global__ void __launch_bounds__(256) k_upd(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
+        const T *__restrict__ kv, const T *__restrict__ mv, const double2 *__restrict__ z, int ncol,
+        int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_active, const double2 *__restrict__ alpha,
+        const typename cplx<T>::t *__restrict__ Pn, typename cplx<T>::t *__restrict__ D,
+        typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA, double *__restrict__ partB)
+{
+    using C = typename cplx<T>::t;
+    using A = typename Acc<T>::t;
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!shift_active[s]) return;
+    const int tpr = ncol / CPT;
+    const int t = threadIdx.x % tpr, rsub = threadIdx.x / tpr, rpb = blockDim.x / tpr;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int64_t off = (int64_t)s * n * ncol + t * CPT;
+    const C *Ps = Pn + off;
+    C *Ds = D + off;
+    C *Rs = R + off;
+    const T zr = (T)z[s].x, zi = (T)z[s].y;
+    T ar[CPT], ai[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) {
+        double2 a = alpha[(int64_t)s * ncol + t * CPT + q];
+        ar[q] = (T)a.x; ai[q] = (T)a.y;
+    }
+    A pa[CPT][2] = {}, pb[CPT] = {};
+    for (int64_t i = r0 + rsub; i < r1; i += rpb) {
+        T am[CPT][2] = {}, ak[CPT][2] = {}, own[CPT][2] = {};
+        const int e1 = rowptr[i + 1];
+        for (int k = rowptr[i]; k < e1; ++k) {
+            const int j = __ldg(col + k);
+            const T a = __ldg(kv + k), b = __ldg(mv + k);
+            V2<T, CPT> pj;
+            pj.load_cg(Ps + (int64_t)j * ncol);
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                am[q][0] = fma(b, pj.v[q].x, am[q][0]); am[q][1] = fma(b, pj.v[q].y, am[q][1]);
+                ak[q][0] = fma(a, pj.v[q].x, ak[q][0]); ak[q][1] = fma(a, pj.v[q].y, ak[q][1]);
+                if (j == i) { own[q][0] = pj.v[q].x; own[q][1] = pj.v[q].y; }
+            }
+        }
+        V2<T, CPT> d, r;
+        d.load_cg(Ds + i * ncol);
+        r.load_cg(Rs + i * ncol);
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            T apr = zr * am[q][0] - zi * am[q][1] - ak[q][0];
+            T api = zr * am[q][1] + zi * am[q][0] - ak[q][1];
+            d.v[q].x += ar[q] * own[q][0] - ai[q] * own[q][1];
+            d.v[q].y += ar[q] * own[q][1] + ai[q] * own[q][0];
+            r.v[q].x -= ar[q] * apr - ai[q] * api;
+            r.v[q].y -= ar[q] * api + ai[q] * apr;
+            pa[q][0] += (A)(r.v[q].x * r.v[q].x - r.v[q].y * r.v[q].y);
+            pa[q][1] += (A)(2 * r.v[q].x * r.v[q].y);
+            pb[q] += (A)(r.v[q].x * r.v[q].x + r.v[q].y * r.v[q].y);
+        }
+        d.store(Ds + i * ncol);
+        r.store(Rs + i * ncol);
+    }
+    const int64_t tile = (int64_t)s * chunks + ch;
+    cta_partials<CPT, A>(pa, pb, ncol, tpr, t, rsub, rpb, partA + tile * ncol, partB + tile * ncol);
+}
+
+// ------------------------------------------------------------------ refinement (reliable update)
+// x64 += d, d = 0 for the shifts flagged for refinement.
+template <typename T>
+__global__ void k_refine_x(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine,
+                           typename cplx<T>::t *__restrict__ D, double2 *__restrict__ X)
+{
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!shift_refine[s]) return;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int64_t base = (int64_t)s * n * ncol;
+    for (int64_t e = r0 * ncol + threadIdx.x; e < r1 * ncol; e += blockDim.x) {
+        typename cplx<T>::t d = D[base + e];
+        double2 x = X[base + e];
+        x.x += (double)d.x; x.y += (double)d.y;
+        X[base + e] = x;
+        d.x = 0; d.y = 0;
+        D[base + e] = d;
+    }
+}
+
+// r64 = b - (z M - K) x64 in FP64; r = (T) r64; partials of r^T r (from the rounded r) and |r64|^2.
+template <typename T, int CPT>
+__global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
+        const double *__restrict__ kv, const double *__restrict__ mv, const double2 *__restrict__ z, int ncol,
+        int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine, const int *__restrict__ rhs_of,
+        const double *__restrict__ B, const double2 *__restrict__ X, typename cplx<T>::t *__restrict__ R,
+        double2 *__restrict__ partA, double *__restrict__ partB)
+{
+    using C = typename cplx<T>::t;
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!shift_refine[s]) return;
+    const int tpr = ncol / CPT;
+    const int t = threadIdx.x % tpr, rsub = threadIdx.x / tpr, rpb = blockDim.x / tpr;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int64_t off = (int64_t)s * n * ncol + t * CPT;
+    const double2 *Xs = X + off;
+    C *Rs = R + off;
+    const double *Bs = B + (int64_t)rhs_of[s] * n * ncol + t * CPT;
+    const double zr = z[s].x, zi = z[s].y;
+    double pa[CPT][2] = {}, pb[CPT] = {};
+    for (int64_t i = r0 + rsub; i < r1; i += rpb) {
+        double am[CPT][2] = {}, ak[CPT][2] = {};
+        const int e1 = rowptr[i + 1];
+        for (int k = rowptr[i]; k < e1; ++k) {
+            const int j = __ldg(col + k);
+            const double a = __ldg(kv + k), b = __ldg(mv + k);
+            const double2 *xj = Xs + (int64_t)j * ncol;
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                double2 x = __ldg(xj + q);
+                am[q][0] = fma(b, x.x, am[q][0]); am[q][1] = fma(b, x.y, am[q][1]);
+                ak[q][0] = fma(a, x.x, ak[q][0]); ak[q][1] = fma(a, x.y, ak[q][1]);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < CPT; ++q) {
+            double apr = zr * am[q][0] - zi * am[q][1] - ak[q][0];
+            double api = zr * am[q][1] + zi * am[q][0] - ak[q][1];
+            double rr = __ldg(Bs + i * ncol + q) - apr, ri = -api;
+            C rt;
+            rt.x = (T)rr; rt.y = (T)ri;
+            Rs[i * ncol + q] = rt;
+            double tr = (double)rt.x, ti = (double)rt.y;
+            pa[q][0] += tr * tr - ti * ti;
+            pa[q][1] += 2 * tr * ti;
+            pb[q] += rr * rr + ri * ri;
+        }
+    }
+    const int64_t tile = (int64_t)s * chunks + ch;
+    cta_partials<CPT, double>(pa, pb, ncol, tpr, t, rsub, rpb, partA + tile * ncol, partB + tile * ncol);
+}
+
+// ------------------------------------------------------------------ per-column scalar kernels
+// One CTA per shift, one thread per column (ncol <= 1024).
+struct Scal {
+    double2 *rho, *alpha, *beta;
+    double *eta, *eta_ref, *bnorm2;
+    int *flag, *shift_active, *shift_refine, *since_refine;
+    double2 *partA;
+    double *partB;
+};
+
+__global__ void k_scal_alpha(int ncol, int chunks, Scal S)
+{
+    const int s = blockIdx.x, l = threadIdx.x;
+    if (!S.shift_active[s] || l >= ncol) return;
+    const int64_t sc = (int64_t)s * ncol + l;
+    double2 sig = make_double2(0, 0);
+    for (int c = 0; c < chunks; ++c) {
+        double2 v = S.partA[((int64_t)s * chunks + c) * ncol + l];
+        sig.x += v.x; sig.y += v.y;
+    }
+    double2 a = make_double2(0, 0);
+    int f = S.flag[sc];
+    if (f & F_ACTIVE) {
+        double mag = fabs(sig.x) + fabs(sig.y);
+        if (!(mag > 0) || !isfinite(mag)) {
+            S.flag[sc] = f | F_RESTART;       // breakdown: restart from the true residual
+        } else {
+            a = cdiv(S.rho[sc], sig);
+        }
+    }
+    S.alpha[sc] = a;
+}
+
+__global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double tol2, int max_since)
+{
+    __shared__ int all_want;
+    const int s = blockIdx.x, l = threadIdx.x;
+    if (!S.shift_active[s]) return;
+    if (l == 0) all_want = 1;
+    __syncthreads();
+    if (l < ncol) {
+        const int64_t sc = (int64_t)s * ncol + l;
+        int f = S.flag[sc];
+        int want = 1;
+        if (f & F_ACTIVE) {
+            double2 rho = make_double2(0, 0);
+            double eta = 0;
+            for (int c = 0; c < chunks; ++c) {
+                int64_t idx = ((int64_t)s * chunks + c) * ncol + l;
+                double2 v = S.partA[idx];
+                rho.x += v.x; rho.y += v.y;
+                eta += S.partB[idx];
+            }
+            double2 ro = S.rho[sc];
+            double2 b = make_double2(0, 0);
+            if (fabs(ro.x) + fabs(ro.y) > 0) b = cdiv(rho, ro);
+            if (!(isfinite(b.x) && isfinite(b.y))) { b = make_double2(0, 0); f |= F_RESTART; }
+            S.beta[sc] = b;
+            S.rho[sc] = rho;
+            S.eta[sc] = eta;
+            S.flag[sc] = f;
+            want = (eta <= delta2 * S.eta_ref[sc]) || (eta <= tol2 * S.bnorm2[sc]) || (f & F_RESTART) || !isfinite(eta);
+        }
+        if (!want) atomicAnd(&all_want, 0);
+    }
+    __syncthreads();
+    if (l == 0) {
+        int since = S.since_refine[s] + 1;
+        S.since_refine[s] = since;
+        if (all_want || since >= max_since) S.shift_refine[s] = 1;
+    }
+}
+
+__global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
+{
+    __shared__ int any_active;
+    const int s = blockIdx.x, l = threadIdx.x;
+    if (!S.shift_refine[s]) return;
+    if (l == 0) any_active = 0;
+    __syncthreads();
+    if (l < ncol) {
+        const int64_t sc = (int64_t)s * ncol + l;
+        double2 rho = make_double2(0, 0);
+        double eta = 0;
+        for (int c = 0; c < chunks; ++c) {
+            int64_t idx = ((int64_t)s * chunks + c) * ncol + l;
+            double2 v = S.partA[idx];
+            rho.x += v.x; rho.y += v.y;
+            eta += S.partB[idx];
+        }
+        int f = S.flag[sc];
+        S.eta_ref[sc] = eta;
+        if (f & F_ACTIVE) {
+            S.eta[sc] = eta;
+            S.rho[sc] = rho;
+            if (eta <= tol2 * S.bnorm2[sc]) {
+                f = F_CONV;
+                S.beta[sc] = make_double2(0, 0);
+            } else if (f & F_RESTART) {
+                f &= ~F_RESTART;
+                S.beta[sc] = make_double2(0, 0);
+            }
+            S.flag[sc] = f;
+        }
+        if (f & F_ACTIVE) atomicOr(&any_active, 1);
+    }
+    __syncthreads();
+    if (l == 0) {
+        S.shift_active[s] = any_active;
+        S.shift_refine[s] = 0;
+        S.since_refine[s] = 0;
+    }
+}
+
+// ||b||^2 per (rhs, column): row-chunk partial sums (partB[rhs][chunk][l]) ...
+__global__ void k_bnorm_part(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const double *__restrict__ B,
+                             double *__restrict__ part)
+{
+    const int r = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const double *b = B + (int64_t)r * n * ncol;
+    for (int l = threadIdx.x; l < ncol; l += blockDim.x) {
+        double acc = 0;
+        for (int64_t i = r0; i < r1; ++i) { double v = b[i * ncol + l]; acc += v * v; }
+        part[((int64_t)r * chunks + ch) * ncol + l] = acc;
+    }
+}
+
+// ... summed in chunk order per (shift, column); initial flags and scalars.
+__global__ void k_bnorm_init(int ncol, int chunks, const int *__restrict__ rhs_of, const double *__restrict__ part, Scal S)
+{
+    const int s = blockIdx.x;
+    for (int l = threadIdx.x; l < ncol; l += blockDim.x) {
+        double acc = 0;
+        for (int c = 0; c < chunks; ++c) acc += part[((int64_t)rhs_of[s] * chunks + c) * ncol + l];
+        const int64_t sc = (int64_t)s * ncol + l;
+        S.bnorm2[sc] = acc;
+        S.flag[sc] = acc > 0 ? F_ACTIVE : F_CONV;
+        S.beta[sc] = make_double2(0, 0);
+        S.alpha[sc] = make_double2(0, 0);
+        S.rho[sc] = make_double2(0, 0);
+        S.eta_ref[sc] = acc;
+    }
+    if (threadIdx.x == 0) { S.shift_active[s] = 1; S.shift_refine[s] = 1; S.since_refine[s] = 0; }
+}
+
+// ------------------------------------------------------------------ host driver
+template <typename T>
+static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
+                   const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, SolveInfo *info)
+{
+    using C = typename cplx<T>::t;
+    constexpr int CPT = sizeof(T) == 4 ? 2 : 1;
+    const int64_t n = p->n;
+    if (ncol % CPT || ncol > 1024 || ncol <= 0) { set_error("cocg: ncol must be even and <= 1024"); return GCIE_EINVAL; }
+    Geo g = make_geo(c, n, nshift, ncol, CPT);
+    Geo gr = make_geo(c, n, nshift, ncol, 2);  // refine sweep: 2 columns per thread
+    if (ncol % 2) gr = make_geo(c, n, nshift, ncol, 1);
+    const int64_t blk = (int64_t)nshift * n * ncol;
+    const int ntiles = nshift * g.chunks, ntiles_r = nshift * gr.chunks;
+    const int maxch = std::max(g.chunks, gr.chunks);
+    // device memory: D, R, P0, P1 blocks; state; partials
+    size_t bytes = 4 * blk * sizeof(C) + (size_t)nshift * ncol * (3 * sizeof(double2) + 3 * sizeof(double) + sizeof(int)) +
+                   (size_t)nshift * 3 * sizeof(int) + (size_t)nshift * maxch * ncol * (sizeof(double2) + sizeof(double)) +
+                   (size_t)nshift * (sizeof(double2) + sizeof(int)) + 4096;
+    char *base = nullptr;
+    cudaError_t ce = cudaMallocAsync((void **)&base, bytes, c->stream);
+    if (ce != cudaSuccess) {
+        set_error(std::string("cocg: device allocation of ") + std::to_string(bytes) + " bytes failed");
+        cudaGetLastError();
+        return GCIE_ENOMEM;
+    }
+    char *q = base;
+    auto take = [&](size_t b) { char *r = q; q += (b + 255) & ~(size_t)255; return (void *)r; };
+    C *D = (C *)take(blk * sizeof(C));
+    C *R = (C *)take(blk * sizeof(C));
+    C *P[2] = {(C *)take(blk * sizeof(C)), (C *)take(blk * sizeof(C))};
+    Scal S;
+    const size_t ns = (size_t)nshift * ncol;
+    S.rho = (double2 *)take(ns * sizeof(double2));
+    S.alpha = (double2 *)take(ns * sizeof(double2));
+    S.beta = (double2 *)take(ns * sizeof(double2));
+    S.eta = (double *)take(ns * sizeof(double));
+    S.eta_ref = (double *)take(ns * sizeof(double));
+    S.bnorm2 = (double *)take(ns * sizeof(double));
+    S.flag = (int *)take(ns * sizeof(int));
+    S.shift_active = (int *)take(nshift * sizeof(int));
+    S.shift_refine = (int *)take(nshift * sizeof(int));
+    S.since_refine = (int *)take(nshift * sizeof(int));
+    S.partA = (double2 *)take((size_t)nshift * maxch * ncol * sizeof(double2));
+    S.partB = (double *)take((size_t)nshift * maxch * ncol * sizeof(double));
+    double2 *d_z = (double2 *)take(nshift * sizeof(double2));
+    int *d_rhs = (int *)take(nshift * sizeof(int));
+
+    int rc = GCIE_OK;
+    std::vector<double2> hz(nshift);
+    for (int s = 0; s < nshift; ++s) hz[s] = make_double2(h_z[2 * s], h_z[2 * s + 1]);
+    std::vector<int> hact(nshift, 1);
+    int64_t iters = 0, refines = 0;
+    const double delta2 = sizeof(T) == 4 ? 1e-8 : 0.0;   // refine after a 1e4 drop in FP32
+    const double tol2 = lin_tol * lin_tol;
+    const int max_since = sizeof(T) == 4 ? 4000 : 1 << 30;
+    const size_t smem = (size_t)256 * CPT * 3 * sizeof(double) + 64;
+    const size_t smem_r = (size_t)256 * 2 * 3 * sizeof(double) + 64;
+    const T *kv = sizeof(T) == 4 ? (const T *)p->k32 : (const T *)p->k64;
+    const T *mv = sizeof(T) == 4 ? (const T *)p->m32 : (const T *)p->m64;
+    const double esz = sizeof(C);
+    const double mat = (double)p->nnz * (4 + 2 * sizeof(T)) + 4.0 * (n + 1);
+    int active_shifts = nshift;
+
+    GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), nshift * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    GCIE_CUDA_TRY(cudaMemcpyAsync(d_rhs, h_rhs_of, nshift * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    GCIE_CUDA_TRY(cudaMemsetAsync(D, 0, blk * sizeof(C), c->stream));
+    GCIE_CUDA_TRY(cudaMemsetAsync(P[0], 0, blk * sizeof(C), c->stream));
+    if (!x0) GCIE_CUDA_TRY(cudaMemsetAsync(d_X, 0, blk * sizeof(double2), c->stream));
+    {
+        // partB is free before the first refinement; nrhs <= nshift so it has room for nrhs * chunks
+        int bch = (int)std::min<int64_t>(g.chunks, std::max<int64_t>(1, (n + 1023) / 1024));
+        int64_t brpc = (n + bch - 1) / bch;
+        LaunchScope ls(c, GCIE_K_OTHER, (double)nrhs * n * ncol * 8, 0);
+        k_bnorm_part<<<nrhs * bch, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(n, ncol, brpc, bch, d_B, S.partB);
+        GCIE_CUDA_TRY(cudaGetLastError());
+        k_bnorm_init<<<nshift, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, bch, d_rhs, S.partB, S);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    auto refine = [&](int nact) -> int {
+        {
+            LaunchScope ls(c, GCIE_K_REFINE, (double)nact * n * ncol * (2 * esz + 32), 0);
+            k_refine_x<T><<<ntiles, 256, 0, c->stream>>>(n, ncol, g.rows_per_chunk, g.chunks, S.shift_refine, D, d_X);
+            GCIE_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
+                           (double)nact * p->nnz * ncol * 8.0);
+            if (ncol % 2 == 0)
+                k_refine_r<T, 2><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64, p->m64, d_z,
+                    ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, R, S.partA, S.partB);
+            else
+                k_refine_r<T, 1><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64, p->m64, d_z,
+                    ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, R, S.partA, S.partB);
+            GCIE_CUDA_TRY(cudaGetLastError());
+        }
+        {
+            LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
+            k_scal_refine<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, gr.chunks, S, tol2);
+            GCIE_CUDA_TRY(cudaGetLastError());
+        }
+        return GCIE_OK;
+    };
+    rc = refine(nshift);
+    if (rc) goto done;
+    {
+        const int check_every = 8;
+        int it = 0;
+        while (true) {
+            GCIE_CUDA_TRY(cudaMemcpyAsync(hact.data(), S.shift_active, nshift * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+            GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+            active_shifts = 0;
+            for (int s = 0; s < nshift; ++s) active_shifts += hact[s] != 0;
+            if (active_shifts == 0 || it >= max_iters) break;
+            for (int k = 0; k < check_every && it < max_iters; ++k, ++it) {
+                C *Pold = P[it & 1], *Pnew = P[(it + 1) & 1];
+                {
+                    LaunchScope ls(c, GCIE_K_SPMM_DIR, (double)active_shifts * (n * ncol * 3 * esz + mat),
+                                   (double)active_shifts * p->nnz * ncol * 12.0);
+                    k_dir<T, CPT><<<ntiles, g.threads, smem, c->stream>>>(n, p->rowptr, p->col, kv, mv, d_z, ncol,
+                        g.rows_per_chunk, g.chunks, S.shift_active, S.beta, R, Pold, Pnew, S.partA);
+                    GCIE_CUDA_TRY(cudaGetLastError());
+                }
+                {
+                    LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
+                    k_scal_alpha<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, g.chunks, S);
+                    GCIE_CUDA_TRY(cudaGetLastError());
+                }
+                {
+                    LaunchScope ls(c, GCIE_K_SPMM_UPD, (double)active_shifts * (n * ncol * 5 * esz + mat),
+                                   (double)active_shifts * p->nnz * ncol * 8.0);
+                    k_upd<T, CPT><<<ntiles, g.threads, smem, c->stream>>>(n, p->rowptr, p->col, kv, mv, d_z, ncol,
+                        g.rows_per_chunk, g.chunks, S.shift_active, S.alpha, Pnew, D, R, S.partA, S.partB);
+                    GCIE_CUDA_TRY(cudaGetLastError());
+                }
+                {
+                    LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
+                    k_scal_beta<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, g.chunks, S,
+                        delta2, tol2, max_since);
+                    GCIE_CUDA_TRY(cudaGetLastError());
+                }
+                rc = refine(0);
+                if (rc) goto done;
+            }
+            iters = it;
+        }
+        iters = it;
+        // fold any remaining correction into x64 for columns that did not converge
+        if (active_shifts) {
+            GCIE_CUDA_TRY(cudaMemcpyAsync(S.shift_refine, S.shift_active, nshift * sizeof(int), cudaMemcpyDeviceToDevice,
+                                          c->stream));
+            rc = refine(active_shifts);
+            if (rc) goto done;
+        }
+        std::vector<int> hf(ns);
+        GCIE_CUDA_TRY(cudaMemcpyAsync(hf.data(), S.flag, ns * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+        GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        int unconv = 0;
+        for (size_t e = 0; e < ns; ++e) unconv += (hf[e] & F_ACTIVE) != 0;
+        if (info) {
+            info->iters += iters;
+            info->refines += refines;
+            info->unconverged_cols += unconv;
+        }
+        if (unconv) {
+            set_error("cocg: " + std::to_string(unconv) + " columns did not reach the tolerance");
+            rc = GCIE_ENOCONV;
+        }
+    }
+done:
+    cudaFreeAsync(base, c->stream);
+    return rc;
+}
+
+int cocg_solve(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
+               const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, int precision, SolveInfo *info)
+{
+    if (nshift <= 0) return GCIE_OK;
+    for (int s = 0; s < nshift; ++s)
+        if (h_rhs_of[s] < 0 || h_rhs_of[s] >= nrhs) { set_error("cocg: rhs index out of range"); return GCIE_EINVAL; }
+    if (precision == GCIE_FP64)
+        return solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, d_B, d_X, x0, lin_tol, max_iters, info);
+    return solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, d_B, d_X, x0, lin_tol, max_iters, info);
+}
+
+}  // namespace gcie

@@ -1,0 +1,105 @@
+// Shared definitions of the gcie CUDA library: context/pencil structures, complex helpers,
+// launch accounting.  Internal header (the public C ABI is include/gcie.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "gcie.h"
+
+namespace gcie {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+
+#define GCIE_CUDA_TRY(expr)                                                                   \
+    do {                                                                                      \
+        cudaError_t e_ = (expr);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            ::gcie::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+            return GCIE_ECUDA;                                                                \
+        }                                                                                     \
+    } while (0)
+
+#define GCIE_TRY(expr)                                                                        \
+    do {                                                                                      \
+        int s_ = (expr);                                                                      \
+        if (s_ != GCIE_OK) return s_;                                                         \
+    } while (0)
+
+// ------------------------------------------------------------------ device pencil
+struct Pencil {
+    gcie_ctx *ctx = nullptr;
+    int64_t n = 0, nnz = 0;          // union pattern
+    int bw = 0;                      // max |i - j| over stored entries
+    int *rowptr = nullptr;           // n+1 (int32: nnz < 2^31 enforced)
+    int *col = nullptr;              // nnz
+    float *k32 = nullptr, *m32 = nullptr;    // FP32 values of K and M on the union pattern
+    double *k64 = nullptr, *m64 = nullptr;   // FP64 values
+    double norm_k1 = 0.0;            // ||K||_1
+    // host copies (union pattern, symmetrised) for the host-side de-duplication
+    std::vector<int64_t> h_rowptr;
+    std::vector<int32_t> h_col;
+    std::vector<double> h_k, h_m;
+};
+
+// ------------------------------------------------------------------ context
+struct Ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    size_t smem_optin = 0;
+    gcie_stats stats{};
+    bool profile = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // device scratch reused across calls (grown on demand)
+    void *scratch = nullptr;
+    size_t scratch_bytes = 0;
+};
+
+// Launch bookkeeping: every kernel launch goes through `launch_begin/launch_end` so the stats
+// count launches, algorithmic bytes and (when profiling) event-timed durations per class.
+struct LaunchScope {
+    Ctx *c;
+    int cls;
+    double bytes, flops;
+    LaunchScope(Ctx *ctx, int klass, double b, double f);
+    ~LaunchScope();
+};
+
+// device scratch of at least `bytes` (reused; contents undefined)
+int ctx_scratch(Ctx *c, size_t bytes, void **out);
+
+// ------------------------------------------------------------------ complex helpers
+template <typename T> struct cplx;
+template <> struct cplx<float> { using t = float2; };
+template <> struct cplx<double> { using t = double2; };
+
+template <typename C> __host__ __device__ inline C cmk(double re, double im) { C c; c.x = re; c.y = im; return c; }
+__host__ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline double2 cmul(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__host__ __device__ inline float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__host__ __device__ inline float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__host__ __device__ inline double2 cdiv(double2 a, double2 b) {
+    // a / b with scaling by the larger component of b (Smith's algorithm)
+    if (fabs(b.x) >= fabs(b.y)) {
+        double r = b.y / b.x, d = b.x + b.y * r;
+        return make_double2((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        double r = b.x / b.y, d = b.x * r + b.y;
+        return make_double2((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
+
+// ------------------------------------------------------------------ launch geometry
+inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+}  // namespace gcie
+
+struct gcie_ctx : gcie::Ctx {};
+struct gcie_pencil : gcie::Pencil {};

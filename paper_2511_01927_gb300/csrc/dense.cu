@@ -1,0 +1,462 @@
+// Everything after the shifted solves, in FP64 on the device (steps a7-a11):
+//   moments      S_k = 2 Re sum_s w_s ((z_s - c)/r)^k X_s           (Appendix A.3.3, moment method)
+//   gram         G = Y^T W, tall-skinny (row chunks -> per-CTA partial p x p -> ordered sum)
+//   gemm_tall    Z = Y T with a small T held in shared memory
+//   jacobi       cyclic Jacobi, one CTA per matrix, round-robin (tournament) pair ordering so
+//                each round applies p/2 disjoint rotations in parallel
+//   m_orthonormalize, rayleigh_ritz   (Algorithm 1: Q <- orth(Y); Q^T A Q, Q^T B Q; reduced GEP;
+//                x <- Q u) and the residual ||K z - theta M z|| / (||K||_1 ||z||)
+#include <algorithm>
+#include <cmath>
+
+#include "kernels.cuh"
+
+namespace gcie {
+
+// ------------------------------------------------------------------ moments
+// S[i, k*ncol + l] += 2 Re( coef[s][k] * X[s][i][l] ), summed over the shifts s of one contour.
+__global__ void k_moments(int64_t n, int nshift, const double2 *__restrict__ coef, int m, int ncol,
+                          const double2 *__restrict__ X, double *__restrict__ S, int ldS)
+{
+    const int64_t total = n * ncol;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / ncol;
+        const int l = (int)(e % ncol);
+        double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int s = 0; s < nshift; ++s) {
+            const double2 x = X[(int64_t)s * total + e];
+            for (int k = 0; k < m; ++k) {
+                const double2 cf = coef[s * m + k];
+                acc[k] += 2.0 * (cf.x * x.x - cf.y * x.y);
+            }
+        }
+        for (int k = 0; k < m; ++k) S[i * ldS + (int64_t)k * ncol + l] += acc[k];
+    }
+}
+
+int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int ncol, const double2 *X, double *S, int ldS)
+{
+    if (m > 8 || m < 1) { set_error("moments: 1 <= m <= 8"); return GCIE_EINVAL; }
+    double2 *d_coef = nullptr;
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_coef, sizeof(double2) * nshift * m, c->stream));
+    cudaError_t e = cudaMemcpyAsync(d_coef, h_coef, sizeof(double2) * nshift * m, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) {
+        LaunchScope ls(c, GCIE_K_MOMENT, (double)n * ncol * (16.0 * nshift + 16.0 * m), 4.0 * n * ncol * nshift * m);
+        int64_t blocks = std::min<int64_t>((n * ncol + 255) / 256, (int64_t)c->num_sms * 32);
+        k_moments<<<(int)std::max<int64_t>(1, blocks), 256, 0, c->stream>>>(n, nshift, d_coef, m, ncol, X, S, ldS);
+        e = cudaGetLastError();
+    }
+    cudaFreeAsync(d_coef, c->stream);
+    if (e != cudaSuccess) { set_error(std::string("moments: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ Gram
+// Per-CTA partial G_c = sum_{i in chunk c} Y[i,:]^T W[i,:].  Thread (ta, tb) owns the 8 x 8 tile
+// rows 8ta.., cols 8tb..; rows of Y and W are staged through shared memory in batches of RB.
+constexpr int GRAM_RB = 16;
+__global__ void k_gram_part(int64_t n, int p, int pp, int64_t rows_per_chunk, const double *__restrict__ Y,
+                            const double *__restrict__ W, double *__restrict__ part)
+{
+    extern __shared__ double sm[];
+    double *sY = sm;                   // [RB][pp]
+    double *sW = sm + GRAM_RB * pp;    // [RB][pp]
+    const int nt = pp / 8;
+    const int ta = threadIdx.x / nt, tb = threadIdx.x % nt;
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    double acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0;
+    for (int64_t i0 = r0; i0 < r1; i0 += GRAM_RB) {
+        const int rb = (int)min((int64_t)GRAM_RB, r1 - i0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < GRAM_RB * pp; e += blockDim.x) {
+            const int r = e / pp, k = e % pp;
+            const bool ok = r < rb && k < p;
+            sY[e] = ok ? Y[(i0 + r) * p + k] : 0.0;
+            sW[e] = ok ? W[(i0 + r) * p + k] : 0.0;
+        }
+        __syncthreads();
+        for (int r = 0; r < rb; ++r) {
+            double ya[8], wb[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) ya[a] = sY[r * pp + 8 * ta + a];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) wb[b] = sW[r * pp + 8 * tb + b];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fma(ya[a], wb[b], acc[a][b]);
+        }
+    }
+    double *out = part + (int64_t)blockIdx.x * pp * pp;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) out[(8 * ta + a) * pp + 8 * tb + b] = acc[a][b];
+}
+
+__global__ void k_gram_sum(int nchunk, int p, int pp, const double *__restrict__ part, double *__restrict__ G)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
+        const int a = e / p, b = e % p;
+        double s = 0.0;
+        for (int cidx = 0; cidx < nchunk; ++cidx) s += part[(int64_t)cidx * pp * pp + a * pp + b];
+        G[e] = s;
+    }
+}
+
+int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G)
+{
+    if (p <= 0) return GCIE_OK;
+    if (p > 256) { set_error("gram: p > 256"); return GCIE_EINVAL; }
+    const int pp = ((p + 7) / 8) * 8;
+    const int threads = (pp / 8) * (pp / 8);
+    int nchunk = (int)std::min<int64_t>((int64_t)c->num_sms * (threads <= 256 ? 4 : 1), (n + 63) / 64);
+    nchunk = std::max(nchunk, 1);
+    const int64_t rpc = (n + nchunk - 1) / nchunk;
+    nchunk = (int)((n + rpc - 1) / rpc);
+    double *part = nullptr;
+    GCIE_TRY(ctx_scratch(c, sizeof(double) * (size_t)nchunk * pp * pp, (void **)&part));
+    const size_t smem = sizeof(double) * 2 * GRAM_RB * pp;
+    {
+        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * n * p, 2.0 * n * p * p);
+        k_gram_part<<<nchunk, std::max(threads, 32), smem, c->stream>>>(n, p, pp, rpc, Y, W, part);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        LaunchScope ls(c, GCIE_K_DENSE, 8.0 * nchunk * pp * pp, 0);
+        k_gram_sum<<<std::max(1, (p * p + 255) / 256), 256, 0, c->stream>>>(nchunk, p, pp, part, G);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ Z = Y T
+// CTA handles rows [r0, r1) and output columns [q0, q0 + QB); T[:, q0:q0+QB] in shared memory.
+__global__ void k_gemm_tall(int64_t n, int p, int q, int QB, int64_t rows_per_chunk, const double *__restrict__ Y,
+                            int ldY, const double *__restrict__ T, double *__restrict__ Z, int ldZ)
+{
+    extern __shared__ double sT[];   // [p][QB]
+    const int q0 = blockIdx.y * QB;
+    const int qb = min(QB, q - q0);
+    for (int e = threadIdx.x; e < p * QB; e += blockDim.x) {
+        const int k = e / QB, j = e % QB;
+        sT[e] = j < qb ? T[(int64_t)k * q + q0 + j] : 0.0;
+    }
+    __syncthreads();
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    const int j = threadIdx.x % QB, rsub = threadIdx.x / QB, rpb = blockDim.x / QB;
+    if (rsub >= rpb || j >= qb) return;
+    for (int64_t i = r0 + rsub; i < r1; i += rpb) {
+        const double *y = Y + i * ldY;
+        double acc = 0.0;
+        for (int k = 0; k < p; ++k) acc = fma(__ldg(y + k), sT[k * QB + j], acc);
+        Z[i * ldZ + q0 + j] = acc;
+    }
+}
+
+int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const double *T, double *Z, int ldZ)
+{
+    if (q <= 0 || n <= 0) return GCIE_OK;
+    const int QB = std::min(q, 64);
+    const int threads = std::max(QB, (256 / QB) * QB);
+    const int qblocks = (q + QB - 1) / QB;
+    int64_t nchunk = std::min<int64_t>(((int64_t)c->num_sms * 8 + qblocks - 1) / qblocks, (n + 31) / 32);
+    nchunk = std::max<int64_t>(nchunk, 1);
+    const int64_t rpc = (n + nchunk - 1) / nchunk;
+    nchunk = (n + rpc - 1) / rpc;
+    const size_t smem = sizeof(double) * (size_t)p * QB;
+    if (smem > c->smem_optin) { set_error("gemm_tall: p too large"); return GCIE_EINVAL; }
+    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tall, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope ls(c, GCIE_K_DENSE, 8.0 * n * (p + q), 2.0 * n * p * q);
+    k_gemm_tall<<<dim3((unsigned)nchunk, qblocks), threads, smem, c->stream>>>(n, p, q, QB, rpc, Y, ldY, T, Z, ldZ);
+    GCIE_CUDA_TRY(cudaGetLastError());
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ Jacobi
+// Two-sided cyclic Jacobi on a symmetric p x p matrix (row-major, in global memory, one CTA per
+// matrix).  A sweep is p' - 1 rounds (p' = p rounded up to even); round r pairs position k with
+// position p'-1-k where position 0 holds index 0 and position m >= 1 holds 1 + (m - 1 + r) mod
+// (p' - 1), so every pair (q, r) meets once per sweep.  For each pair the rotation
+// J = [[c, s], [-s, c]] in the (q, r) plane with t = sgn(tau) / (|tau| + sqrt(1 + tau^2)),
+// tau = (a_rr - a_qq) / (2 a_qr), c = 1/sqrt(1 + t^2), s = t c zeroes a_qr in J^T A J.  The
+// p'/2 rotations of a round touch disjoint rows/columns and are applied together: columns
+// (A <- A J, V <- V J), then rows (A <- J^T A).  Stops when the off-diagonal Frobenius norm is
+// at most tol * ||A||_F.  Output: ascending eigenvalues w and eigenvectors as columns of V.
+__global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aall, double *__restrict__ wall,
+                                                 double *__restrict__ Vall, double *__restrict__ Wk, double tol,
+                                                 int maxsweep)
+{
+    double *A = Aall + (int64_t)blockIdx.x * p * p;
+    double *Vo = Vall + (int64_t)blockIdx.x * p * p;
+    double *V = Wk + (int64_t)blockIdx.x * p * p;       // unsorted eigenvectors
+    double *w = wall + (int64_t)blockIdx.x * p;
+    const int pe = p + (p & 1), half = pe / 2;
+    __shared__ double cs[512], sn[512];
+    __shared__ int qi[512], ri[512];
+    __shared__ double red[32];
+    __shared__ double fro2, off2;
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int e = tid; e < p * p; e += nth) V[e] = (e / p == e % p) ? 1.0 : 0.0;
+    // ||A||_F^2
+    auto block_sum = [&](double v) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        __syncthreads();
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        double s = 0.0;
+        if (tid < 32) {
+            s = tid < (nth + 31) / 32 ? red[tid] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        }
+        return s;   // valid in thread 0
+    };
+    double loc = 0.0;
+    for (int e = tid; e < p * p; e += nth) loc += A[e] * A[e];
+    double f = block_sum(loc);
+    if (tid == 0) fro2 = f;
+    __syncthreads();
+    for (int sweep = 0; sweep <= maxsweep; ++sweep) {
+        loc = 0.0;
+        for (int e = tid; e < p * p; e += nth)
+            if (e / p != e % p) loc += A[e] * A[e];
+        double o = block_sum(loc);
+        if (tid == 0) off2 = o;
+        __syncthreads();
+        if (off2 <= tol * tol * fro2 || fro2 == 0.0 || sweep == maxsweep) break;
+        for (int round = 0; round < pe - 1; ++round) {
+            for (int k = tid; k < half; k += nth) {
+                auto who = [&](int pos) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (pe - 1); };
+                int a = who(k), b = who(pe - 1 - k);
+                int q = min(a, b), r = max(a, b);
+                double c = 1.0, s = 0.0;
+                if (r < p) {
+                    const double aqr = A[q * p + r];
+                    if (aqr != 0.0) {
+                        const double tau = (A[r * p + r] - A[q * p + q]) / (2.0 * aqr);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                qi[k] = q; ri[k] = r < p ? r : -1; cs[k] = c; sn[k] = s;
+            }
+            __syncthreads();
+            // A <- A J and V <- V J (column pairs)
+            for (int e = tid; e < p * half; e += nth) {
+                const int i = e / half, k = e % half;
+                const int r = ri[k];
+                if (r < 0 || sn[k] == 0.0) continue;
+                const int q = qi[k];
+                const double c = cs[k], s = sn[k];
+                double aq = A[i * p + q], ar = A[i * p + r];
+                A[i * p + q] = c * aq - s * ar;
+                A[i * p + r] = s * aq + c * ar;
+                double vq = V[i * p + q], vr = V[i * p + r];
+                V[i * p + q] = c * vq - s * vr;
+                V[i * p + r] = s * vq + c * vr;
+            }
+            __syncthreads();
+            // A <- J^T A (row pairs)
+            for (int e = tid; e < p * half; e += nth) {
+                const int k = e / p, j = e % p;
+                const int r = ri[k];
+                if (r < 0 || sn[k] == 0.0) continue;
+                const int q = qi[k];
+                const double c = cs[k], s = sn[k];
+                double aq = A[q * p + j], ar = A[r * p + j];
+                A[q * p + j] = c * aq - s * ar;
+                A[r * p + j] = s * aq + c * ar;
+            }
+            __syncthreads();
+            for (int k = tid; k < half; k += nth) {
+                const int r = ri[k];
+                if (r >= 0 && sn[k] != 0.0) { A[qi[k] * p + r] = 0.0; A[r * p + qi[k]] = 0.0; }
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    // sort ascending (stable rank), permute eigenvector columns
+    for (int i = tid; i < p; i += nth) {
+        const double di = A[i * p + i];
+        int rank = 0;
+        for (int j = 0; j < p; ++j) {
+            const double dj = A[j * p + j];
+            rank += (dj < di) || (dj == di && j < i);
+        }
+        w[rank] = di;
+        for (int r = 0; r < p; ++r) Vo[r * p + rank] = V[r * p + i];
+    }
+}
+
+int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
+{
+    if (nmat <= 0 || p <= 0) return GCIE_OK;
+    if (p > 1024) { set_error("jacobi: p > 1024"); return GCIE_EINVAL; }
+    double *wk = nullptr;
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&wk, sizeof(double) * (size_t)nmat * p * p, c->stream));
+    LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
+    k_jacobi<<<nmat, 1024, 0, c->stream>>>(p, A, w, V, wk, 1e-15, 60);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(wk, c->stream);
+    if (e != cudaSuccess) { set_error(std::string("jacobi: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ residual norms
+// part[c][l] = sum over the chunk's rows of (KZ - theta_l MZ)^2, part2[c][l] = sum Z^2.
+__global__ void k_resid_part(int64_t n, int q, int64_t rows_per_chunk, const double *__restrict__ KZ,
+                             const double *__restrict__ MZ, const double *__restrict__ Z,
+                             const double *__restrict__ theta, double *__restrict__ part)
+{
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    for (int l = threadIdx.x; l < q; l += blockDim.x) {
+        const double th = theta[l];
+        double a = 0.0, b = 0.0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const double r = KZ[i * q + l] - th * MZ[i * q + l];
+            const double zz = Z[i * q + l];
+            a = fma(r, r, a);
+            b = fma(zz, zz, b);
+        }
+        part[((int64_t)blockIdx.x * 2 + 0) * q + l] = a;
+        part[((int64_t)blockIdx.x * 2 + 1) * q + l] = b;
+    }
+}
+
+__global__ void k_resid_sum(int nchunk, int q, const double *__restrict__ part, double *__restrict__ r2,
+                            double *__restrict__ z2)
+{
+    for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < q; l += gridDim.x * blockDim.x) {
+        double a = 0.0, b = 0.0;
+        for (int cidx = 0; cidx < nchunk; ++cidx) {
+            a += part[((int64_t)cidx * 2 + 0) * q + l];
+            b += part[((int64_t)cidx * 2 + 1) * q + l];
+        }
+        r2[l] = a;
+        z2[l] = b;
+    }
+}
+
+int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, const double *Z, const double *d_theta,
+                double *d_r2, double *d_z2)
+{
+    if (q <= 0) return GCIE_OK;
+    int nchunk = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->num_sms * 4, (n + 255) / 256));
+    const int64_t rpc = (n + nchunk - 1) / nchunk;
+    nchunk = (int)((n + rpc - 1) / rpc);
+    double *part = nullptr;
+    GCIE_TRY(ctx_scratch(c, sizeof(double) * (size_t)nchunk * 2 * q, (void **)&part));
+    {
+        LaunchScope ls(c, GCIE_K_DENSE, 24.0 * n * q, 6.0 * n * q);
+        k_resid_part<<<nchunk, std::min(1024, ((q + 31) / 32) * 32), 0, c->stream>>>(n, q, rpc, KZ, MZ, Z, d_theta, part);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    {
+        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * nchunk * q, 0);
+        k_resid_sum<<<(q + 255) / 256, 256, 0, c->stream>>>(nchunk, q, part, d_r2, d_z2);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ basis and Rayleigh-Ritz
+// T[:, j] = U[:, idx_j] / sqrt(s[idx_j]) for the kept eigenpairs (largest first).
+__global__ void k_scale_cols(int p, int k, const double *__restrict__ U, const double *__restrict__ s,
+                             double *__restrict__ T)
+{
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * k; e += gridDim.x * blockDim.x) {
+        const int r = e / k, j = e % k;
+        const int src = p - 1 - j;   // ascending order from Jacobi: largest last
+        T[e] = U[r * p + src] / sqrt(s[src]);
+    }
+}
+
+// One pass: Q = Y U_k diag(s_k)^-1/2 where G = Y^T M Y = U diag(s) U^T and s_i > drop * max s.
+static int orth_pass(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q, int *rank,
+                     double *work)
+{
+    double *W = work;                            // n x ncol (M Y)
+    double *G = W + (size_t)n * ncol;            // ncol^2
+    double *U = G + (size_t)ncol * ncol;         // ncol^2
+    double *s = U + (size_t)ncol * ncol;         // ncol
+    double *T = s + ncol;                        // ncol^2
+    GCIE_TRY(spmm_real(c, p, 1, ncol, Y, W));
+    GCIE_TRY(gram(c, n, ncol, Y, W, G));
+    GCIE_TRY(jacobi(c, 1, ncol, G, s, U));
+    std::vector<double> hs(ncol);
+    GCIE_CUDA_TRY(cudaMemcpyAsync(hs.data(), s, sizeof(double) * ncol, cudaMemcpyDeviceToHost, c->stream));
+    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    const double smax = hs[ncol - 1];
+    int k = 0;
+    if (smax > 0 && std::isfinite(smax))
+        for (int i = ncol - 1; i >= 0; --i)
+            if (hs[i] > drop * smax) ++k;
+    *rank = k;
+    if (k == 0) { set_error("m_orthonormalize: basis has rank 0"); return GCIE_ENOTSPD; }
+    {
+        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * ncol * k, 0);
+        k_scale_cols<<<std::max(1, (ncol * k + 255) / 256), 256, 0, c->stream>>>(ncol, k, U, s, T);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    GCIE_CUDA_TRY(cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * ncol, c->stream));
+    return gemm_tall(c, n, ncol, k, Y, ncol, T, Q, ncol);
+}
+
+int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q, int *rank)
+{
+    double *work = nullptr, *Q1 = nullptr;
+    const size_t wbytes = sizeof(double) * ((size_t)n * ncol + 3 * (size_t)ncol * ncol + ncol);
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&work, wbytes, c->stream));
+    cudaError_t e = cudaMallocAsync((void **)&Q1, sizeof(double) * (size_t)n * ncol, c->stream);
+    if (e != cudaSuccess) { cudaFreeAsync(work, c->stream); set_error("m_orthonormalize: out of memory"); return GCIE_ENOMEM; }
+    int r1 = 0, r2 = 0;
+    int rc = orth_pass(c, p, n, ncol, Y, drop, Q1, &r1, work);
+    // second pass on the r1 valid columns (zero columns beyond r1 are dropped by the rank test)
+    if (rc == GCIE_OK) rc = orth_pass(c, p, n, ncol, Q1, drop, Q, &r2, work);
+    cudaFreeAsync(work, c->stream);
+    cudaFreeAsync(Q1, c->stream);
+    *rank = r2;
+    return rc;
+}
+
+int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, double *h_theta, double *h_res)
+{
+    const int64_t n = p->n;
+    double *work = nullptr;
+    const size_t wbytes = sizeof(double) * (2 * (size_t)n * q + 2 * (size_t)q * q + 3 * (size_t)q);
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&work, wbytes, c->stream));
+    double *KQ = work;                        // n x q, later K Z
+    double *MZ = KQ + (size_t)n * q;          // n x q
+    double *Kh = MZ + (size_t)n * q;          // q x q
+    double *U = Kh + (size_t)q * q;           // q x q
+    double *th = U + (size_t)q * q;           // q
+    double *r2 = th + q, *z2 = r2 + q;
+    int rc = GCIE_OK;
+    std::vector<double> hr2(q), hz2(q);
+    do {
+        if ((rc = spmm_real(c, p, 0, q, Q, KQ))) break;
+        if ((rc = gram(c, n, q, Q, KQ, Kh))) break;
+        if ((rc = jacobi(c, 1, q, Kh, th, U))) break;
+        if ((rc = gemm_tall(c, n, q, q, Q, q, U, Z, q))) break;
+        if ((rc = spmm_real(c, p, 0, q, Z, KQ))) break;
+        if ((rc = spmm_real(c, p, 1, q, Z, MZ))) break;
+        if ((rc = resid_norms(c, n, q, KQ, MZ, Z, th, r2, z2))) break;
+        cudaMemcpyAsync(h_theta, th, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hr2.data(), r2, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
+        cudaMemcpyAsync(hz2.data(), z2, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { set_error(std::string("rayleigh_ritz: ") + cudaGetErrorString(e)); rc = GCIE_ECUDA; break; }
+        for (int l = 0; l < q; ++l)
+            h_res[l] = hz2[l] > 0 ? std::sqrt(hr2[l]) / (p->norm_k1 * std::sqrt(hz2[l])) : INFINITY;
+    } while (0);
+    cudaFreeAsync(work, c->stream);
+    return rc;
+}
+
+}  // namespace gcie

@@ -1,0 +1,57 @@
+// Internal kernel entry points of the gcie library (host-side launchers).
+#pragma once
+
+#include "common.cuh"
+
+namespace gcie {
+
+// Launch geometry for the row-tiled block kernels: each CTA owns a contiguous row range of one
+// shift (node); `tpr` threads cover one row of ncol columns (cpt complex values per thread) and a
+// CTA holds `rpb` rows at a time.
+struct Geo {
+    int tpr, rpb, threads, chunks;
+    int64_t rows_per_chunk;
+};
+Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt);
+
+// a4: Q[s] = z_s M P[s] - K P[s] for s < nshift (FP32 or FP64 complex blocks, n x ncol row-major).
+int shifted_spmm_f32(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, int ncol, const float2 *P, float2 *Q);
+int shifted_spmm_f64(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, int ncol, const double2 *P, double2 *Q);
+
+// Y = A X with A = K (which = 0) or M (which = 1), FP64 real, X and Y n x q row-major.
+int spmm_real(Ctx *c, const Pencil *p, int which, int q, const double *X, double *Y);
+
+// a4-a6: batched shifted solves.  Shift s solves (z_s M - K) X[s] = B[rhs_of[s]] (B: nrhs blocks of
+// n x ncol real FP64; X: nshift blocks of n x ncol complex FP64).
+struct SolveInfo {
+    int64_t iters = 0;
+    int64_t refines = 0;
+    int unconverged_cols = 0;
+    int breakdowns = 0;
+};
+int cocg_solve(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs,
+               int ncol, const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters,
+               int precision, SolveInfo *info);
+
+// a7: S[:, k*ncol + l] += 2 Re( coef[s][k] X[s][:, l] ), coef[s][k] = w_s ((z_s - c)/r)^k, summed over
+// s < nshift; S is n x (m*ncol) row-major (leading dimension ldS >= m*ncol).
+int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int ncol, const double2 *X, double *S,
+            int ldS);
+
+// G = Y^T W (p x p), Y and W n x p row-major FP64 (p <= 256).
+int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G);
+// Z = Y T, Y n x p (leading dim ldY), T p x q row-major, Z n x q (leading dim ldZ).
+int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const double *T, double *Z, int ldZ);
+// Batched cyclic Jacobi: nmat symmetric p x p matrices (A destroyed), ascending w, V columns.
+int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V);
+// Column sums over rows: out[l] = sum_i (KZ_il - theta_l MZ_il)^2 and out2[l] = sum_i Z_il^2.
+int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, const double *Z,
+                const double *d_theta, double *d_r2, double *d_z2);
+
+// a8: two-pass M-orthonormalisation; Q has *rank valid columns (row-major n x ldQ).
+int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q,
+                     int *rank);
+// a9-a11 for one basis: theta (host, ascending), residuals (host), Z = Q W on device (n x q).
+int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, double *h_theta, double *h_res);
+
+}  // namespace gcie
