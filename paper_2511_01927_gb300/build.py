@@ -49,6 +49,13 @@ def _compile(src: str, extra=()) -> str:
 def build(verbose: bool = False, extra=()) -> str:
     """Compile every CUDA source for sm_103a and link libgcie.so; returns its path."""
     os.makedirs(OBJ, exist_ok=True)
+    stamp = os.path.join(OBJ, "flags.txt")
+    want = " ".join(_flags(extra))
+    if not os.path.exists(stamp) or open(stamp).read() != want:
+        for o in glob.glob(os.path.join(OBJ, "*.o")):
+            os.remove(o)
+        with open(stamp, "w") as fh:
+            fh.write(want)
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))

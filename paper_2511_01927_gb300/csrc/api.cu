@@ -52,6 +52,19 @@ LaunchScope::LaunchScope(Ctx *ctx, int klass, double b, double f) : c(ctx), cls(
 
 LaunchScope::~LaunchScope()
 {
+#ifdef GCIE_CHECKED
+    {
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        DbgRec h{};
+        cudaMemcpy(&h, c->dbg, sizeof(h), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess || h.count) {
+            fprintf(stderr, "GCIE_CHECKED class %d: %s; violations %llu first tag %lld idx %lld bound %lld\n", cls,
+                    cudaGetErrorString(e), h.count, h.tag, h.idx, h.bound);
+            DbgRec z{};
+            cudaMemcpy(c->dbg, &z, sizeof(z), cudaMemcpyHostToDevice);
+        }
+    }
+#endif
     c->stats.launches[cls] += 1;
     c->stats.bytes[cls] += bytes;
     c->stats.flops[cls] += flops;
@@ -213,6 +226,11 @@ int gcie_create(gcie_ctx **out, int device, void *stream)
     cudaGetDeviceProperties(&prop, device);
     c->num_sms = prop.multiProcessorCount;
     c->smem_optin = prop.sharedMemPerBlockOptin;
+    if (cudaMalloc(&c->dbg, sizeof(DbgRec)) != cudaSuccess || cudaMemset(c->dbg, 0, sizeof(DbgRec)) != cudaSuccess) {
+        delete c;
+        set_error("gcie_create: allocation failed");
+        return GCIE_ECUDA;
+    }
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -234,6 +252,7 @@ void gcie_destroy(gcie_ctx *c)
     cudaStreamSynchronize(c->stream);
     flush_timing(c);
     if (c->scratch) cudaFree(c->scratch);
+    if (c->dbg) cudaFree(c->dbg);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -522,13 +541,16 @@ __global__ void k_gather_cols(int64_t n, int q, int k, const int *__restrict__ i
 
 // copy columns [0, k) of a row-major n x ld block into a row-major n x k block; padding columns
 // [k, kpad) are zeroed
-__global__ void k_copy_cols(int64_t n, int ld, int k, int kpad, const double *__restrict__ A, double *__restrict__ B)
+__global__ void k_copy_cols(int64_t n, int ld, int k, int kpad, const double *__restrict__ A, double *__restrict__ B,
+                            DbgRec *dbg)
 {
     const int64_t total = n * kpad;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
         const int l = (int)(e % kpad);
         const int64_t i = e / kpad;
-        B[e] = l < k ? A[i * ld + l] : 0.0;
+        double v = 0.0;
+        if (l < k && GCHK(dbg, i * ld + l, n * ld, 901)) v = A[i * ld + l];
+        B[e] = v;
     }
 }
 
@@ -666,7 +688,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     ContourState &s = cs[act[b0 + bi]];
                     {
                         LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * ncol, 0);
-                        k_copy_cols<<<grid_for(c, n * ncol), 256, 0, c->stream>>>(n, s.q, s.q, ncol, s.Z, tmp);
+                        k_copy_cols<<<grid_for(c, n * ncol), 256, 0, c->stream>>>(n, s.q, s.q, ncol, s.Z, tmp, c->dbg);
                         GCIE_CUDA_TRY(cudaGetLastError());
                     }
                     GCIE_TRY(spmm_real(c, p, 1, ncol, tmp, dBb + (size_t)bi * n * ncol));
@@ -723,7 +745,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 GCIE_CUDA_TRY(cudaMalloc(&Z, sizeof(double) * (size_t)n * rank));
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
-                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pY, rank, rank, Q, Qc);
+                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pY, rank, rank, Q, Qc, c->dbg);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 std::vector<double> th(rank), rs(rank);

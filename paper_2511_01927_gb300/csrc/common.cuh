@@ -29,6 +29,26 @@ void set_error(const std::string &msg);
         if (s_ != GCIE_OK) return s_;                                                         \
     } while (0)
 
+// ------------------------------------------------------------------ checked builds
+// Built with -DGCIE_CHECKED, the kernels of the dense path test every global index against the
+// size of its array; a violation is recorded (first one kept) and the access skipped, and the
+// launch wrapper reports it after a stream sync.  Production builds compile the checks away.
+struct DbgRec {
+    unsigned long long count;
+    long long tag, idx, bound;
+};
+#ifdef GCIE_CHECKED
+__device__ __forceinline__ bool gchk(DbgRec *d, long long idx, long long bound, int tag)
+{
+    if (idx >= 0 && idx < bound) return true;
+    if (atomicAdd(&d->count, 1ull) == 0ull) { d->tag = tag; d->idx = idx; d->bound = bound; }
+    return false;
+}
+#define GCHK(d, idx, bound, tag) ::gcie::gchk((d), (long long)(idx), (long long)(bound), (tag))
+#else
+#define GCHK(d, idx, bound, tag) true
+#endif
+
 // ------------------------------------------------------------------ device pencil
 struct Pencil {
     gcie_ctx *ctx = nullptr;
@@ -58,6 +78,7 @@ struct Ctx {
     // device scratch reused across calls (grown on demand)
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
+    DbgRec *dbg = nullptr;           // device record of the first index violation (checked builds)
 };
 
 // Launch bookkeeping: every kernel launch goes through `launch_begin/launch_end` so the stats

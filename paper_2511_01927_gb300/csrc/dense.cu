@@ -16,7 +16,7 @@ namespace gcie {
 // ------------------------------------------------------------------ moments
 // S[i, k*ncol + l] += 2 Re( coef[s][k] * X[s][i][l] ), summed over the shifts s of one contour.
 __global__ void k_moments(int64_t n, int nshift, const double2 *__restrict__ coef, int m, int ncol,
-                          const double2 *__restrict__ X, double *__restrict__ S, int ldS)
+                          const double2 *__restrict__ X, double *__restrict__ S, int ldS, DbgRec *dbg)
 {
     const int64_t total = n * ncol;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
@@ -24,13 +24,16 @@ __global__ void k_moments(int64_t n, int nshift, const double2 *__restrict__ coe
         const int l = (int)(e % ncol);
         double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
         for (int s = 0; s < nshift; ++s) {
+            if (!GCHK(dbg, (int64_t)s * total + e, (int64_t)nshift * total, 382)) continue;
             const double2 x = X[(int64_t)s * total + e];
             for (int k = 0; k < m; ++k) {
+                if (!GCHK(dbg, s * m + k, nshift * m, 381)) continue;
                 const double2 cf = coef[s * m + k];
                 acc[k] += 2.0 * (cf.x * x.x - cf.y * x.y);
             }
         }
-        for (int k = 0; k < m; ++k) S[i * ldS + (int64_t)k * ncol + l] += acc[k];
+        for (int k = 0; k < m; ++k)
+            if (GCHK(dbg, i * ldS + (int64_t)k * ncol + l, n * ldS, 383)) S[i * ldS + (int64_t)k * ncol + l] += acc[k];
     }
 }
 
@@ -43,7 +46,7 @@ int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int nco
     if (e == cudaSuccess) {
         LaunchScope ls(c, GCIE_K_MOMENT, (double)n * ncol * (16.0 * nshift + 16.0 * m), 4.0 * n * ncol * nshift * m);
         int64_t blocks = std::min<int64_t>((n * ncol + 255) / 256, (int64_t)c->num_sms * 32);
-        k_moments<<<(int)std::max<int64_t>(1, blocks), 256, 0, c->stream>>>(n, nshift, d_coef, m, ncol, X, S, ldS);
+        k_moments<<<(int)std::max<int64_t>(1, blocks), 256, 0, c->stream>>>(n, nshift, d_coef, m, ncol, X, S, ldS, c->dbg);
         e = cudaGetLastError();
     }
     cudaFreeAsync(d_coef, c->stream);
@@ -56,13 +59,14 @@ int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int nco
 // rows 8ta.., cols 8tb..; rows of Y and W are staged through shared memory in batches of RB.
 constexpr int GRAM_RB = 16;
 __global__ void k_gram_part(int64_t n, int p, int pp, int64_t rows_per_chunk, const double *__restrict__ Y,
-                            const double *__restrict__ W, double *__restrict__ part)
+                            const double *__restrict__ W, double *__restrict__ part, int nchunk, DbgRec *dbg)
 {
     extern __shared__ double sm[];
     double *sY = sm;                   // [RB][pp]
     double *sW = sm + GRAM_RB * pp;    // [RB][pp]
     const int nt = pp / 8;
-    const int ta = threadIdx.x / nt, tb = threadIdx.x % nt;
+    const bool valid = threadIdx.x < nt * nt;   // the block may be padded to a full warp
+    const int ta = valid ? threadIdx.x / nt : 0, tb = threadIdx.x % nt;
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
     double acc[8][8];
 #pragma unroll
@@ -75,8 +79,9 @@ __global__ void k_gram_part(int64_t n, int p, int pp, int64_t rows_per_chunk, co
         for (int e = threadIdx.x; e < GRAM_RB * pp; e += blockDim.x) {
             const int r = e / pp, k = e % pp;
             const bool ok = r < rb && k < p;
-            sY[e] = ok ? Y[(i0 + r) * p + k] : 0.0;
-            sW[e] = ok ? W[(i0 + r) * p + k] : 0.0;
+            const int64_t gi = (i0 + r) * p + k;
+            sY[e] = (ok && GCHK(dbg, gi, n * p, 301)) ? Y[gi] : 0.0;
+            sW[e] = (ok && GCHK(dbg, gi, n * p, 302)) ? W[gi] : 0.0;
         }
         __syncthreads();
         for (int r = 0; r < rb; ++r) {
@@ -91,19 +96,25 @@ __global__ void k_gram_part(int64_t n, int p, int pp, int64_t rows_per_chunk, co
                 for (int b = 0; b < 8; ++b) acc[a][b] = fma(ya[a], wb[b], acc[a][b]);
         }
     }
+    if (!valid) return;
     double *out = part + (int64_t)blockIdx.x * pp * pp;
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) out[(8 * ta + a) * pp + 8 * tb + b] = acc[a][b];
+        for (int b = 0; b < 8; ++b)
+            if (GCHK(dbg, (int64_t)blockIdx.x * pp * pp + (8 * ta + a) * pp + 8 * tb + b, (int64_t)nchunk * pp * pp, 303))
+                out[(8 * ta + a) * pp + 8 * tb + b] = acc[a][b];
 }
 
-__global__ void k_gram_sum(int nchunk, int p, int pp, const double *__restrict__ part, double *__restrict__ G)
+__global__ void k_gram_sum(int nchunk, int p, int pp, const double *__restrict__ part, double *__restrict__ G,
+                           DbgRec *dbg)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
         const int a = e / p, b = e % p;
         double s = 0.0;
-        for (int cidx = 0; cidx < nchunk; ++cidx) s += part[(int64_t)cidx * pp * pp + a * pp + b];
+        for (int cidx = 0; cidx < nchunk; ++cidx)
+            if (GCHK(dbg, (int64_t)cidx * pp * pp + a * pp + b, (int64_t)nchunk * pp * pp, 311))
+                s += part[(int64_t)cidx * pp * pp + a * pp + b];
         G[e] = s;
     }
 }
@@ -123,12 +134,12 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G)
     const size_t smem = sizeof(double) * 2 * GRAM_RB * pp;
     {
         LaunchScope ls(c, GCIE_K_DENSE, 16.0 * n * p, 2.0 * n * p * p);
-        k_gram_part<<<nchunk, std::max(threads, 32), smem, c->stream>>>(n, p, pp, rpc, Y, W, part);
+        k_gram_part<<<nchunk, std::max(threads, 32), smem, c->stream>>>(n, p, pp, rpc, Y, W, part, nchunk, c->dbg);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     {
         LaunchScope ls(c, GCIE_K_DENSE, 8.0 * nchunk * pp * pp, 0);
-        k_gram_sum<<<std::max(1, (p * p + 255) / 256), 256, 0, c->stream>>>(nchunk, p, pp, part, G);
+        k_gram_sum<<<std::max(1, (p * p + 255) / 256), 256, 0, c->stream>>>(nchunk, p, pp, part, G, c->dbg);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     return GCIE_OK;
@@ -137,14 +148,14 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G)
 // ------------------------------------------------------------------ Z = Y T
 // CTA handles rows [r0, r1) and output columns [q0, q0 + QB); T[:, q0:q0+QB] in shared memory.
 __global__ void k_gemm_tall(int64_t n, int p, int q, int QB, int64_t rows_per_chunk, const double *__restrict__ Y,
-                            int ldY, const double *__restrict__ T, double *__restrict__ Z, int ldZ)
+                            int ldY, const double *__restrict__ T, double *__restrict__ Z, int ldZ, DbgRec *dbg)
 {
     extern __shared__ double sT[];   // [p][QB]
     const int q0 = blockIdx.y * QB;
     const int qb = min(QB, q - q0);
     for (int e = threadIdx.x; e < p * QB; e += blockDim.x) {
         const int k = e / QB, j = e % QB;
-        sT[e] = j < qb ? T[(int64_t)k * q + q0 + j] : 0.0;
+        sT[e] = (j < qb && GCHK(dbg, (int64_t)k * q + q0 + j, (int64_t)p * q, 321)) ? T[(int64_t)k * q + q0 + j] : 0.0;
     }
     __syncthreads();
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
@@ -153,8 +164,9 @@ __global__ void k_gemm_tall(int64_t n, int p, int q, int QB, int64_t rows_per_ch
     for (int64_t i = r0 + rsub; i < r1; i += rpb) {
         const double *y = Y + i * ldY;
         double acc = 0.0;
-        for (int k = 0; k < p; ++k) acc = fma(__ldg(y + k), sT[k * QB + j], acc);
-        Z[i * ldZ + q0 + j] = acc;
+        for (int k = 0; k < p; ++k)
+            if (GCHK(dbg, i * ldY + k, n * ldY, 322)) acc = fma(__ldg(y + k), sT[k * QB + j], acc);
+        if (GCHK(dbg, i * ldZ + q0 + j, n * ldZ, 323)) Z[i * ldZ + q0 + j] = acc;
     }
 }
 
@@ -172,7 +184,7 @@ int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const d
     if (smem > c->smem_optin) { set_error("gemm_tall: p too large"); return GCIE_EINVAL; }
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tall, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope ls(c, GCIE_K_DENSE, 8.0 * n * (p + q), 2.0 * n * p * q);
-    k_gemm_tall<<<dim3((unsigned)nchunk, qblocks), threads, smem, c->stream>>>(n, p, q, QB, rpc, Y, ldY, T, Z, ldZ);
+    k_gemm_tall<<<dim3((unsigned)nchunk, qblocks), threads, smem, c->stream>>>(n, p, q, QB, rpc, Y, ldY, T, Z, ldZ, c->dbg);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
@@ -189,7 +201,7 @@ int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const d
 // at most tol * ||A||_F.  Output: ascending eigenvalues w and eigenvectors as columns of V.
 __global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aall, double *__restrict__ wall,
                                                  double *__restrict__ Vall, double *__restrict__ Wk, double tol,
-                                                 int maxsweep)
+                                                 int maxsweep, DbgRec *dbg)
 {
     double *A = Aall + (int64_t)blockIdx.x * p * p;
     double *Vo = Vall + (int64_t)blockIdx.x * p * p;
@@ -253,6 +265,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aal
                 if (r < 0 || sn[k] == 0.0) continue;
                 const int q = qi[k];
                 const double c = cs[k], s = sn[k];
+                if (!GCHK(dbg, i * p + q, p * p, 331) || !GCHK(dbg, i * p + r, p * p, 332)) continue;
                 double aq = A[i * p + q], ar = A[i * p + r];
                 A[i * p + q] = c * aq - s * ar;
                 A[i * p + r] = s * aq + c * ar;
@@ -268,6 +281,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aal
                 if (r < 0 || sn[k] == 0.0) continue;
                 const int q = qi[k];
                 const double c = cs[k], s = sn[k];
+                if (!GCHK(dbg, q * p + j, p * p, 333) || !GCHK(dbg, r * p + j, p * p, 334)) continue;
                 double aq = A[q * p + j], ar = A[r * p + j];
                 A[q * p + j] = c * aq - s * ar;
                 A[r * p + j] = s * aq + c * ar;
@@ -289,6 +303,7 @@ __global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aal
             const double dj = A[j * p + j];
             rank += (dj < di) || (dj == di && j < i);
         }
+        if (!GCHK(dbg, rank, p, 335)) continue;
         w[rank] = di;
         for (int r = 0; r < p; ++r) Vo[r * p + rank] = V[r * p + i];
     }
@@ -301,7 +316,7 @@ int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
     double *wk = nullptr;
     GCIE_CUDA_TRY(cudaMallocAsync((void **)&wk, sizeof(double) * (size_t)nmat * p * p, c->stream));
     LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
-    k_jacobi<<<nmat, 1024, 0, c->stream>>>(p, A, w, V, wk, 1e-15, 60);
+    k_jacobi<<<nmat, 1024, 0, c->stream>>>(p, A, w, V, wk, 1e-15, 60, c->dbg);
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(wk, c->stream);
     if (e != cudaSuccess) { set_error(std::string("jacobi: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
@@ -312,18 +327,20 @@ int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
 // part[c][l] = sum over the chunk's rows of (KZ - theta_l MZ)^2, part2[c][l] = sum Z^2.
 __global__ void k_resid_part(int64_t n, int q, int64_t rows_per_chunk, const double *__restrict__ KZ,
                              const double *__restrict__ MZ, const double *__restrict__ Z,
-                             const double *__restrict__ theta, double *__restrict__ part)
+                             const double *__restrict__ theta, double *__restrict__ part, int nchunk, DbgRec *dbg)
 {
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
     for (int l = threadIdx.x; l < q; l += blockDim.x) {
         const double th = theta[l];
         double a = 0.0, b = 0.0;
         for (int64_t i = r0; i < r1; ++i) {
+            if (!GCHK(dbg, i * q + l, n * q, 341)) continue;
             const double r = KZ[i * q + l] - th * MZ[i * q + l];
             const double zz = Z[i * q + l];
             a = fma(r, r, a);
             b = fma(zz, zz, b);
         }
+        if (!GCHK(dbg, ((int64_t)blockIdx.x * 2 + 1) * q + l, (int64_t)nchunk * 2 * q, 343)) continue;
         part[((int64_t)blockIdx.x * 2 + 0) * q + l] = a;
         part[((int64_t)blockIdx.x * 2 + 1) * q + l] = b;
     }
@@ -354,7 +371,8 @@ int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, co
     GCIE_TRY(ctx_scratch(c, sizeof(double) * (size_t)nchunk * 2 * q, (void **)&part));
     {
         LaunchScope ls(c, GCIE_K_DENSE, 24.0 * n * q, 6.0 * n * q);
-        k_resid_part<<<nchunk, std::min(1024, ((q + 31) / 32) * 32), 0, c->stream>>>(n, q, rpc, KZ, MZ, Z, d_theta, part);
+        k_resid_part<<<nchunk, std::min(1024, ((q + 31) / 32) * 32), 0, c->stream>>>(n, q, rpc, KZ, MZ, Z, d_theta, part,
+                                                                                   nchunk, c->dbg);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     {
@@ -368,11 +386,12 @@ int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, co
 // ------------------------------------------------------------------ basis and Rayleigh-Ritz
 // T[:, j] = U[:, idx_j] / sqrt(s[idx_j]) for the kept eigenpairs (largest first).
 __global__ void k_scale_cols(int p, int k, const double *__restrict__ U, const double *__restrict__ s,
-                             double *__restrict__ T)
+                             double *__restrict__ T, DbgRec *dbg)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * k; e += gridDim.x * blockDim.x) {
         const int r = e / k, j = e % k;
         const int src = p - 1 - j;   // ascending order from Jacobi: largest last
+        if (!GCHK(dbg, r * p + src, p * p, 361) || !GCHK(dbg, src, p, 362)) continue;
         T[e] = U[r * p + src] / sqrt(s[src]);
     }
 }
@@ -401,7 +420,7 @@ static int orth_pass(Ctx *c, const Pencil *p, int64_t n, int ncol, const double 
     if (k == 0) { set_error("m_orthonormalize: basis has rank 0"); return GCIE_ENOTSPD; }
     {
         LaunchScope ls(c, GCIE_K_DENSE, 16.0 * ncol * k, 0);
-        k_scale_cols<<<std::max(1, (ncol * k + 255) / 256), 256, 0, c->stream>>>(ncol, k, U, s, T);
+        k_scale_cols<<<std::max(1, (ncol * k + 255) / 256), 256, 0, c->stream>>>(ncol, k, U, s, T, c->dbg);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     GCIE_CUDA_TRY(cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * ncol, c->stream));

@@ -118,7 +118,7 @@ int shifted_spmm_f64(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, in
 // Y = A X, X and Y n x q row-major.  Thread layout: q threads per row (one column each).
 __global__ void __launch_bounds__(256) k_spmm_real(int64_t n, const int *__restrict__ rowptr,
         const int *__restrict__ col, const double *__restrict__ val, int q, const double *__restrict__ X,
-        double *__restrict__ Y)
+        double *__restrict__ Y, int64_t nnz, DbgRec *dbg)
 {
     const int rpb = blockDim.x / q;
     const int t = threadIdx.x % q, rsub = threadIdx.x / q;
@@ -126,8 +126,12 @@ __global__ void __launch_bounds__(256) k_spmm_real(int64_t n, const int *__restr
     for (int64_t i = (int64_t)blockIdx.x * rpb + rsub; i < n; i += (int64_t)gridDim.x * rpb) {
         double acc = 0.0;
         const int e1 = rowptr[i + 1];
-        for (int k = rowptr[i]; k < e1; ++k) acc = fma(__ldg(val + k), __ldg(X + (int64_t)__ldg(col + k) * q + t), acc);
-        Y[i * q + t] = acc;
+        for (int k = rowptr[i]; k < e1; ++k) {
+            if (!GCHK(dbg, k, nnz, 372)) continue;
+            const int64_t xi = (int64_t)__ldg(col + k) * q + t;
+            if (GCHK(dbg, xi, n * q, 373)) acc = fma(__ldg(val + k), __ldg(X + xi), acc);
+        }
+        if (GCHK(dbg, i * q + t, n * q, 374)) Y[i * q + t] = acc;
     }
 }
 
@@ -140,7 +144,8 @@ int spmm_real(Ctx *c, const Pencil *p, int which, int q, const double *X, double
     int64_t blocks = (p->n + rpb - 1) / rpb;
     if (blocks > (int64_t)c->num_sms * 64) blocks = (int64_t)c->num_sms * 64;
     LaunchScope ls(c, GCIE_K_DENSE, (double)p->n * q * 16 + p->nnz * 12.0, 2.0 * p->nnz * q);
-    k_spmm_real<<<(int)blocks, threads, 0, c->stream>>>(p->n, p->rowptr, p->col, which ? p->m64 : p->k64, q, X, Y);
+    k_spmm_real<<<(int)blocks, threads, 0, c->stream>>>(p->n, p->rowptr, p->col, which ? p->m64 : p->k64, q, X, Y,
+                                                          p->nnz, c->dbg);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
