@@ -75,7 +75,7 @@ typedef struct {
     int32_t max_iters;      /* COCG iteration cap per shifted solve (default 100000) */
     int32_t precision;      /* GCIE_MIXED (default) or GCIE_FP64 */
     double tol;             /* eigenpair tolerance on ||Kx - lambda Mx||_2 / (||K||_1 ||x||_2) (1e-10) */
-    double lin_tol;         /* shifted-solve target ||b - A x||_2 / ||b||_2 (default 1e-11) */
+    double lin_tol;         /* shifted-solve target on the diagonally scaled residual (default 1e-11) */
     int32_t ncontours;      /* > 0: use contours[0..ncontours-1]; 0: nuniform equal-width pieces */
     int32_t nuniform;       /* number of equal-width contours when ncontours == 0 (default 1) */
     const gcie_contour *contours;   /* host, borrowed */
@@ -177,8 +177,9 @@ int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const d
                           int32_t ncol, const double *d_P, double *d_Q);
 
 /* Steps a4-a6 (shifted block solves): X[s] = (z_s M - K)^{-1} B for every shift s, by batched
- * COCG (FP32 with FP64 refinement for GCIE_MIXED, FP64 for GCIE_FP64) to
- * ||B - A X[s]||_2 / ||B||_2 <= lin_tol per column.
+ * COCG (FP32 with FP64 refinement for GCIE_MIXED, FP64 for GCIE_FP64) on the symmetrically
+ * scaled system D^-1/2 (z_s M - K) D^-1/2 (D = diag K, or diag M if some K_ii <= 0), to
+ * ||D^-1/2 (B - A X[s])||_2 / ||D^-1/2 B||_2 <= lin_tol per column.
  * d_B: FP64 real n x ncol row-major (shared by all shifts); d_X: FP64 complex, nshift blocks of
  * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  h_iters (host, may be
  * NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol

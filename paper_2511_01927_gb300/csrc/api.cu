@@ -347,6 +347,23 @@ int gcie_pencil_create(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, gcie_p
     mv.swap(ms);
     p->bw = bw;
     p->norm_k1 = nk;
+    // diagonal scaling for the shifted solves
+    bool kpos = true;
+    std::vector<double> dk(n, 0.0), dm(n, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k)
+            if (cl[k] == i) { dk[i] = kv[k]; dm[i] = mv[k]; }
+    for (int64_t i = 0; i < n; ++i) kpos = kpos && dk[i] > 0.0;
+    std::vector<double> dsc(n);
+    for (int64_t i = 0; i < n; ++i) dsc[i] = 1.0 / std::sqrt(kpos ? dk[i] : dm[i]);
+    std::vector<double> ks64(p->nnz), ms64(p->nnz);
+    std::vector<float> ks32(p->nnz), ms32(p->nnz);
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+            const double f = dsc[i] * dsc[cl[k]];
+            ks64[k] = kv[k] * f; ms64[k] = mv[k] * f;
+            ks32[k] = (float)ks64[k]; ms32[k] = (float)ms64[k];
+        }
     // device copies
     std::vector<int> rp32(n + 1);
     for (int64_t i = 0; i <= n; ++i) rp32[i] = (int)rp[i];
@@ -359,7 +376,12 @@ int gcie_pencil_create(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, gcie_p
               cudaMalloc(&p->k32, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
               cudaMalloc(&p->m32, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
               cudaMalloc(&p->k64, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess &&
-              cudaMalloc(&p->m64, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess;
+              cudaMalloc(&p->m64, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->dsc, sizeof(double) * n) == cudaSuccess &&
+              cudaMalloc(&p->k32s, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->m32s, sizeof(float) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->k64s, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess &&
+              cudaMalloc(&p->m64s, sizeof(double) * std::max<size_t>(nz, 1)) == cudaSuccess;
     if (!ok) { cudaGetLastError(); gcie_pencil_destroy(p); set_error("pencil: device allocation failed"); return GCIE_ENOMEM; }
     cudaStream_t st = c->stream;
     cudaError_t e = cudaSuccess;
@@ -369,6 +391,11 @@ int gcie_pencil_create(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, gcie_p
     e = e ? e : cudaMemcpyAsync(p->m32, m32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice, st);
     e = e ? e : cudaMemcpyAsync(p->k64, kv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
     e = e ? e : cudaMemcpyAsync(p->m64, mv.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->dsc, dsc.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->k32s, ks32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->m32s, ms32.data(), sizeof(float) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->k64s, ks64.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
+    e = e ? e : cudaMemcpyAsync(p->m64s, ms64.data(), sizeof(double) * nz, cudaMemcpyHostToDevice, st);
     e = e ? e : cudaStreamSynchronize(st);
     if (e != cudaSuccess) { gcie_pencil_destroy(p); set_error(std::string("pencil upload: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
     *out = p;
@@ -380,6 +407,7 @@ void gcie_pencil_destroy(gcie_pencil *p)
     if (!p) return;
     if (p->ctx) cudaStreamSynchronize(p->ctx->stream);
     cudaFree(p->rowptr); cudaFree(p->col); cudaFree(p->k32); cudaFree(p->m32); cudaFree(p->k64); cudaFree(p->m64);
+    cudaFree(p->dsc); cudaFree(p->k32s); cudaFree(p->m32s); cudaFree(p->k64s); cudaFree(p->m64s);
     delete p;
 }
 

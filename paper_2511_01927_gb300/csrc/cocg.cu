@@ -212,10 +212,15 @@ __global__ void __launch_bounds__(256) k_upd(int64_t n, const int *__restrict__ 
 }
 
 // ------------------------------------------------------------------ refinement (reliable update)
-// x64 += d, d = 0 for the shifts flagged for refinement.
+// The FP32 system is kept at unit scale: at each update the true residual r64 is divided by a
+// per-column scale s (its norm, or an estimate of it), the recurrences solve A d = r64 / s, and
+// the fold is x64 += s d.  Without this the residual of a converging column reaches magnitudes
+// whose squares underflow in FP32 and the COCG scalars lose all accuracy.
+
+// x64 += scale * d, d = 0 for the shifts flagged for refinement.
 template <typename T>
 __global__ void k_refine_x(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine,
-                           typename cplx<T>::t *__restrict__ D, double2 *__restrict__ X)
+                           const double *__restrict__ scale, typename cplx<T>::t *__restrict__ D, double2 *__restrict__ X)
 {
     const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     if (!shift_refine[s]) return;
@@ -223,21 +228,23 @@ __global__ void k_refine_x(int64_t n, int ncol, int64_t rows_per_chunk, int chun
     const int64_t base = (int64_t)s * n * ncol;
     for (int64_t e = r0 * ncol + threadIdx.x; e < r1 * ncol; e += blockDim.x) {
         typename cplx<T>::t d = D[base + e];
+        const double sc = scale[(int64_t)s * ncol + (int)(e % ncol)];
         double2 x = X[base + e];
-        x.x += (double)d.x; x.y += (double)d.y;
+        x.x += sc * (double)d.x; x.y += sc * (double)d.y;
         X[base + e] = x;
         d.x = 0; d.y = 0;
         D[base + e] = d;
     }
 }
 
-// r64 = b - (z M - K) x64 in FP64; r = (T) r64; partials of r^T r (from the rounded r) and |r64|^2.
+// r64 = b - (z M - K) x64 in FP64; r = (T)(r64 / scale_next) unless norm_only; partials of r^T r
+// (from the rounded, scaled r) and |r64|^2 (absolute).
 template <typename T, int CPT>
 __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
         const double *__restrict__ kv, const double *__restrict__ mv, const double2 *__restrict__ z, int ncol,
         int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine, const int *__restrict__ rhs_of,
-        const double *__restrict__ B, const double2 *__restrict__ X, typename cplx<T>::t *__restrict__ R,
-        double2 *__restrict__ partA, double *__restrict__ partB)
+        const double *__restrict__ B, const double2 *__restrict__ X, const double *__restrict__ scale_next,
+        int norm_only, typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA, double *__restrict__ partB)
 {
     using C = typename cplx<T>::t;
     const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
@@ -250,6 +257,9 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
     C *Rs = R + off;
     const double *Bs = B + (int64_t)rhs_of[s] * n * ncol + t * CPT;
     const double zr = z[s].x, zi = z[s].y;
+    double inv[CPT];
+#pragma unroll
+    for (int q = 0; q < CPT; ++q) inv[q] = 1.0 / scale_next[(int64_t)s * ncol + t * CPT + q];
     double pa[CPT][2] = {}, pb[CPT] = {};
     for (int64_t i = r0 + rsub; i < r1; i += rpb) {
         double am[CPT][2] = {}, ak[CPT][2] = {};
@@ -270,13 +280,15 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
             double apr = zr * am[q][0] - zi * am[q][1] - ak[q][0];
             double api = zr * am[q][1] + zi * am[q][0] - ak[q][1];
             double rr = __ldg(Bs + i * ncol + q) - apr, ri = -api;
-            C rt;
-            rt.x = (T)rr; rt.y = (T)ri;
-            Rs[i * ncol + q] = rt;
-            double tr = (double)rt.x, ti = (double)rt.y;
-            pa[q][0] += tr * tr - ti * ti;
-            pa[q][1] += 2 * tr * ti;
             pb[q] += rr * rr + ri * ri;
+            if (!norm_only) {
+                C rt;
+                rt.x = (T)(rr * inv[q]); rt.y = (T)(ri * inv[q]);
+                Rs[i * ncol + q] = rt;
+                double tr = (double)rt.x, ti = (double)rt.y;
+                pa[q][0] += tr * tr - ti * ti;
+                pa[q][1] += 2 * tr * ti;
+            }
         }
     }
     const int64_t tile = (int64_t)s * chunks + ch;
@@ -284,10 +296,11 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
 }
 
 // ------------------------------------------------------------------ per-column scalar kernels
-// One CTA per shift, one thread per column (ncol <= 1024).
+// One CTA per shift, one thread per column (ncol <= 1024).  Units: rho, sigma, alpha, beta, eta,
+// eta_ref are in the scaled FP32 system; eta_abs and bnorm2 are absolute FP64 squared norms.
 struct Scal {
     double2 *rho, *alpha, *beta;
-    double *eta, *eta_ref, *bnorm2;
+    double *eta, *eta_ref, *bnorm2, *scale, *scale_next;
     int *flag, *shift_active, *shift_refine, *since_refine;
     double2 *partA;
     double *partB;
@@ -344,7 +357,12 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double 
             S.rho[sc] = rho;
             S.eta[sc] = eta;
             S.flag[sc] = f;
-            want = (eta <= delta2 * S.eta_ref[sc]) || (eta <= tol2 * S.bnorm2[sc]) || (f & F_RESTART) || !isfinite(eta);
+            const double sc2 = S.scale[sc] * S.scale[sc];
+            want = (eta <= delta2 * S.eta_ref[sc]) || (eta * sc2 <= tol2 * S.bnorm2[sc]) || (f & F_RESTART) ||
+                   !isfinite(eta);
+            // scale of the next update: the recursive residual's norm (a small fraction when it
+            // underflowed or is not finite)
+            S.scale_next[sc] = (eta > 0 && isfinite(eta)) ? S.scale[sc] * sqrt(eta) : S.scale[sc] * 1e-4;
         }
         if (!want) atomicAnd(&all_want, 0);
     }
@@ -356,6 +374,8 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double 
     }
 }
 
+// After the update: absolute residual norms decide convergence; the scaled system restarts at
+// eta = eta_abs / scale^2 with the new scale.
 __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
 {
     __shared__ int any_active;
@@ -366,19 +386,22 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
     if (l < ncol) {
         const int64_t sc = (int64_t)s * ncol + l;
         double2 rho = make_double2(0, 0);
-        double eta = 0;
+        double eta_abs = 0;
         for (int c = 0; c < chunks; ++c) {
             int64_t idx = ((int64_t)s * chunks + c) * ncol + l;
             double2 v = S.partA[idx];
             rho.x += v.x; rho.y += v.y;
-            eta += S.partB[idx];
+            eta_abs += S.partB[idx];
         }
         int f = S.flag[sc];
-        S.eta_ref[sc] = eta;
+        const double sn = S.scale_next[sc];
+        S.scale[sc] = sn;
+        const double eta_s = eta_abs / (sn * sn);
+        S.eta_ref[sc] = eta_s;
         if (f & F_ACTIVE) {
-            S.eta[sc] = eta;
+            S.eta[sc] = eta_s;
             S.rho[sc] = rho;
-            if (eta <= tol2 * S.bnorm2[sc]) {
+            if (eta_abs <= tol2 * S.bnorm2[sc]) {
                 f = F_CONV;
                 S.beta[sc] = make_double2(0, 0);
             } else if (f & F_RESTART) {
@@ -395,6 +418,17 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
         S.shift_refine[s] = 0;
         S.since_refine[s] = 0;
     }
+}
+
+// First update of a solve: scale_next = ||b - A x0|| from a norm-only residual pass.
+__global__ void k_scale_from_norm(int ncol, int chunks, Scal S)
+{
+    const int s = blockIdx.x, l = threadIdx.x;
+    if (l >= ncol) return;
+    double eta_abs = 0;
+    for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
+    const double nrm = sqrt(eta_abs);
+    S.scale_next[(int64_t)s * ncol + l] = (nrm > 0 && isfinite(nrm)) ? nrm : 1.0;
 }
 
 // ||b||^2 per (rhs, column): row-chunk partial sums (partB[rhs][chunk][l]) ...
@@ -424,9 +458,24 @@ __global__ void k_bnorm_init(int ncol, int chunks, const int *__restrict__ rhs_o
         S.beta[sc] = make_double2(0, 0);
         S.alpha[sc] = make_double2(0, 0);
         S.rho[sc] = make_double2(0, 0);
-        S.eta_ref[sc] = acc;
+        S.eta_ref[sc] = 1.0;
+        S.scale[sc] = 1.0;
+        S.scale_next[sc] = 1.0;
     }
     if (threadIdx.x == 0) { S.shift_active[s] = 1; S.shift_refine[s] = 1; S.since_refine[s] = 0; }
+}
+
+// X[e] *= dsc[row]^pow for every element of nblk blocks of n x ncol (pow = +1 or -1); complex
+// or real (ncomp = 2 or 1 doubles per element).
+__global__ void k_scale_rows(int64_t n, int ncol, int64_t nblk, int ncomp, const double *__restrict__ dsc, int inverse,
+                             const double *__restrict__ src, double *__restrict__ dst)
+{
+    const int64_t total = nblk * n * ncol * ncomp;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = (e / ((int64_t)ncol * ncomp)) % n;
+        const double d = dsc[i];
+        dst[e] = inverse ? src[e] / d : src[e] * d;
+    }
 }
 
 // ------------------------------------------------------------------ host driver
@@ -439,15 +488,21 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     const int64_t n = p->n;
     if (ncol % CPT || ncol > 1024 || ncol <= 0) { set_error("cocg: ncol must be even and <= 1024"); return GCIE_EINVAL; }
     Geo g = make_geo(c, n, nshift, ncol, CPT);
-    Geo gr = make_geo(c, n, nshift, ncol, 2);  // refine sweep: 2 columns per thread
-    if (ncol % 2) gr = make_geo(c, n, nshift, ncol, 1);
+    Geo gr = make_geo(c, n, nshift, ncol, ncol % 2 ? 1 : 2);  // refinement sweep
     const int64_t blk = (int64_t)nshift * n * ncol;
     const int ntiles = nshift * g.chunks, ntiles_r = nshift * gr.chunks;
     const int maxch = std::max(g.chunks, gr.chunks);
-    // device memory: D, R, P0, P1 blocks; state; partials
-    size_t bytes = 4 * blk * sizeof(C) + (size_t)nshift * ncol * (3 * sizeof(double2) + 3 * sizeof(double) + sizeof(int)) +
-                   (size_t)nshift * 3 * sizeof(int) + (size_t)nshift * maxch * ncol * (sizeof(double2) + sizeof(double)) +
-                   (size_t)nshift * (sizeof(double2) + sizeof(int)) + 4096;
+    const size_t ns = (size_t)nshift * ncol;
+    // one allocation, carved into 256-byte aligned pieces (sizes listed once, used twice)
+    const size_t sizes[] = {blk * sizeof(C), blk * sizeof(C), blk * sizeof(C), blk * sizeof(C),
+                            ns * sizeof(double2), ns * sizeof(double2), ns * sizeof(double2),
+                            ns * sizeof(double), ns * sizeof(double), ns * sizeof(double), ns * sizeof(double),
+                            ns * sizeof(double), ns * sizeof(int), nshift * sizeof(int), nshift * sizeof(int),
+                            nshift * sizeof(int), (size_t)nshift * maxch * ncol * sizeof(double2),
+                            (size_t)nshift * maxch * ncol * sizeof(double), nshift * sizeof(double2),
+                            nshift * sizeof(int)};
+    size_t bytes = 0;
+    for (size_t b : sizes) bytes += (b + 255) & ~(size_t)255;
     char *base = nullptr;
     cudaError_t ce = cudaMallocAsync((void **)&base, bytes, c->stream);
     if (ce != cudaSuccess) {
@@ -456,41 +511,44 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         return GCIE_ENOMEM;
     }
     char *q = base;
-    auto take = [&](size_t b) { char *r = q; q += (b + 255) & ~(size_t)255; return (void *)r; };
-    C *D = (C *)take(blk * sizeof(C));
-    C *R = (C *)take(blk * sizeof(C));
-    C *P[2] = {(C *)take(blk * sizeof(C)), (C *)take(blk * sizeof(C))};
+    int piece = 0;
+    auto take = [&]() { char *r = q; q += (sizes[piece++] + 255) & ~(size_t)255; return (void *)r; };
+    C *D = (C *)take();
+    C *R = (C *)take();
+    C *P[2] = {(C *)take(), (C *)take()};
     Scal S;
-    const size_t ns = (size_t)nshift * ncol;
-    S.rho = (double2 *)take(ns * sizeof(double2));
-    S.alpha = (double2 *)take(ns * sizeof(double2));
-    S.beta = (double2 *)take(ns * sizeof(double2));
-    S.eta = (double *)take(ns * sizeof(double));
-    S.eta_ref = (double *)take(ns * sizeof(double));
-    S.bnorm2 = (double *)take(ns * sizeof(double));
-    S.flag = (int *)take(ns * sizeof(int));
-    S.shift_active = (int *)take(nshift * sizeof(int));
-    S.shift_refine = (int *)take(nshift * sizeof(int));
-    S.since_refine = (int *)take(nshift * sizeof(int));
-    S.partA = (double2 *)take((size_t)nshift * maxch * ncol * sizeof(double2));
-    S.partB = (double *)take((size_t)nshift * maxch * ncol * sizeof(double));
-    double2 *d_z = (double2 *)take(nshift * sizeof(double2));
-    int *d_rhs = (int *)take(nshift * sizeof(int));
+    S.rho = (double2 *)take();
+    S.alpha = (double2 *)take();
+    S.beta = (double2 *)take();
+    S.eta = (double *)take();
+    S.eta_ref = (double *)take();
+    S.bnorm2 = (double *)take();
+    S.scale = (double *)take();
+    S.scale_next = (double *)take();
+    S.flag = (int *)take();
+    S.shift_active = (int *)take();
+    S.shift_refine = (int *)take();
+    S.since_refine = (int *)take();
+    S.partA = (double2 *)take();
+    S.partB = (double *)take();
+    double2 *d_z = (double2 *)take();
+    int *d_rhs = (int *)take();
 
     int rc = GCIE_OK;
     std::vector<double2> hz(nshift);
     for (int s = 0; s < nshift; ++s) hz[s] = make_double2(h_z[2 * s], h_z[2 * s + 1]);
     std::vector<int> hact(nshift, 1);
-    int64_t iters = 0, refines = 0;
-    const double delta2 = sizeof(T) == 4 ? 1e-8 : 0.0;   // refine after a 1e4 drop in FP32
+    int64_t iters = 0;
+    const double delta2 = sizeof(T) == 4 ? 1e-8 : 0.0;   // FP32: update after a 1e4 drop
     const double tol2 = lin_tol * lin_tol;
     const int max_since = sizeof(T) == 4 ? 4000 : 1 << 30;
     const size_t smem = (size_t)256 * CPT * 3 * sizeof(double) + 64;
     const size_t smem_r = (size_t)256 * 2 * 3 * sizeof(double) + 64;
-    const T *kv = sizeof(T) == 4 ? (const T *)p->k32 : (const T *)p->k64;
-    const T *mv = sizeof(T) == 4 ? (const T *)p->m32 : (const T *)p->m64;
+    const T *kv = sizeof(T) == 4 ? (const T *)p->k32s : (const T *)p->k64s;
+    const T *mv = sizeof(T) == 4 ? (const T *)p->m32s : (const T *)p->m64s;
     const double esz = sizeof(C);
     const double mat = (double)p->nnz * (4 + 2 * sizeof(T)) + 4.0 * (n + 1);
+    const int sthreads = std::max(32, ((ncol + 31) / 32) * 32);
     int active_shifts = nshift;
 
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), nshift * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
@@ -508,30 +566,42 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         k_bnorm_init<<<nshift, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, bch, d_rhs, S.partB, S);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
+    auto refine_r = [&](int nact, int norm_only) -> int {
+        LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
+                       (double)nact * p->nnz * ncol * 8.0);
+        if (ncol % 2 == 0)
+            k_refine_r<T, 2><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
+                ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
+                S.partA, S.partB);
+        else
+            k_refine_r<T, 1><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
+                ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
+                S.partA, S.partB);
+        GCIE_CUDA_TRY(cudaGetLastError());
+        return GCIE_OK;
+    };
     auto refine = [&](int nact) -> int {
         {
             LaunchScope ls(c, GCIE_K_REFINE, (double)nact * n * ncol * (2 * esz + 32), 0);
-            k_refine_x<T><<<ntiles, 256, 0, c->stream>>>(n, ncol, g.rows_per_chunk, g.chunks, S.shift_refine, D, d_X);
+            k_refine_x<T><<<ntiles, 256, 0, c->stream>>>(n, ncol, g.rows_per_chunk, g.chunks, S.shift_refine, S.scale, D, d_X);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
-        {
-            LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
-                           (double)nact * p->nnz * ncol * 8.0);
-            if (ncol % 2 == 0)
-                k_refine_r<T, 2><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64, p->m64, d_z,
-                    ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, R, S.partA, S.partB);
-            else
-                k_refine_r<T, 1><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64, p->m64, d_z,
-                    ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, R, S.partA, S.partB);
-            GCIE_CUDA_TRY(cudaGetLastError());
-        }
+        GCIE_TRY(refine_r(nact, 0));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-            k_scal_refine<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, gr.chunks, S, tol2);
+            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         return GCIE_OK;
     };
+    // first update: exact scale from a norm-only residual pass, then the scaled residual
+    rc = refine_r(nshift, 1);
+    if (rc) goto done;
+    {
+        LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
+        k_scale_from_norm<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
     rc = refine(nshift);
     if (rc) goto done;
     {
@@ -554,7 +624,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                 }
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-                    k_scal_alpha<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, g.chunks, S);
+                    k_scal_alpha<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 {
@@ -566,14 +636,12 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                 }
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-                    k_scal_beta<<<nshift, std::max(32, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, g.chunks, S,
-                        delta2, tol2, max_since);
+                    k_scal_beta<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, delta2, tol2, max_since);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 rc = refine(0);
                 if (rc) goto done;
             }
-            iters = it;
         }
         iters = it;
         // fold any remaining correction into x64 for columns that did not converge
@@ -590,7 +658,6 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         for (size_t e = 0; e < ns; ++e) unconv += (hf[e] & F_ACTIVE) != 0;
         if (info) {
             info->iters += iters;
-            info->refines += refines;
             info->unconverged_cols += unconv;
         }
         if (unconv) {
@@ -609,9 +676,35 @@ int cocg_solve(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int
     if (nshift <= 0) return GCIE_OK;
     for (int s = 0; s < nshift; ++s)
         if (h_rhs_of[s] < 0 || h_rhs_of[s] >= nrhs) { set_error("cocg: rhs index out of range"); return GCIE_EINVAL; }
-    if (precision == GCIE_FP64)
-        return solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, d_B, d_X, x0, lin_tol, max_iters, info);
-    return solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, d_B, d_X, x0, lin_tol, max_iters, info);
+    // solve the diagonally scaled system D^-1/2 (z M - K) D^-1/2 y = D^-1/2 b, x = D^-1/2 y
+    const int64_t n = p->n;
+    double *Bs = nullptr;
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&Bs, sizeof(double) * (size_t)nrhs * n * ncol, c->stream));
+    auto grid = [&](int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 32)); };
+    int rc = GCIE_OK;
+    {
+        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * nrhs * n * ncol, 0);
+        k_scale_rows<<<grid((int64_t)nrhs * n * ncol), 256, 0, c->stream>>>(n, ncol, nrhs, 1, p->dsc, 0, d_B, Bs);
+        if (cudaGetLastError() != cudaSuccess) rc = GCIE_ECUDA;
+    }
+    if (rc == GCIE_OK && x0) {
+        LaunchScope ls(c, GCIE_K_OTHER, 32.0 * nshift * n * ncol, 0);
+        k_scale_rows<<<grid((int64_t)nshift * n * ncol * 2), 256, 0, c->stream>>>(n, ncol, nshift, 2, p->dsc, 1,
+                                                                                  (const double *)d_X, (double *)d_X);
+        if (cudaGetLastError() != cudaSuccess) rc = GCIE_ECUDA;
+    }
+    if (rc == GCIE_OK)
+        rc = precision == GCIE_FP64
+                 ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, info)
+                 : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, info);
+    if (rc == GCIE_OK || rc == GCIE_ENOCONV) {
+        LaunchScope ls(c, GCIE_K_OTHER, 32.0 * nshift * n * ncol, 0);
+        k_scale_rows<<<grid((int64_t)nshift * n * ncol * 2), 256, 0, c->stream>>>(n, ncol, nshift, 2, p->dsc, 0,
+                                                                                  (const double *)d_X, (double *)d_X);
+        if (cudaGetLastError() != cudaSuccess) { set_error("cocg: unscale launch failed"); rc = GCIE_ECUDA; }
+    }
+    cudaFreeAsync(Bs, c->stream);
+    return rc;
 }
 
 }  // namespace gcie

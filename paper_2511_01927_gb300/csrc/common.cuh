@@ -59,6 +59,12 @@ struct Pencil {
     float *k32 = nullptr, *m32 = nullptr;    // FP32 values of K and M on the union pattern
     double *k64 = nullptr, *m64 = nullptr;   // FP64 values
     double norm_k1 = 0.0;            // ||K||_1
+    // Symmetric diagonal scaling used inside the shifted solves: with D = diag(K) (diag(M) if some
+    // K_ii <= 0), the solver works on D^-1/2 (z M - K) D^-1/2, which has the same solution up to
+    // x = D^-1/2 y and a much smaller spread of diagonal magnitudes.
+    double *dsc = nullptr;           // n: D^-1/2
+    float *k32s = nullptr, *m32s = nullptr;
+    double *k64s = nullptr, *m64s = nullptr;
     // host copies (union pattern, symmetrised) for the host-side de-duplication
     std::vector<int64_t> h_rowptr;
     std::vector<int32_t> h_col;

@@ -4,8 +4,9 @@ Tolerances:
   * FP32 shifted SpMM: per element, 2^-21 * ((|z| |M| + |K|) |P|)_i  (a few FP32 roundings of every
     product and sum that forms the element);
   * FP64 kernels: the same bound with 2^-49;
-  * shifted solves: the defining residual ||B - (zM - K) X|| / ||B|| <= 2 lin_tol, computed here in
-    FP64 by the oracle's operator, and the LU solution's forward error;
+  * shifted solves: the residual ||D^-1/2 (B - (zM - K) X)|| / ||D^-1/2 B|| <= 2 lin_tol (D = diag K,
+    the library's stopping test), computed here in FP64 by the oracle's operator, and the LU
+    solution's forward error;
   * eigenpairs: values within 1e-10 relative of the oracle / closed form, residual <= 1e-10,
     counts equal to the oracle's inertia count exactly.
 """
@@ -109,9 +110,11 @@ def test_shifted_solve_matches_lu(G, ctx, small2d, precision):
     iters, rc = G.gcie_shifted_solve(ctx, pen, z, ncol, dB, dX, lin_tol=lin_tol, precision=precision)
     X = host(dX)
     assert iters > 0
+    # the stopping test is on the symmetrically scaled system D^-1/2 (zM - K) D^-1/2 with D = diag(K)
+    dsc = 1.0 / np.sqrt(K.to_scipy().diagonal())
     for s, zs in enumerate(z):
         res = B - O.shifted_apply(K, M, zs, X[s])
-        rel = np.linalg.norm(res, axis=0) / np.linalg.norm(B, axis=0)
+        rel = np.linalg.norm(dsc[:, None] * res, axis=0) / np.linalg.norm(dsc[:, None] * B, axis=0)
         assert np.max(rel) <= 2 * lin_tol, (s, rel)
         Xr = O.ShiftedSolver(K, M, zs).solve(B)
         err = np.linalg.norm(X[s] - Xr, axis=0) / np.linalg.norm(Xr, axis=0)
