@@ -85,6 +85,7 @@ typedef struct {
     size_t hbm_budget_bytes;/* device memory the solve may use (0: 90% of free memory) */
     int32_t expected_count; /* >= 0: return GCIE_ECOUNT if the merged count differs; -1: off */
     int32_t profile;        /* 1: time every kernel launch with CUDA events (see gcie_stats) */
+    int32_t precond;        /* 1 (default): multigrid-preconditioned COCG; 0: plain COCG */
 } gcie_opts;
 
 /* Results: library-allocated host arrays, released by gcie_result_free. */
@@ -106,7 +107,7 @@ typedef struct {
 
 /* Per-kernel-class accounting since the last gcie_reset_stats (profile = 1 fills times). */
 enum { GCIE_K_SPMM_DIR = 0, GCIE_K_SPMM_UPD = 1, GCIE_K_REFINE = 2, GCIE_K_MOMENT = 3,
-       GCIE_K_DENSE = 4, GCIE_K_OTHER = 5, GCIE_K_NCLASS = 6 };
+       GCIE_K_DENSE = 4, GCIE_K_OTHER = 5, GCIE_K_PREC = 6, GCIE_K_NCLASS = 7 };
 typedef struct {
     int64_t launches[GCIE_K_NCLASS];
     double ms[GCIE_K_NCLASS];          /* summed CUDA-event durations of those launches */
@@ -181,12 +182,13 @@ int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const d
  * scaled system D^-1/2 (z_s M - K) D^-1/2 (D = diag K, or diag M if some K_ii <= 0), to
  * ||D^-1/2 (B - A X[s])||_2 / ||D^-1/2 B||_2 <= lin_tol per column.
  * d_B: FP64 real n x ncol row-major (shared by all shifts); d_X: FP64 complex, nshift blocks of
- * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  h_iters (host, may be
- * NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
+ * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  precond = 1 applies the
+ * multigrid V-cycle preconditioner (built from K and M on the first call for this pencil and kept
+ * with it), 0 runs plain COCG.  h_iters (host, may be NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
  * within max_iters (d_X then holds the best iterate). */
 int gcie_shifted_solve(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
                        int32_t ncol, const double *d_B, double *d_X, int32_t x0, double lin_tol,
-                       int32_t max_iters, int32_t precision, int64_t *h_iters);
+                       int32_t max_iters, int32_t precision, int32_t precond, int64_t *h_iters);
 
 /* Step a7 (moments): S_k += 2 Re( w_s ((z_s - c)/r)^k X[s] ), k = 0..m-1, summed over the nshift
  * upper-half nodes.  d_X as in gcie_shifted_solve; d_S: FP64 n x (m*ncol) row-major, column

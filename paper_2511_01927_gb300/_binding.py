@@ -41,7 +41,7 @@ class Opts(C.Structure):
                 ("max_iters", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double), ("lin_tol", C.c_double),
                 ("ncontours", C.c_int32), ("nuniform", C.c_int32), ("contours", C.c_void_p), ("alpha", C.c_double),
                 ("h_V0", C.c_void_p), ("seed", C.c_uint64), ("hbm_budget_bytes", C.c_size_t),
-                ("expected_count", C.c_int32), ("profile", C.c_int32)]
+                ("expected_count", C.c_int32), ("profile", C.c_int32), ("precond", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -52,8 +52,8 @@ class Result(C.Structure):
                 ("outer_iters", C.c_int32), ("cocg_iters", C.c_int64), ("norm_k1", C.c_double)]
 
 
-NCLASS = 6
-KERNEL_CLASSES = ["spmm_dir", "spmm_upd", "refine", "moment", "dense", "other"]
+NCLASS = 7
+KERNEL_CLASSES = ["spmm_dir", "spmm_upd", "refine", "moment", "dense", "other", "prec"]
 
 
 class Stats(C.Structure):
@@ -96,7 +96,7 @@ def lib():
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
         "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_spmm_f64": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
-        "gcie_shifted_solve": (C.c_int, [vp, vp, i32, vp, i32, vp, vp, i32, d, i32, i32, C.POINTER(i64)]),
+        "gcie_shifted_solve": (C.c_int, [vp, vp, i32, vp, i32, vp, vp, i32, d, i32, i32, i32, C.POINTER(i64)]),
         "gcie_moments": (C.c_int, [vp, i64, i32, vp, vp, d, d, i32, i32, vp, vp]),
         "gcie_m_orthonormalize": (C.c_int, [vp, vp, i32, vp, d, vp, C.POINTER(i32)]),
         "gcie_rayleigh_ritz": (C.c_int, [vp, vp, i32, vp, vp, vp, vp]),
@@ -270,11 +270,11 @@ def gcie_shifted_spmm_f64(ctx, pencil, z, ncol: int, d_P, d_Q):
 
 
 def gcie_shifted_solve(ctx, pencil, z, ncol: int, d_B, d_X, x0: bool = False, lin_tol: float = 1e-11,
-                       max_iters: int = 100000, precision: int = MIXED, allow_noconv: bool = False):
+                       max_iters: int = 100000, precision: int = MIXED, precond: int = 1, allow_noconv: bool = False):
     zz = _zarr(z)
     it = C.c_int64(0)
     rc = lib().gcie_shifted_solve(ctx, pencil, len(zz), zz.ctypes.data, int(ncol), _ptr(d_B), _ptr(d_X), int(bool(x0)),
-                                  float(lin_tol), int(max_iters), int(precision), C.byref(it))
+                                  float(lin_tol), int(max_iters), int(precision), int(precond), C.byref(it))
     _check(rc, "gcie_shifted_solve", allow=(5,) if allow_noconv else ())
     return int(it.value), rc
 

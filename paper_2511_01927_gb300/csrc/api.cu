@@ -9,7 +9,7 @@
 #include <string>
 #include <vector>
 
-#include "kernels.cuh"
+#include "amg.cuh"
 
 namespace gcie {
 
@@ -207,6 +207,7 @@ void gcie_default_opts(gcie_opts *o)
     o->alpha = 0.0;
     o->seed = 1;
     o->expected_count = -1;
+    o->precond = 1;
 }
 
 int gcie_create(gcie_ctx **out, int device, void *stream)
@@ -408,6 +409,7 @@ void gcie_pencil_destroy(gcie_pencil *p)
     if (p->ctx) cudaStreamSynchronize(p->ctx->stream);
     cudaFree(p->rowptr); cudaFree(p->col); cudaFree(p->k32); cudaFree(p->m32); cudaFree(p->k64); cudaFree(p->m64);
     cudaFree(p->dsc); cudaFree(p->k32s); cudaFree(p->m32s); cudaFree(p->k64s); cudaFree(p->m64s);
+    amg_destroy(p->amg);
     delete p;
 }
 
@@ -460,7 +462,8 @@ int gcie_shifted_spmm_f64(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const dou
 }
 
 int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const double *d_B,
-                       double *d_X, int32_t x0, double lin_tol, int32_t max_iters, int32_t precision, int64_t *h_iters)
+                       double *d_X, int32_t x0, double lin_tol, int32_t max_iters, int32_t precision, int32_t precond,
+                       int64_t *h_iters)
 {
     if (!c || !p || !h_z || !d_B || !d_X || nshift <= 0 || ncol <= 0 || !(lin_tol > 0) || max_iters < 0) {
         set_error("shifted_solve: bad argument");
@@ -471,7 +474,7 @@ int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double
     std::vector<int> rhs(nshift, 0);
     SolveInfo info;
     int rc = cocg_solve(c, p, nshift, h_z, rhs.data(), 1, ncol, d_B, (double2 *)d_X, x0 != 0, lin_tol, max_iters,
-                        precision, &info);
+                        precision, precond, &info);
     if (h_iters) *h_iters = info.iters;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
@@ -743,7 +746,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             }
             SolveInfo info;
             int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
-                                 o->precision, &info);
+                                 o->precision, o->precond, &info);
             cocg_iters += info.iters;
             if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
             // per contour: moments, basis, Rayleigh-Ritz, keep

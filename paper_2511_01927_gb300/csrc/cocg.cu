@@ -25,7 +25,7 @@
 #include <algorithm>
 #include <cmath>
 
-#include "kernels.cuh"
+#include "amg.cuh"
 
 namespace gcie {
 
@@ -329,7 +329,8 @@ __global__ void k_scal_alpha(int ncol, int chunks, Scal S)
     S.alpha[sc] = a;
 }
 
-__global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double tol2, int max_since)
+__global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int rho_chunks,
+                            double delta2, double tol2, int max_since)
 {
     __shared__ int all_want;
     const int s = blockIdx.x, l = threadIdx.x;
@@ -343,11 +344,10 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double 
         if (f & F_ACTIVE) {
             double2 rho = make_double2(0, 0);
             double eta = 0;
-            for (int c = 0; c < chunks; ++c) {
-                int64_t idx = ((int64_t)s * chunks + c) * ncol + l;
-                double2 v = S.partA[idx];
+            for (int c = 0; c < chunks; ++c) eta += S.partB[((int64_t)s * chunks + c) * ncol + l];
+            for (int c = 0; c < rho_chunks; ++c) {
+                double2 v = rho_part[((int64_t)s * rho_chunks + c) * ncol + l];
                 rho.x += v.x; rho.y += v.y;
-                eta += S.partB[idx];
             }
             double2 ro = S.rho[sc];
             double2 b = make_double2(0, 0);
@@ -376,7 +376,8 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, double delta2, double 
 
 // After the update: absolute residual norms decide convergence; the scaled system restarts at
 // eta = eta_abs / scale^2 with the new scale.
-__global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
+__global__ void k_scal_refine(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int rho_chunks,
+                              double tol2)
 {
     __shared__ int any_active;
     const int s = blockIdx.x, l = threadIdx.x;
@@ -387,11 +388,10 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
         const int64_t sc = (int64_t)s * ncol + l;
         double2 rho = make_double2(0, 0);
         double eta_abs = 0;
-        for (int c = 0; c < chunks; ++c) {
-            int64_t idx = ((int64_t)s * chunks + c) * ncol + l;
-            double2 v = S.partA[idx];
+        for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
+        for (int c = 0; c < rho_chunks; ++c) {
+            double2 v = rho_part[((int64_t)s * rho_chunks + c) * ncol + l];
             rho.x += v.x; rho.y += v.y;
-            eta_abs += S.partB[idx];
         }
         int f = S.flag[sc];
         const double sn = S.scale_next[sc];
@@ -481,7 +481,8 @@ __global__ void k_scale_rows(int64_t n, int ncol, int64_t nblk, int ncomp, const
 // ------------------------------------------------------------------ host driver
 template <typename T>
 static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
-                   const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, SolveInfo *info)
+                   const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, const Amg *amg,
+                   SolveInfo *info)
 {
     using C = typename cplx<T>::t;
     constexpr int CPT = sizeof(T) == 4 ? 2 : 1;
@@ -500,7 +501,10 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                             ns * sizeof(double), ns * sizeof(int), nshift * sizeof(int), nshift * sizeof(int),
                             nshift * sizeof(int), (size_t)nshift * maxch * ncol * sizeof(double2),
                             (size_t)nshift * maxch * ncol * sizeof(double), nshift * sizeof(double2),
-                            nshift * sizeof(int)};
+                            nshift * sizeof(int),
+                            // preconditioned iteration: z, two fine-level cycle blocks, r^T z partials
+                            amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0,
+                            amg ? (size_t)nshift * maxch * ncol * sizeof(double2) : 0};
     size_t bytes = 0;
     for (size_t b : sizes) bytes += (b + 255) & ~(size_t)255;
     char *base = nullptr;
@@ -533,6 +537,14 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     S.partB = (double *)take();
     double2 *d_z = (double2 *)take();
     int *d_rhs = (int *)take();
+    C *Zp = (C *)take();
+    C *R1 = (C *)take();
+    C *XF = (C *)take();
+    double2 *partC = (double2 *)take();
+    AmgWork<T> aw;
+    // the direction sweep reads the preconditioned residual z (= r without preconditioner)
+    C *Zdir = amg ? Zp : R;
+    double2 *rho_part = amg ? partC : S.partA;
 
     int rc = GCIE_OK;
     std::vector<double2> hz(nshift);
@@ -552,6 +564,10 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     int active_shifts = nshift;
 
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), nshift * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+    if (amg) {
+        rc = aw.init(c, amg, nshift, ncol, d_z);
+        if (rc) { aw.release(); cudaFreeAsync(base, c->stream); return rc; }
+    }
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_rhs, h_rhs_of, nshift * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     GCIE_CUDA_TRY(cudaMemsetAsync(D, 0, blk * sizeof(C), c->stream));
     GCIE_CUDA_TRY(cudaMemsetAsync(P[0], 0, blk * sizeof(C), c->stream));
@@ -587,9 +603,10 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         GCIE_TRY(refine_r(nact, 0));
+        if (amg) GCIE_TRY(aw.apply(S.shift_refine, R, R1, XF, Zp, partC, nact));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2);
+            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, rho_part, amg ? g.chunks : gr.chunks, tol2);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         return GCIE_OK;
@@ -619,7 +636,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                     LaunchScope ls(c, GCIE_K_SPMM_DIR, (double)active_shifts * (n * ncol * 3 * esz + mat),
                                    (double)active_shifts * p->nnz * ncol * 12.0);
                     k_dir<T, CPT><<<ntiles, g.threads, smem, c->stream>>>(n, p->rowptr, p->col, kv, mv, d_z, ncol,
-                        g.rows_per_chunk, g.chunks, S.shift_active, S.beta, R, Pold, Pnew, S.partA);
+                        g.rows_per_chunk, g.chunks, S.shift_active, S.beta, Zdir, Pold, Pnew, S.partA);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 {
@@ -634,9 +651,14 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                         g.rows_per_chunk, g.chunks, S.shift_active, S.alpha, Pnew, D, R, S.partA, S.partB);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
+                if (amg) {
+                    rc = aw.apply(S.shift_active, R, R1, XF, Zp, partC, active_shifts);
+                    if (rc) goto done;
+                }
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-                    k_scal_beta<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, delta2, tol2, max_since);
+                    k_scal_beta<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, rho_part, g.chunks, delta2, tol2,
+                                                                    max_since);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 rc = refine(0);
@@ -666,12 +688,14 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         }
     }
 done:
+    if (amg) aw.release();
     cudaFreeAsync(base, c->stream);
     return rc;
 }
 
-int cocg_solve(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
-               const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, int precision, SolveInfo *info)
+int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
+               const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, int precision, int precond,
+               SolveInfo *info)
 {
     if (nshift <= 0) return GCIE_OK;
     for (int s = 0; s < nshift; ++s)
@@ -693,10 +717,20 @@ int cocg_solve(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int
                                                                                   (const double *)d_X, (double *)d_X);
         if (cudaGetLastError() != cudaSuccess) rc = GCIE_ECUDA;
     }
+    const Amg *amg = nullptr;
+    if (rc == GCIE_OK && precond) {
+        if (!p->amg && !p->amg_failed) {
+            Amg *a = nullptr;
+            // a pencil too small or too irregular for a hierarchy is solved without preconditioner
+            if (amg_build(c, p, AmgParams(), &a) == GCIE_OK) p->amg = a;
+            else p->amg_failed = true;
+        }
+        amg = p->amg;
+    }
     if (rc == GCIE_OK)
         rc = precision == GCIE_FP64
-                 ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, info)
-                 : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, info);
+                 ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg, info)
+                 : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg, info);
     if (rc == GCIE_OK || rc == GCIE_ENOCONV) {
         LaunchScope ls(c, GCIE_K_OTHER, 32.0 * nshift * n * ncol, 0);
         k_scale_rows<<<grid((int64_t)nshift * n * ncol * 2), 256, 0, c->stream>>>(n, ncol, nshift, 2, p->dsc, 0,

@@ -65,6 +65,8 @@ struct Pencil {
     double *dsc = nullptr;           // n: D^-1/2
     float *k32s = nullptr, *m32s = nullptr;
     double *k64s = nullptr, *m64s = nullptr;
+    struct Amg *amg = nullptr;       // multigrid hierarchy of the scaled pencil (built on first use)
+    bool amg_failed = false;
     // host copies (union pattern, symmetrised) for the host-side de-duplication
     std::vector<int64_t> h_rowptr;
     std::vector<int32_t> h_col;

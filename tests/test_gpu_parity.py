@@ -94,8 +94,8 @@ def test_shifted_spmm_f64(G, ctx, small2d, ncol):
 
 # --------------------------------------------------------------------------- a4-a6: shifted solves
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_shifted_solve_matches_lu(G, ctx, small2d, precision):
+@pytest.mark.parametrize("precision,precond", [(0, 1), (1, 1), (0, 0), (1, 0)])
+def test_shifted_solve_matches_lu(G, ctx, small2d, precision, precond):
     K, M, spec, pen = small2d
     lo, hi = spec["lo"], spec["hi"]
     c, R = 0.5 * (lo + hi), 0.5 * (hi - lo)
@@ -107,9 +107,11 @@ def test_shifted_solve_matches_lu(G, ctx, small2d, precision):
     dB = dev(B)
     dX = torch.zeros((len(z), K.n, ncol), dtype=torch.complex128, device="cuda")
     lin_tol = 1e-11
-    iters, rc = G.gcie_shifted_solve(ctx, pen, z, ncol, dB, dX, lin_tol=lin_tol, precision=precision)
+    iters, rc = G.gcie_shifted_solve(ctx, pen, z, ncol, dB, dX, lin_tol=lin_tol, precision=precision, precond=precond)
     X = host(dX)
     assert iters > 0
+    if precond:
+        assert iters < 300          # the multigrid cycle keeps the iteration count small
     # the stopping test is on the symmetrically scaled system D^-1/2 (zM - K) D^-1/2 with D = diag(K)
     dsc = 1.0 / np.sqrt(K.to_scipy().diagonal())
     for s, zs in enumerate(z):
