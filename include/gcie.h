@@ -49,6 +49,8 @@ enum {
 };
 
 enum { GCIE_MIXED = 0, GCIE_FP64 = 1 };   /* precision of the shifted solves */
+/* preconditioner of the shifted solves */
+enum { GCIE_PREC_NONE = 0, GCIE_PREC_AUTO = 1, GCIE_PREC_AMG = 2, GCIE_PREC_BAND = 3 };
 
 /* Sparse matrix in CSR form, host memory: 0-based, column indices sorted and unique within a
  * row, both triangles stored, n >= 1, rowptr[0] = 0, rowptr[n] = nnz. */
@@ -85,7 +87,8 @@ typedef struct {
     size_t hbm_budget_bytes;/* device memory the solve may use (0: 90% of free memory) */
     int32_t expected_count; /* >= 0: return GCIE_ECOUNT if the merged count differs; -1: off */
     int32_t profile;        /* 1: time every kernel launch with CUDA events (see gcie_stats) */
-    int32_t precond;        /* 1 (default): multigrid-preconditioned COCG; 0: plain COCG */
+    int32_t precond;        /* GCIE_PREC_AUTO (default): banded LDL^T factors when the bandwidth
+                               allows (mixed precision), else the multigrid cycle; or a GCIE_PREC_* */
 } gcie_opts;
 
 /* Results: library-allocated host arrays, released by gcie_result_free. */
@@ -182,9 +185,12 @@ int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const d
  * scaled system D^-1/2 (z_s M - K) D^-1/2 (D = diag K, or diag M if some K_ii <= 0), to
  * ||D^-1/2 (B - A X[s])||_2 / ||D^-1/2 B||_2 <= lin_tol per column.
  * d_B: FP64 real n x ncol row-major (shared by all shifts); d_X: FP64 complex, nshift blocks of
- * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  precond = 1 applies the
- * multigrid V-cycle preconditioner (built from K and M on the first call for this pencil and kept
- * with it), 0 runs plain COCG.  h_iters (host, may be NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
+ * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  precond: a GCIE_PREC_*
+ * value; GCIE_PREC_BAND factors every shifted matrix as a complex-symmetric band L D L^T in FP32 and
+ * uses the factors as the COCG preconditioner (mixed precision, bandwidth limited by shared memory),
+ * GCIE_PREC_AMG applies the multigrid V-cycle (hierarchy built on the first call for this pencil and
+ * kept with it), GCIE_PREC_AUTO picks the band factors when possible, GCIE_PREC_NONE runs plain COCG.
+ * h_iters (host, may be NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
  * within max_iters (d_X then holds the best iterate). */
 int gcie_shifted_solve(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
                        int32_t ncol, const double *d_B, double *d_X, int32_t x0, double lin_tol,

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "amg.cuh"
+#include "ldlt.cuh"
 
 namespace gcie {
 
@@ -474,7 +475,7 @@ int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double
     std::vector<int> rhs(nshift, 0);
     SolveInfo info;
     int rc = cocg_solve(c, p, nshift, h_z, rhs.data(), 1, ncol, d_B, (double2 *)d_X, x0 != 0, lin_tol, max_iters,
-                        precision, precond, &info);
+                        precision, precond, nullptr, &info);
     if (h_iters) *h_iters = info.iters;
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
@@ -663,6 +664,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     const size_t budget = o->hbm_budget_bytes ? o->hbm_budget_bytes : (size_t)(0.85 * free_b);
     const size_t esz = o->precision == GCIE_FP64 ? 16 : 8;
     int64_t cocg_iters = 0;
+    BandCache bands;   // band factors of the nodes, reused by the later FEAST iterations
 
     for (int it = 0; it < o->max_outer; ++it) {
         std::vector<int> act;
@@ -677,7 +679,12 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             while (b1 < act.size()) {
                 int nn = std::max(ncol, cs[act[b1]].ncol);
                 nn += nn & 1;
-                const size_t per = (size_t)half * n * nn * (4 * esz + 16) + (size_t)n * nn * 8 * 4;
+                // per contour: COCG blocks (7 with a preconditioner), the FP64 iterate, moments and
+                // basis blocks, and FP32 band factors of its nodes
+                const bool band = o->precision == GCIE_MIXED && o->precond != GCIE_PREC_NONE &&
+                                  o->precond != GCIE_PREC_AMG && band_feasible(c, p->bw);
+                const size_t per = (size_t)half * n * nn * (7 * esz + 16) + (size_t)n * nn * 8 * 4 +
+                                   (band ? (size_t)half * n * (p->bw + 1) * 8 : 0);
                 if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
                 ncol = nn;
                 ++b1;
@@ -746,7 +753,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             }
             SolveInfo info;
             int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
-                                 o->precision, o->precond, &info);
+                                 o->precision, o->precond, &bands, &info);
             cocg_iters += info.iters;
             if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
             // per contour: moments, basis, Rayleigh-Ritz, keep
@@ -918,7 +925,8 @@ int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const g
     if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi)) { set_error("solve: need finite lo < hi"); return GCIE_EINVAL; }
     if (o.nodes < 2 || o.nodes > 64 || o.nodes % 2 || o.L < 1 || o.moments < 1 || o.moments > 8 || o.max_outer < 1 ||
         o.max_iters < 1 || !(o.tol > 0) || !(o.lin_tol > 0) || (o.precision != GCIE_MIXED && o.precision != GCIE_FP64) ||
-        o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0) {
+        o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0 ||
+        o.precond < GCIE_PREC_NONE || o.precond > GCIE_PREC_BAND) {
         set_error("solve: option out of range");
         return GCIE_EINVAL;
     }

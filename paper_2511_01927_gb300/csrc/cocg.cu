@@ -26,6 +26,7 @@
 #include <cmath>
 
 #include "amg.cuh"
+#include "ldlt.cuh"
 
 namespace gcie {
 
@@ -482,8 +483,9 @@ __global__ void k_scale_rows(int64_t n, int ncol, int64_t nblk, int ncomp, const
 template <typename T>
 static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
                    const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, const Amg *amg,
-                   SolveInfo *info)
+                   float2 *const *bandAB, SolveInfo *info)
 {
+    const bool prec = amg != nullptr || bandAB != nullptr;
     using C = typename cplx<T>::t;
     constexpr int CPT = sizeof(T) == 4 ? 2 : 1;
     const int64_t n = p->n;
@@ -503,8 +505,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                             (size_t)nshift * maxch * ncol * sizeof(double), nshift * sizeof(double2),
                             nshift * sizeof(int),
                             // preconditioned iteration: z, two fine-level cycle blocks, r^T z partials
-                            amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0,
-                            amg ? (size_t)nshift * maxch * ncol * sizeof(double2) : 0};
+                            prec ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0,
+                            prec ? (size_t)nshift * maxch * ncol * sizeof(double2) : 0};
     size_t bytes = 0;
     for (size_t b : sizes) bytes += (b + 255) & ~(size_t)255;
     char *base = nullptr;
@@ -543,8 +545,19 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     double2 *partC = (double2 *)take();
     AmgWork<T> aw;
     // the direction sweep reads the preconditioned residual z (= r without preconditioner)
-    C *Zdir = amg ? Zp : R;
-    double2 *rho_part = amg ? partC : S.partA;
+    C *Zdir = prec ? Zp : R;
+    double2 *rho_part = prec ? partC : S.partA;
+    // preconditioner application z = M^-1 r on the masked shifts, with the partial sums of r^T z
+    auto apply_prec = [&](const int *mask, int nact) -> int {
+        if (amg) return aw.apply(mask, R, R1, XF, Zp, partC, nact);
+        if constexpr (sizeof(T) == 4) {
+            GCIE_TRY(band_apply(c, p, nshift, ncol, mask, bandAB, (const float2 *)R, (float2 *)Zp, nact));
+            return rz_partials(c, n, nshift, ncol, g.rows_per_chunk, g.chunks, mask, (const float2 *)R, (const float2 *)Zp,
+                               partC, nact);
+        }
+        set_error("band preconditioner needs the mixed-precision solver");
+        return GCIE_EINVAL;
+    };
 
     int rc = GCIE_OK;
     std::vector<double2> hz(nshift);
@@ -603,10 +616,10 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         GCIE_TRY(refine_r(nact, 0));
-        if (amg) GCIE_TRY(aw.apply(S.shift_refine, R, R1, XF, Zp, partC, nact));
+        if (prec) GCIE_TRY(apply_prec(S.shift_refine, nact));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, rho_part, amg ? g.chunks : gr.chunks, tol2);
+            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, rho_part, prec ? g.chunks : gr.chunks, tol2);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         return GCIE_OK;
@@ -651,8 +664,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                         g.rows_per_chunk, g.chunks, S.shift_active, S.alpha, Pnew, D, R, S.partA, S.partB);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
-                if (amg) {
-                    rc = aw.apply(S.shift_active, R, R1, XF, Zp, partC, active_shifts);
+                if (prec) {
+                    rc = apply_prec(S.shift_active, active_shifts);
                     if (rc) goto done;
                 }
                 {
@@ -695,7 +708,7 @@ done:
 
 int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
                const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters, int precision, int precond,
-               SolveInfo *info)
+               BandCache *cache, SolveInfo *info)
 {
     if (nshift <= 0) return GCIE_OK;
     for (int s = 0; s < nshift; ++s)
@@ -717,8 +730,16 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
                                                                                   (const double *)d_X, (double *)d_X);
         if (cudaGetLastError() != cudaSuccess) rc = GCIE_ECUDA;
     }
+    // preconditioner: banded LDL^T when the band fits the shared-memory kernels (mixed precision),
+    // otherwise the multigrid cycle
     const Amg *amg = nullptr;
-    if (rc == GCIE_OK && precond) {
+    float2 **bandAB = nullptr;
+    BandCache local;
+    const bool use_band = precision == GCIE_MIXED && (precond == GCIE_PREC_BAND || precond == GCIE_PREC_AUTO) &&
+                          band_feasible(c, p->bw);
+    if (rc == GCIE_OK && use_band) {
+        rc = (cache ? cache : &local)->get(c, p, nshift, h_z, &bandAB);
+    } else if (rc == GCIE_OK && (precond == GCIE_PREC_AMG || precond == GCIE_PREC_AUTO)) {
         if (!p->amg && !p->amg_failed) {
             Amg *a = nullptr;
             // a pencil too small or too irregular for a hierarchy is solved without preconditioner
@@ -726,11 +747,17 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
             else p->amg_failed = true;
         }
         amg = p->amg;
+    } else if (rc == GCIE_OK && precond == GCIE_PREC_BAND) {
+        set_error("band preconditioner: bandwidth too large or FP64 mode");
+        rc = GCIE_EINVAL;
     }
     if (rc == GCIE_OK)
         rc = precision == GCIE_FP64
-                 ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg, info)
-                 : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg, info);
+                 ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
+                                   nullptr, info)
+                 : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
+                                  bandAB, info);
+    if (bandAB) cudaFreeAsync(bandAB, c->stream);
     if (rc == GCIE_OK || rc == GCIE_ENOCONV) {
         LaunchScope ls(c, GCIE_K_OTHER, 32.0 * nshift * n * ncol, 0);
         k_scale_rows<<<grid((int64_t)nshift * n * ncol * 2), 256, 0, c->stream>>>(n, ncol, nshift, 2, p->dsc, 0,

@@ -29,9 +29,10 @@ struct SolveInfo {
     int unconverged_cols = 0;
     int breakdowns = 0;
 };
+struct BandCache;
 int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs,
                int ncol, const double *d_B, double2 *d_X, bool x0, double lin_tol, int max_iters,
-               int precision, int precond, SolveInfo *info);
+               int precision, int precond, BandCache *cache, SolveInfo *info);
 
 // a7: S[:, k*ncol + l] += 2 Re( coef[s][k] X[s][:, l] ), coef[s][k] = w_s ((z_s - c)/r)^k, summed over
 // s < nshift; S is n x (m*ncol) row-major (leading dimension ldS >= m*ncol).

@@ -1,0 +1,467 @@
+// Banded complex-symmetric LDL^T of the shifted matrices, used as the preconditioner of COCG.
+//
+// For every node z_s the (diagonally scaled) matrix A_s = z_s M - K is complex symmetric with
+// positive definite imaginary part (Im z_s > 0, M > 0), so all leading principal minors are
+// nonzero and A_s = L D L^T exists without pivoting.  FEM pencils ordered along a grid have a
+// narrow band (2D: about sqrt(n)), where the factorization costs n b^2 / 2 complex multiply-adds
+// and the two triangular sweeps 2 n b per right-hand side.  The factors are computed in FP32:
+// COCG preconditioned with them reaches the FP64 tolerance (with the residual refinement) in a
+// few iterations, and they depend only on the node, so one factorization serves every FEAST
+// iteration.
+//
+// Storage: per shift, column-oriented band AB[j][t] = A[j + t][j] for t = 0..b (b + 1 complex
+// values per column), so column j of L is contiguous.  After the factorization AB[j][0] = d_j
+// and AB[j][t] = l_{j+t, j}.
+//
+// Kernels (one CTA per shift for the factorization, nshift x column groups for the sweeps):
+//   k_band_assemble  A_s from the union CSR pattern;
+//   k_band_ldlt      right-looking factorization by panels of NB columns: the panel (NB + b rows)
+//                    is factored in shared memory, then the trailing b x b triangle receives the
+//                    rank-NB update L_p D_p L_p^T (tiles of 4 x 4 per thread);
+//   k_band_solve     z = L^-T D^-1 L^-1 r for a group of right-hand sides, with a sliding window of
+//                    b + NB rows in shared memory for each sweep.
+#include <algorithm>
+#include <cmath>
+
+#include "ldlt.cuh"
+
+namespace gcie {
+
+constexpr int NB = 16;        // panel / block width
+constexpr int SOLVE_COLS = 8; // right-hand sides per CTA in the sweeps
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+__device__ __forceinline__ float2 cdivf(float2 a, float2 b)
+{
+    const float den = b.x * b.x + b.y * b.y;
+    return make_float2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
+}
+
+// ------------------------------------------------------------------ assembly
+__global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
+                                const double *__restrict__ kv, const double *__restrict__ mv,
+                                const double2 *__restrict__ z, int nshift, int b, float2 *const *__restrict__ ABp)
+{
+    const int64_t B1 = b + 1;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+            const int64_t j = col[k];
+            if (j > i || i - j > b) continue;
+            const double a = kv[k], m = mv[k];
+            for (int s = 0; s < nshift; ++s) {
+                const double2 zs = z[s];
+                ABp[s][j * B1 + (i - j)] = make_float2((float)(zs.x * m - a), (float)(zs.y * m));
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------ factorization
+// smem: P[(NB + b) x NB] panel (row-major: P[t * NB + c] = A[p0 + t][p0 + c]), W[b x NB] = P D,
+// D[NB].
+__global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp,
+                                                    int *__restrict__ status)
+{
+    extern __shared__ float2 sm2[];
+    const int64_t B1 = b + 1;
+    float2 *AB = ABp[blockIdx.x];
+    const int R = NB + b;
+    float2 *P = sm2;                 // R x NB
+    float2 *W = P + (size_t)R * NB;  // b x NB
+    float2 *D = W + (size_t)b * NB;  // NB
+    const int tid = threadIdx.x, nth = blockDim.x;
+    for (int64_t p0 = 0; p0 < n; p0 += NB) {
+        const int nc = (int)min((int64_t)NB, n - p0);
+        const int rows = (int)min((int64_t)R, n - p0);   // local rows present
+        // load the panel (zeros outside the band / matrix)
+        for (int e = tid; e < R * NB; e += nth) {
+            const int t = e / NB, c = e % NB;
+            float2 v = make_float2(0.f, 0.f);
+            if (c < nc && t >= c && t < rows && t - c <= b) v = AB[(p0 + c) * B1 + (t - c)];
+            P[e] = v;
+        }
+        __syncthreads();
+        // factor the panel column by column
+        for (int c = 0; c < nc; ++c) {
+            const float2 d = P[c * NB + c];
+            if (tid == 0) {
+                D[c] = d;
+                if (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)) atomicExch(status, 1);
+            }
+            const int tmax = min(rows - 1, c + b);
+            // multipliers l_tc = a_tc / d
+            for (int t = c + 1 + tid; t <= tmax; t += nth) P[t * NB + c] = cdivf(P[t * NB + c], d);
+            __syncthreads();
+            // update the remaining panel columns: a_{t,c2} -= l_tc d l_{c2,c}, c < c2 <= t
+            const int ncol2 = nc - c - 1;
+            if (ncol2 > 0) {
+                const int nrow2 = tmax - c;   // rows c+1..tmax
+                for (int e = tid; e < nrow2 * ncol2; e += nth) {
+                    const int t = c + 1 + e / ncol2, c2 = c + 1 + e % ncol2;
+                    if (c2 > t) continue;
+                    const float2 w = cmulf(d, P[c2 * NB + c]);
+                    const float2 l = P[t * NB + c];
+                    float2 v = P[t * NB + c2];
+                    v.x -= l.x * w.x - l.y * w.y;
+                    v.y -= l.x * w.y + l.y * w.x;
+                    P[t * NB + c2] = v;
+                }
+            }
+            __syncthreads();
+        }
+        // write the panel back: D on the diagonal, L below
+        for (int e = tid; e < R * NB; e += nth) {
+            const int t = e / NB, c = e % NB;
+            if (c < nc && t >= c && t < rows && t - c <= b) AB[(p0 + c) * B1 + (t - c)] = t == c ? D[c] : P[e];
+        }
+        // W = rows NB..NB+b-1 of the panel times D (for the trailing update)
+        for (int e = tid; e < b * NB; e += nth) {
+            const int t = NB + e / NB, c = e % NB;
+            W[e] = (c < nc && t < rows) ? cmulf(P[t * NB + c], D[c]) : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        // trailing update of the b x b lower triangle at (p0 + NB, p0 + NB):
+        // A[i][j] -= sum_c L[i][c] d_c L[j][c] for i >= j, i - j <= b
+        if (nc == NB) {
+            const int tr = min((int64_t)b, n - p0 - NB);   // trailing rows present
+            const int nt = (tr + 3) / 4;
+            const int ntile = nt * (nt + 1) / 2;
+            for (int tile = tid; tile < ntile; tile += nth) {
+                // tile -> (ti, tj) with tj <= ti (row-major lower triangle)
+                int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
+                while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
+                while (ti * (ti + 1) / 2 > tile) --ti;
+                const int tj = tile - ti * (ti + 1) / 2;
+                float2 acc[4][4];
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+                for (int c = 0; c < NB; ++c) {
+                    float2 li[4], wj[4];
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int I = 4 * ti + a, J = 4 * tj + a;
+                        li[a] = I < tr ? P[(NB + I) * NB + c] : make_float2(0.f, 0.f);
+                        wj[a] = J < tr ? W[J * NB + c] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int a = 0; a < 4; ++a)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            acc[a][q].x += li[a].x * wj[q].x - li[a].y * wj[q].y;
+                            acc[a][q].y += li[a].x * wj[q].y + li[a].y * wj[q].x;
+                        }
+                }
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int J = 4 * tj + q;
+                    if (J >= tr) continue;
+                    const int64_t j = p0 + NB + J;
+#pragma unroll
+                    for (int a = 0; a < 4; ++a) {
+                        const int I = 4 * ti + a;
+                        if (I >= tr || I < J || I - J > b) continue;
+                        float2 *pv = AB + j * B1 + (I - J);
+                        float2 v = *pv;
+                        v.x -= acc[a][q].x;
+                        v.y -= acc[a][q].y;
+                        *pv = v;
+                    }
+                }
+            }
+        } else {
+            // last (partial) panel: nothing below it
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------ triangular sweeps
+// z = L^-T D^-1 L^-1 r for columns [c0, c0 + SOLVE_COLS) of shift s.  Y: window of b + NB rows.
+__global__ void __launch_bounds__(256) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
+        const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
+{
+    extern __shared__ float2 sm2[];
+    const int ngrp = (ncol + SOLVE_COLS - 1) / SOLVE_COLS;
+    const int s = blockIdx.x / ngrp, g = blockIdx.x % ngrp;
+    if (!mask[s]) return;
+    const int c0 = g * SOLVE_COLS;
+    const int nrc = min(SOLVE_COLS, ncol - c0);
+    const int64_t B1 = b + 1;
+    const float2 *AB = ABp[s];
+    const float2 *Rs = Rall + (int64_t)s * n * ncol;
+    float2 *Zs = Zall + (int64_t)s * n * ncol;
+    const int WR = b + NB;                       // window rows
+    float2 *Y = sm2;                             // WR x SOLVE_COLS (row slot = row mod WR)
+    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;    // NB x B1: columns of L of the current block
+    const int tid = threadIdx.x, nth = blockDim.x;
+    auto slot = [&](int64_t i) { return (int)(i % WR); };
+
+    // ---------------- forward: L y = r, then y /= d (written to Z)
+    for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
+        const int t = e / SOLVE_COLS, c = e % SOLVE_COLS;
+        Y[e] = (t < n && c < nrc) ? Rs[(int64_t)t * ncol + c0 + c] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t blk = 0; blk < n; blk += NB) {
+        const int nb = (int)min((int64_t)NB, n - blk);
+        for (int e = tid; e < nb * (int)B1; e += nth) {
+            const int c = e / (int)B1, t = e % (int)B1;
+            Lb[e] = AB[(blk + c) * B1 + t];
+        }
+        __syncthreads();
+        // within the block (sequential over columns)
+        for (int c = 0; c < nb; ++c) {
+            for (int e = tid; e < (nb - c - 1) * SOLVE_COLS; e += nth) {
+                const int c2 = c + 1 + e / SOLVE_COLS, q = e % SOLVE_COLS;
+                if (c2 - c > b) continue;
+                const float2 l = Lb[c * B1 + (c2 - c)];
+                const float2 y = Y[slot(blk + c) * SOLVE_COLS + q];
+                float2 &v = Y[slot(blk + c2) * SOLVE_COLS + q];
+                v.x -= l.x * y.x - l.y * y.y;
+                v.y -= l.x * y.y + l.y * y.x;
+            }
+            __syncthreads();
+        }
+        // rows below the block inside the band
+        const int64_t rlo = blk + nb, rhi = min(n, blk + nb + b);   // [rlo, rhi)
+        for (int e = tid; e < (int)(rhi - rlo) * SOLVE_COLS; e += nth) {
+            const int64_t i = rlo + e / SOLVE_COLS;
+            const int q = e % SOLVE_COLS;
+            float2 acc = make_float2(0.f, 0.f);
+            for (int c = 0; c < nb; ++c) {
+                const int64_t t = i - (blk + c);
+                if (t > b) continue;
+                const float2 l = Lb[c * B1 + t];
+                const float2 y = Y[slot(blk + c) * SOLVE_COLS + q];
+                acc.x += l.x * y.x - l.y * y.y;
+                acc.y += l.x * y.y + l.y * y.x;
+            }
+            float2 &v = Y[slot(i) * SOLVE_COLS + q];
+            v.x -= acc.x;
+            v.y -= acc.y;
+        }
+        __syncthreads();
+        // block rows are final: write y / d, load the rows entering the window
+        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int64_t i = blk + c;
+            if (q < nrc) Zs[i * ncol + c0 + q] = cdivf(Y[slot(i) * SOLVE_COLS + q], Lb[c * B1]);
+            const int64_t inew = i + WR;
+            Y[slot(i) * SOLVE_COLS + q] = (inew < n && q < nrc) ? Rs[inew * ncol + c0 + q] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    }
+    // ---------------- backward: L^T x = y' (in place in Z), from the last block up
+    const int64_t lastblk = ((n - 1) / NB) * NB;
+    // window holds rows [blk, blk + WR): load rows [lastblk, n) (the rest are beyond the matrix)
+    for (int e = tid; e < WR * SOLVE_COLS; e += nth) Y[e] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int e = tid; e < (int)(n - lastblk) * SOLVE_COLS; e += nth) {
+        const int64_t i = lastblk + e / SOLVE_COLS;
+        const int q = e % SOLVE_COLS;
+        Y[slot(i) * SOLVE_COLS + q] = q < nrc ? Zs[i * ncol + c0 + q] : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    for (int64_t blk = lastblk; blk >= 0; blk -= NB) {
+        const int nb = (int)min((int64_t)NB, n - blk);
+        for (int e = tid; e < nb * (int)B1; e += nth) {
+            const int c = e / (int)B1, t = e % (int)B1;
+            Lb[e] = AB[(blk + c) * B1 + t];
+        }
+        __syncthreads();
+        // contributions of the rows below the block: x_k -= sum_{i >= blk+nb, i <= k+b} l_ik x_i
+        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int64_t k = blk + c;
+            const int64_t ihi = min(n - 1, k + b);
+            float2 acc = make_float2(0.f, 0.f);
+            for (int64_t i = blk + nb; i <= ihi; ++i) {
+                const float2 l = Lb[c * B1 + (i - k)];
+                const float2 x = Y[slot(i) * SOLVE_COLS + q];
+                acc.x += l.x * x.x - l.y * x.y;
+                acc.y += l.x * x.y + l.y * x.x;
+            }
+            float2 &v = Y[slot(k) * SOLVE_COLS + q];
+            v.x -= acc.x;
+            v.y -= acc.y;
+        }
+        __syncthreads();
+        // within the block, from the bottom
+        for (int c = nb - 1; c >= 0; --c) {
+            // x_{blk+c} is final; remove it from the rows above within the block
+            for (int e = tid; e < c * SOLVE_COLS; e += nth) {
+                const int c2 = e / SOLVE_COLS, q = e % SOLVE_COLS;
+                if (c - c2 > b) continue;
+                const float2 l = Lb[c2 * B1 + (c - c2)];
+                const float2 x = Y[slot(blk + c) * SOLVE_COLS + q];
+                float2 &v = Y[slot(blk + c2) * SOLVE_COLS + q];
+                v.x -= l.x * x.x - l.y * x.y;
+                v.y -= l.x * x.y + l.y * x.x;
+            }
+            __syncthreads();
+        }
+        // rows leaving the window at the bottom: [blk + WR - NB, blk + WR) ∩ [0, n); rows entering: [blk - NB, blk)
+        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int64_t iout = blk + WR - NB + c;
+            if (iout < n && iout >= blk + nb && q < nrc) Zs[iout * ncol + c0 + q] = Y[slot(iout) * SOLVE_COLS + q];
+        }
+        __syncthreads();
+        if (blk == 0) {
+            // flush every row still in the window
+            for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
+                const int64_t i = e / SOLVE_COLS;
+                const int q = e % SOLVE_COLS;
+                if (i < n && i < WR - NB + blk + nb && q < nrc) Zs[i * ncol + c0 + q] = Y[slot(i) * SOLVE_COLS + q];
+            }
+            break;
+        }
+        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int64_t inew = blk - NB + c;
+            Y[slot(inew) * SOLVE_COLS + q] = q < nrc ? Zs[inew * ncol + c0 + q] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+    }
+}
+
+// partial sums of r^T z (unconjugated) per (shift, chunk, column), geometry of the COCG sweeps
+__global__ void k_rz_partials(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const int *__restrict__ mask,
+                              const float2 *__restrict__ R, const float2 *__restrict__ Z, double2 *__restrict__ part)
+{
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!mask[s]) return;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        for (int64_t i = r0; i < r1; ++i) {
+            const float2 r = R[((int64_t)s * n + i) * ncol + c], z = Z[((int64_t)s * n + i) * ncol + c];
+            re += (double)r.x * z.x - (double)r.y * z.y;
+            im += (double)r.x * z.y + (double)r.y * z.x;
+        }
+        part[((int64_t)s * chunks + ch) * ncol + c] = make_double2(re, im);
+    }
+}
+
+// ------------------------------------------------------------------ host
+BandCache::~BandCache()
+{
+    for (auto &e : entries) cudaFree(e.AB);
+}
+
+// factors for the given shifts (reusing those already computed for identical shift values)
+int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float2 ***d_ptrs_out)
+{
+    std::vector<int> missing;
+    std::vector<float2 *> ptr(nshift, nullptr);
+    for (int s = 0; s < nshift; ++s) {
+        for (auto &e : entries)
+            if (e.z.x == h_z[2 * s] && e.z.y == h_z[2 * s + 1]) { ptr[s] = e.AB; break; }
+        if (!ptr[s]) missing.push_back(s);
+    }
+    const size_t per = sizeof(float2) * (size_t)p->n * (p->bw + 1);
+    if (!missing.empty()) {
+        std::vector<float2 *> newp;
+        std::vector<double2> hz;
+        for (int s : missing) {
+            float2 *q = nullptr;
+            if (cudaMalloc(&q, per) != cudaSuccess) {
+                cudaGetLastError();
+                for (float2 *r : newp) cudaFree(r);
+                set_error("band LDL^T: factor storage allocation failed");
+                return GCIE_ENOMEM;
+            }
+            newp.push_back(q);
+            hz.push_back(make_double2(h_z[2 * s], h_z[2 * s + 1]));
+        }
+        float2 **d_p = nullptr;
+        double2 *d_z = nullptr;
+        GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_p, sizeof(float2 *) * newp.size(), c->stream));
+        GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_z, sizeof(double2) * hz.size(), c->stream));
+        GCIE_CUDA_TRY(cudaMemcpyAsync(d_p, newp.data(), sizeof(float2 *) * newp.size(), cudaMemcpyHostToDevice, c->stream));
+        GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), sizeof(double2) * hz.size(), cudaMemcpyHostToDevice, c->stream));
+        int rc = band_factor(c, p, (int)newp.size(), d_z, d_p, newp);
+        cudaFreeAsync(d_p, c->stream);
+        cudaFreeAsync(d_z, c->stream);
+        if (rc) { for (float2 *r : newp) cudaFree(r); return rc; }
+        for (size_t k = 0; k < missing.size(); ++k) {
+            entries.push_back({hz[k], newp[k]});
+            ptr[missing[k]] = newp[k];
+        }
+    }
+    float2 **d_ptrs = nullptr;
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_ptrs, sizeof(float2 *) * nshift, c->stream));
+    GCIE_CUDA_TRY(cudaMemcpyAsync(d_ptrs, ptr.data(), sizeof(float2 *) * nshift, cudaMemcpyHostToDevice, c->stream));
+    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    *d_ptrs_out = d_ptrs;
+    return GCIE_OK;
+}
+
+size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
+size_t band_smem_solve(int b) { return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + (size_t)NB * (b + 1)); }
+
+bool band_feasible(const Ctx *c, int b)
+{
+    return band_smem_factor(b) <= c->smem_optin && band_smem_solve(b) <= c->smem_optin;
+}
+
+int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
+                const std::vector<float2 *> &h_ABp)
+{
+    const int b = p->bw;
+    const int64_t n = p->n;
+    for (float2 *q : h_ABp) GCIE_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(float2) * (size_t)n * (b + 1), c->stream));
+    {
+        LaunchScope ls(c, GCIE_K_PREC, (double)p->nnz * 20 + (double)nshift * n * (b + 1) * 8, 0);
+        const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
+        k_band_assemble<<<blocks, 256, 0, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z, nshift, b, d_ABp);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    int *d_status = nullptr;
+    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_status, sizeof(int), c->stream));
+    GCIE_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), c->stream));
+    const size_t smem = band_smem_factor(b);
+    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        const double macs = (double)nshift * n * b * (b + 1) / 2.0;
+        LaunchScope ls(c, GCIE_K_PREC, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
+        k_band_ldlt<<<nshift, 1024, smem, c->stream>>>(n, b, d_ABp, d_status);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    int hs = 0;
+    GCIE_CUDA_TRY(cudaMemcpyAsync(&hs, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    cudaFreeAsync(d_status, c->stream);
+    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (hs) { set_error("band LDL^T: zero or non-finite pivot"); return GCIE_EBREAKDOWN; }
+    return GCIE_OK;
+}
+
+int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
+               const float2 *R, float2 *Z, int nact)
+{
+    const int b = p->bw;
+    const int64_t n = p->n;
+    const size_t smem = band_smem_solve(b);
+    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ngrp = (ncol + SOLVE_COLS - 1) / SOLVE_COLS;
+    const double macs = 2.0 * nact * n * b * ncol;
+    LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
+    k_band_solve<<<nshift * ngrp, 256, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
+    GCIE_CUDA_TRY(cudaGetLastError());
+    return GCIE_OK;
+}
+
+int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,
+                const float2 *R, const float2 *Z, double2 *part, int nact)
+{
+    LaunchScope ls(c, GCIE_K_PREC, (double)nact * n * ncol * 16.0, 0);
+    k_rz_partials<<<nshift * chunks, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(n, ncol, rows_per_chunk,
+                                                                                            chunks, mask, R, Z, part);
+    GCIE_CUDA_TRY(cudaGetLastError());
+    return GCIE_OK;
+}
+
+}  // namespace gcie

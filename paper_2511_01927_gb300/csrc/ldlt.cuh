@@ -1,0 +1,28 @@
+// Banded complex-symmetric LDL^T preconditioner of the shifted systems (see ldlt.cu).
+#pragma once
+
+#include "kernels.cuh"
+
+namespace gcie {
+
+// FP32 factors of z M - K (diagonally scaled) per shift value, kept for the duration of a solve
+// so that later FEAST iterations on the same contours reuse them.
+struct BandCache {
+    struct Entry { double2 z; float2 *AB; };
+    std::vector<Entry> entries;
+    // device array of per-shift factor pointers (caller frees it with cudaFreeAsync)
+    int get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float2 ***d_ptrs_out);
+    ~BandCache();
+};
+
+bool band_feasible(const Ctx *c, int b);
+size_t band_smem_factor(int b);
+size_t band_smem_solve(int b);
+int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
+                const std::vector<float2 *> &h_ABp);
+int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
+               const float2 *R, float2 *Z, int nact);
+int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,
+                const float2 *R, const float2 *Z, double2 *part, int nact);
+
+}  // namespace gcie
