@@ -28,7 +28,7 @@
 namespace gcie {
 
 constexpr int NB = 16;        // panel / block width
-constexpr int SOLVE_COLS = 8; // right-hand sides per CTA in the sweeps
+constexpr int SOLVE_COLS = 32; // right-hand sides per CTA in the sweeps
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cdivf(float2 a, float2 b)
@@ -179,8 +179,11 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 }
 
 // ------------------------------------------------------------------ triangular sweeps
-// z = L^-T D^-1 L^-1 r for columns [c0, c0 + SOLVE_COLS) of shift s.  Y: window of b + NB rows.
-__global__ void __launch_bounds__(256) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
+// z = L^-T D^-1 L^-1 r for columns [c0, c0 + SOLVE_COLS) of shift s, 512 threads.  The window Y
+// holds b + NB consecutive rows (slot = row mod (b + NB)); Lb holds the NB columns of L of the
+// current block.  The triangular solve inside a block is done by half-warps (one column each,
+// lane = row of the block) with shuffles; the band parts are block-wide.
+__global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
 {
     extern __shared__ float2 sm2[];
@@ -189,142 +192,144 @@ __global__ void __launch_bounds__(256) k_band_solve(int64_t n, int b, int ncol, 
     if (!mask[s]) return;
     const int c0 = g * SOLVE_COLS;
     const int nrc = min(SOLVE_COLS, ncol - c0);
-    const int64_t B1 = b + 1;
+    const int B1 = b + 1;
     const float2 *AB = ABp[s];
-    const float2 *Rs = Rall + (int64_t)s * n * ncol;
-    float2 *Zs = Zall + (int64_t)s * n * ncol;
-    const int WR = b + NB;                       // window rows
-    float2 *Y = sm2;                             // WR x SOLVE_COLS (row slot = row mod WR)
-    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;    // NB x B1: columns of L of the current block
+    const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
+    float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
+    const int WR = b + NB;
+    float2 *Y = sm2;                                  // WR x SOLVE_COLS
+    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;         // NB x B1
     const int tid = threadIdx.x, nth = blockDim.x;
+    const int lane16 = tid & 15;                      // row of the block handled in the in-block solve
+    const int hw = tid >> 4;                          // half-warp index = column of the in-block solve
+    const int q = tid % SOLVE_COLS;                   // column handled in the band parts
     auto slot = [&](int64_t i) { return (int)(i % WR); };
+    const float2 zero = make_float2(0.f, 0.f);
 
-    // ---------------- forward: L y = r, then y /= d (written to Z)
+    // ---------------- forward: L y = r, then y' = y / d written to Z
     for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
         const int t = e / SOLVE_COLS, c = e % SOLVE_COLS;
-        Y[e] = (t < n && c < nrc) ? Rs[(int64_t)t * ncol + c0 + c] : make_float2(0.f, 0.f);
+        Y[e] = (t < n && c < nrc) ? Rs[(int64_t)t * ncol + c] : zero;
     }
-    __syncthreads();
     for (int64_t blk = 0; blk < n; blk += NB) {
         const int nb = (int)min((int64_t)NB, n - blk);
-        for (int e = tid; e < nb * (int)B1; e += nth) {
-            const int c = e / (int)B1, t = e % (int)B1;
-            Lb[e] = AB[(blk + c) * B1 + t];
+        __syncthreads();
+        for (int e = tid; e < nb * B1; e += nth) Lb[e] = AB[blk * B1 + e];
+        __syncthreads();
+        // in-block: half-warp hw solves column hw (rows blk..blk+nb-1 in lanes)
+        if (hw < SOLVE_COLS) {
+            float2 y = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
+            for (int c = 0; c < nb - 1; ++c) {
+                const float yr = __shfl_sync(0xffffffffu, y.x, c, 16), yi = __shfl_sync(0xffffffffu, y.y, c, 16);
+                if (lane16 > c && lane16 < nb && lane16 - c <= b) {
+                    const float2 l = Lb[c * B1 + (lane16 - c)];
+                    y.x -= l.x * yr - l.y * yi;
+                    y.y -= l.x * yi + l.y * yr;
+                }
+            }
+            if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = y;
         }
         __syncthreads();
-        // within the block (sequential over columns)
-        for (int c = 0; c < nb; ++c) {
-            for (int e = tid; e < (nb - c - 1) * SOLVE_COLS; e += nth) {
-                const int c2 = c + 1 + e / SOLVE_COLS, q = e % SOLVE_COLS;
-                if (c2 - c > b) continue;
-                const float2 l = Lb[c * B1 + (c2 - c)];
-                const float2 y = Y[slot(blk + c) * SOLVE_COLS + q];
-                float2 &v = Y[slot(blk + c2) * SOLVE_COLS + q];
-                v.x -= l.x * y.x - l.y * y.y;
-                v.y -= l.x * y.y + l.y * y.x;
+        // rows below the block inside the band: thread (q, row group) keeps the block's y in registers
+        {
+            float2 yb[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) yb[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q] : zero;
+            const int64_t rlo = blk + nb, rhi = min(n, blk + nb + b);
+            for (int64_t i = rlo + tid / SOLVE_COLS; i < rhi; i += nth / SOLVE_COLS) {
+                float2 acc = zero;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const int64_t t = i - (blk + c);
+                    if (c < nb && t <= b) {
+                        const float2 l = Lb[c * B1 + (int)t];
+                        acc.x += l.x * yb[c].x - l.y * yb[c].y;
+                        acc.y += l.x * yb[c].y + l.y * yb[c].x;
+                    }
+                }
+                float2 &v = Y[slot(i) * SOLVE_COLS + q];
+                v.x -= acc.x;
+                v.y -= acc.y;
             }
-            __syncthreads();
-        }
-        // rows below the block inside the band
-        const int64_t rlo = blk + nb, rhi = min(n, blk + nb + b);   // [rlo, rhi)
-        for (int e = tid; e < (int)(rhi - rlo) * SOLVE_COLS; e += nth) {
-            const int64_t i = rlo + e / SOLVE_COLS;
-            const int q = e % SOLVE_COLS;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int c = 0; c < nb; ++c) {
-                const int64_t t = i - (blk + c);
-                if (t > b) continue;
-                const float2 l = Lb[c * B1 + t];
-                const float2 y = Y[slot(blk + c) * SOLVE_COLS + q];
-                acc.x += l.x * y.x - l.y * y.y;
-                acc.y += l.x * y.y + l.y * y.x;
-            }
-            float2 &v = Y[slot(i) * SOLVE_COLS + q];
-            v.x -= acc.x;
-            v.y -= acc.y;
         }
         __syncthreads();
-        // block rows are final: write y / d, load the rows entering the window
+        // block rows are final: write y / d, load the rows entering the window into their slots
         for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
             const int64_t i = blk + c;
-            if (q < nrc) Zs[i * ncol + c0 + q] = cdivf(Y[slot(i) * SOLVE_COLS + q], Lb[c * B1]);
+            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SOLVE_COLS + qq], Lb[c * B1]);
             const int64_t inew = i + WR;
-            Y[slot(i) * SOLVE_COLS + q] = (inew < n && q < nrc) ? Rs[inew * ncol + c0 + q] : make_float2(0.f, 0.f);
+            Y[slot(i) * SOLVE_COLS + qq] = (inew < n && qq < nrc) ? Rs[inew * ncol + qq] : zero;
         }
-        __syncthreads();
     }
-    // ---------------- backward: L^T x = y' (in place in Z), from the last block up
+    __syncthreads();
+    // ---------------- backward: L^T x = y' (in place in Z), from the last block up; the window holds
+    // rows [blk, blk + WR) at block blk
     const int64_t lastblk = ((n - 1) / NB) * NB;
-    // window holds rows [blk, blk + WR): load rows [lastblk, n) (the rest are beyond the matrix)
-    for (int e = tid; e < WR * SOLVE_COLS; e += nth) Y[e] = make_float2(0.f, 0.f);
+    for (int e = tid; e < WR * SOLVE_COLS; e += nth) Y[e] = zero;
     __syncthreads();
     for (int e = tid; e < (int)(n - lastblk) * SOLVE_COLS; e += nth) {
         const int64_t i = lastblk + e / SOLVE_COLS;
-        const int q = e % SOLVE_COLS;
-        Y[slot(i) * SOLVE_COLS + q] = q < nrc ? Zs[i * ncol + c0 + q] : make_float2(0.f, 0.f);
+        const int qq = e % SOLVE_COLS;
+        Y[slot(i) * SOLVE_COLS + qq] = qq < nrc ? Zs[i * ncol + qq] : zero;
     }
-    __syncthreads();
     for (int64_t blk = lastblk; blk >= 0; blk -= NB) {
         const int nb = (int)min((int64_t)NB, n - blk);
-        for (int e = tid; e < nb * (int)B1; e += nth) {
-            const int c = e / (int)B1, t = e % (int)B1;
-            Lb[e] = AB[(blk + c) * B1 + t];
-        }
         __syncthreads();
-        // contributions of the rows below the block: x_k -= sum_{i >= blk+nb, i <= k+b} l_ik x_i
+        for (int e = tid; e < nb * B1; e += nth) Lb[e] = AB[blk * B1 + e];
+        __syncthreads();
+        // rows below the block: x_k -= sum_{i >= blk + nb, i <= k + b} l_ik x_i, thread = (k, q)
         for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
+            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
             const int64_t k = blk + c;
             const int64_t ihi = min(n - 1, k + b);
-            float2 acc = make_float2(0.f, 0.f);
+            float2 acc = zero;
             for (int64_t i = blk + nb; i <= ihi; ++i) {
-                const float2 l = Lb[c * B1 + (i - k)];
-                const float2 x = Y[slot(i) * SOLVE_COLS + q];
+                const float2 l = Lb[c * B1 + (int)(i - k)];
+                const float2 x = Y[slot(i) * SOLVE_COLS + qq];
                 acc.x += l.x * x.x - l.y * x.y;
                 acc.y += l.x * x.y + l.y * x.x;
             }
-            float2 &v = Y[slot(k) * SOLVE_COLS + q];
+            float2 &v = Y[slot(k) * SOLVE_COLS + qq];
             v.x -= acc.x;
             v.y -= acc.y;
         }
         __syncthreads();
-        // within the block, from the bottom
-        for (int c = nb - 1; c >= 0; --c) {
-            // x_{blk+c} is final; remove it from the rows above within the block
-            for (int e = tid; e < c * SOLVE_COLS; e += nth) {
-                const int c2 = e / SOLVE_COLS, q = e % SOLVE_COLS;
-                if (c - c2 > b) continue;
-                const float2 l = Lb[c2 * B1 + (c - c2)];
-                const float2 x = Y[slot(blk + c) * SOLVE_COLS + q];
-                float2 &v = Y[slot(blk + c2) * SOLVE_COLS + q];
-                v.x -= l.x * x.x - l.y * x.y;
-                v.y -= l.x * x.y + l.y * x.x;
+        // in-block from the bottom: half-warp hw solves column hw
+        if (hw < SOLVE_COLS) {
+            float2 x = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
+            for (int c = nb - 1; c > 0; --c) {
+                const float xr = __shfl_sync(0xffffffffu, x.x, c, 16), xi = __shfl_sync(0xffffffffu, x.y, c, 16);
+                if (lane16 < c && c - lane16 <= b) {
+                    const float2 l = Lb[lane16 * B1 + (c - lane16)];
+                    x.x -= l.x * xr - l.y * xi;
+                    x.y -= l.x * xi + l.y * xr;
+                }
             }
-            __syncthreads();
-        }
-        // rows leaving the window at the bottom: [blk + WR - NB, blk + WR) ∩ [0, n); rows entering: [blk - NB, blk)
-        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
-            const int64_t iout = blk + WR - NB + c;
-            if (iout < n && iout >= blk + nb && q < nrc) Zs[iout * ncol + c0 + q] = Y[slot(iout) * SOLVE_COLS + q];
+            if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = x;
         }
         __syncthreads();
+        // rows [blk + b, blk + b + NB) leave the window (all final); rows [blk - NB, blk) enter
+        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
+            const int64_t iout = blk + b + c;
+            if (iout < n && qq < nrc) Zs[iout * ncol + qq] = Y[slot(iout) * SOLVE_COLS + qq];
+        }
         if (blk == 0) {
-            // flush every row still in the window
+            // flush the rows still in the window: [0, min(n, b))
             for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
                 const int64_t i = e / SOLVE_COLS;
-                const int q = e % SOLVE_COLS;
-                if (i < n && i < WR - NB + blk + nb && q < nrc) Zs[i * ncol + c0 + q] = Y[slot(i) * SOLVE_COLS + q];
+                const int qq = e % SOLVE_COLS;
+                if (i < n && i < b && qq < nrc) Zs[i * ncol + qq] = Y[slot(i) * SOLVE_COLS + qq];
             }
             break;
         }
-        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, q = e % SOLVE_COLS;
-            const int64_t inew = blk - NB + c;
-            Y[slot(inew) * SOLVE_COLS + q] = q < nrc ? Zs[inew * ncol + c0 + q] : make_float2(0.f, 0.f);
-        }
         __syncthreads();
+        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
+            const int64_t inew = blk - NB + c;
+            Y[slot(inew) * SOLVE_COLS + qq] = qq < nrc ? Zs[inew * ncol + qq] : zero;
+        }
     }
 }
 
@@ -449,7 +454,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     const int ngrp = (ncol + SOLVE_COLS - 1) / SOLVE_COLS;
     const double macs = 2.0 * nact * n * b * ncol;
     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
-    k_band_solve<<<nshift * ngrp, 256, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
+    k_band_solve<<<nshift * ngrp, 512, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
