@@ -110,7 +110,7 @@ typedef struct {
 
 /* Per-kernel-class accounting since the last gcie_reset_stats (profile = 1 fills times). */
 enum { GCIE_K_SPMM_DIR = 0, GCIE_K_SPMM_UPD = 1, GCIE_K_REFINE = 2, GCIE_K_MOMENT = 3,
-       GCIE_K_DENSE = 4, GCIE_K_OTHER = 5, GCIE_K_PREC = 6, GCIE_K_NCLASS = 7 };
+       GCIE_K_DENSE = 4, GCIE_K_OTHER = 5, GCIE_K_PREC = 6, GCIE_K_FACTOR = 7, GCIE_K_NCLASS = 8 };
 typedef struct {
     int64_t launches[GCIE_K_NCLASS];
     double ms[GCIE_K_NCLASS];          /* summed CUDA-event durations of those launches */

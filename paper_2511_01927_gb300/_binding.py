@@ -52,8 +52,8 @@ class Result(C.Structure):
                 ("outer_iters", C.c_int32), ("cocg_iters", C.c_int64), ("norm_k1", C.c_double)]
 
 
-NCLASS = 7
-KERNEL_CLASSES = ["spmm_dir", "spmm_upd", "refine", "moment", "dense", "other", "prec"]
+NCLASS = 8
+KERNEL_CLASSES = ["spmm_dir", "spmm_upd", "refine", "moment", "dense", "other", "prec", "factor"]
 
 
 class Stats(C.Structure):

@@ -690,7 +690,7 @@ int AmgWork<T>::init(Ctx *c, const Amg *a, int nshift_, int ncol_, const double2
     int *status = (int *)take(256);
     GCIE_CUDA_TRY(cudaMemsetAsync(status, 0, sizeof(int), c->stream));
     {
-        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * nshift * a->nc * a->nc * (double)a->nc, 8.0 * nshift * pow((double)a->nc, 3));
+        LaunchScope ls(c, GCIE_K_FACTOR, 16.0 * nshift * a->nc * a->nc * (double)a->nc, 8.0 * nshift * pow((double)a->nc, 3));
         k_coarse_inverse<T><<<nshift, 1024, 0, c->stream>>>((int)a->nc, a->Kc, a->Mc, d_z, Ainv, perm, status);
         GCIE_CUDA_TRY(cudaGetLastError());
     }

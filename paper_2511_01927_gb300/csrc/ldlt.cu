@@ -57,8 +57,18 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 }
 
 // ------------------------------------------------------------------ factorization
-// smem: P[(NB + b) x NB] panel (row-major: P[t * NB + c] = A[p0 + t][p0 + c]), W[b x NB] = P D,
-// D[NB].
+// One CTA (1024 threads) per shift walks the band by panels of NB columns.  Shared memory:
+// PT[c][t] = A[p0 + t][p0 + c] (panel transposed: NB x R, R = NB + b), W[J][c] = l_{p0+NB+J, p0+c} d_c
+// (b x NB), D[NB].  Per panel:
+//   1. load the panel (coalesced along the columns of the band);
+//   2. warp 0 factors the NB x NB diagonal block (lane = row, __syncwarp between columns);
+//   3. every row t >= NB of the panel is solved against the diagonal block by one thread
+//      (l_tc = (a_tc - sum_{c'<c} l_tc' d_c' l_cc') / d_c), no block-wide synchronisation;
+//   4. the panel goes back to global memory and W = L D is formed;
+//   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel:
+//      each warp owns groups of 4 columns J and its lanes walk consecutive rows I, so the shared
+//      reads of PT are conflict-free, W is a broadcast and the read-modify-writes of the band are
+//      coalesced.
 __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp,
                                                     int *__restrict__ status)
 {
@@ -66,113 +76,112 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
     const int64_t B1 = b + 1;
     float2 *AB = ABp[blockIdx.x];
     const int R = NB + b;
-    float2 *P = sm2;                 // R x NB
-    float2 *W = P + (size_t)R * NB;  // b x NB
-    float2 *D = W + (size_t)b * NB;  // NB
-    const int tid = threadIdx.x, nth = blockDim.x;
+    float2 *PT = sm2;                  // NB x R
+    float2 *W = PT + (size_t)NB * R;   // b x NB
+    float2 *D = W + (size_t)b * NB;    // NB
+    const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
+    const float2 zero = make_float2(0.f, 0.f);
     for (int64_t p0 = 0; p0 < n; p0 += NB) {
         const int nc = (int)min((int64_t)NB, n - p0);
-        const int rows = (int)min((int64_t)R, n - p0);   // local rows present
-        // load the panel (zeros outside the band / matrix)
-        for (int e = tid; e < R * NB; e += nth) {
-            const int t = e / NB, c = e % NB;
-            float2 v = make_float2(0.f, 0.f);
+        const int rows = (int)min((int64_t)R, n - p0);
+        // 1. load
+        for (int e = tid; e < NB * R; e += nth) {
+            const int c = e / R, t = e % R;
+            float2 v = zero;
             if (c < nc && t >= c && t < rows && t - c <= b) v = AB[(p0 + c) * B1 + (t - c)];
-            P[e] = v;
+            PT[e] = v;
         }
         __syncthreads();
-        // factor the panel column by column
-        for (int c = 0; c < nc; ++c) {
-            const float2 d = P[c * NB + c];
-            if (tid == 0) {
-                D[c] = d;
-                if (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)) atomicExch(status, 1);
+        // 2. diagonal block (warp 0, lane = row)
+        if (warp == 0) {
+            for (int c = 0; c < nc; ++c) {
+                const float2 d = PT[c * R + c];
+                if (lane > c && lane < nc && lane - c <= b) PT[c * R + lane] = cdivf(PT[c * R + lane], d);
+                __syncwarp();
+                if (lane > c && lane < nc) {
+                    const float2 l = PT[c * R + lane];
+                    for (int c2 = c + 1; c2 <= lane; ++c2) {
+                        const float2 w = cmulf(d, PT[c * R + c2]);
+                        float2 v = PT[c2 * R + lane];
+                        v.x -= l.x * w.x - l.y * w.y;
+                        v.y -= l.x * w.y + l.y * w.x;
+                        PT[c2 * R + lane] = v;
+                    }
+                }
+                if (lane == 0) {
+                    D[c] = d;
+                    if (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)) atomicExch(status, 1);
+                }
+                __syncwarp();
             }
-            const int tmax = min(rows - 1, c + b);
-            // multipliers l_tc = a_tc / d
-            for (int t = c + 1 + tid; t <= tmax; t += nth) P[t * NB + c] = cdivf(P[t * NB + c], d);
-            __syncthreads();
-            // update the remaining panel columns: a_{t,c2} -= l_tc d l_{c2,c}, c < c2 <= t
-            const int ncol2 = nc - c - 1;
-            if (ncol2 > 0) {
-                const int nrow2 = tmax - c;   // rows c+1..tmax
-                for (int e = tid; e < nrow2 * ncol2; e += nth) {
-                    const int t = c + 1 + e / ncol2, c2 = c + 1 + e % ncol2;
-                    if (c2 > t) continue;
-                    const float2 w = cmulf(d, P[c2 * NB + c]);
-                    const float2 l = P[t * NB + c];
-                    float2 v = P[t * NB + c2];
-                    v.x -= l.x * w.x - l.y * w.y;
-                    v.y -= l.x * w.y + l.y * w.x;
-                    P[t * NB + c2] = v;
+        }
+        __syncthreads();
+        // 3. rows below the diagonal block: one thread per row
+        for (int t = NB + tid; t < rows; t += nth) {
+            float2 a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[c] = PT[c * R + t];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) {
+                if (c >= nc) break;
+                const float2 l = cdivf(a[c], D[c]);
+                a[c] = l;
+                const float2 ld = cmulf(l, D[c]);
+#pragma unroll
+                for (int c2 = c + 1; c2 < NB; ++c2) {
+                    const float2 lc = PT[c * R + c2];     // l_{c2, c} of the diagonal block
+                    a[c2].x -= ld.x * lc.x - ld.y * lc.y;
+                    a[c2].y -= ld.x * lc.y + ld.y * lc.x;
                 }
             }
-            __syncthreads();
-        }
-        // write the panel back: D on the diagonal, L below
-        for (int e = tid; e < R * NB; e += nth) {
-            const int t = e / NB, c = e % NB;
-            if (c < nc && t >= c && t < rows && t - c <= b) AB[(p0 + c) * B1 + (t - c)] = t == c ? D[c] : P[e];
-        }
-        // W = rows NB..NB+b-1 of the panel times D (for the trailing update)
-        for (int e = tid; e < b * NB; e += nth) {
-            const int t = NB + e / NB, c = e % NB;
-            W[e] = (c < nc && t < rows) ? cmulf(P[t * NB + c], D[c]) : make_float2(0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < NB; ++c) PT[c * R + t] = c < nc ? a[c] : zero;
         }
         __syncthreads();
-        // trailing update of the b x b lower triangle at (p0 + NB, p0 + NB):
-        // A[i][j] -= sum_c L[i][c] d_c L[j][c] for i >= j, i - j <= b
+        // 4. write back (D on the diagonal) and W = L D for the rows below the panel
+        for (int e = tid; e < NB * R; e += nth) {
+            const int c = e / R, t = e % R;
+            if (c < nc && t >= c && t < rows && t - c <= b) AB[(p0 + c) * B1 + (t - c)] = t == c ? D[c] : PT[e];
+        }
+        for (int e = tid; e < b * NB; e += nth) {
+            const int J = e / NB, c = e % NB;
+            W[e] = (c < nc && NB + J < rows) ? cmulf(PT[c * R + NB + J], D[c]) : zero;
+        }
+        __syncthreads();
+        // 5. trailing update
         if (nc == NB) {
-            const int tr = min((int64_t)b, n - p0 - NB);   // trailing rows present
-            const int nt = (tr + 3) / 4;
-            const int ntile = nt * (nt + 1) / 2;
-            for (int tile = tid; tile < ntile; tile += nth) {
-                // tile -> (ti, tj) with tj <= ti (row-major lower triangle)
-                int ti = (int)((sqrtf(8.f * tile + 1.f) - 1.f) * 0.5f);
-                while ((ti + 1) * (ti + 2) / 2 <= tile) ++ti;
-                while (ti * (ti + 1) / 2 > tile) --ti;
-                const int tj = tile - ti * (ti + 1) / 2;
-                float2 acc[4][4];
+            const int tr = (int)min((int64_t)b, n - p0 - NB);
+            const int njb = (tr + 3) / 4;
+            for (int jb = warp; jb < njb; jb += nwarp) {
+                const int J0 = 4 * jb;
+                for (int I0 = J0; I0 < tr; I0 += 32) {
+                    const int I = I0 + lane;
+                    float2 acc[4] = {zero, zero, zero, zero};
+                    if (I < tr) {
 #pragma unroll
-                for (int a = 0; a < 4; ++a)
+                        for (int c = 0; c < NB; ++c) {
+                            const float2 l = PT[c * R + NB + I];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[a][q] = make_float2(0.f, 0.f);
-#pragma unroll 4
-                for (int c = 0; c < NB; ++c) {
-                    float2 li[4], wj[4];
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int I = 4 * ti + a, J = 4 * tj + a;
-                        li[a] = I < tr ? P[(NB + I) * NB + c] : make_float2(0.f, 0.f);
-                        wj[a] = J < tr ? W[J * NB + c] : make_float2(0.f, 0.f);
-                    }
-#pragma unroll
-                    for (int a = 0; a < 4; ++a)
+                            for (int q = 0; q < 4; ++q) {
+                                const float2 w = W[(J0 + q < tr ? J0 + q : 0) * NB + c];
+                                acc[q].x += l.x * w.x - l.y * w.y;
+                                acc[q].y += l.x * w.y + l.y * w.x;
+                            }
+                        }
 #pragma unroll
                         for (int q = 0; q < 4; ++q) {
-                            acc[a][q].x += li[a].x * wj[q].x - li[a].y * wj[q].y;
-                            acc[a][q].y += li[a].x * wj[q].y + li[a].y * wj[q].x;
+                            const int J = J0 + q;
+                            if (J < tr && J <= I) {
+                                float2 *pv = AB + (p0 + NB + J) * B1 + (I - J);
+                                float2 v = *pv;
+                                v.x -= acc[q].x;
+                                v.y -= acc[q].y;
+                                *pv = v;
+                            }
                         }
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int J = 4 * tj + q;
-                    if (J >= tr) continue;
-                    const int64_t j = p0 + NB + J;
-#pragma unroll
-                    for (int a = 0; a < 4; ++a) {
-                        const int I = 4 * ti + a;
-                        if (I >= tr || I < J || I - J > b) continue;
-                        float2 *pv = AB + j * B1 + (I - J);
-                        float2 v = *pv;
-                        v.x -= acc[a][q].x;
-                        v.y -= acc[a][q].y;
-                        *pv = v;
                     }
                 }
             }
-        } else {
-            // last (partial) panel: nothing below it
         }
         __syncthreads();
     }
@@ -263,36 +272,32 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
         }
     }
     __syncthreads();
-    // ---------------- backward: L^T x = y' (in place in Z), from the last block up; the window holds
-    // rows [blk, blk + WR) at block blk
+    // ---------------- backward: L^T x = y' (in place in Z), blocks from the last one up.  The window
+    // holds rows [blk - b, blk + NB) at block blk; a finished block pushes its contributions
+    // x_k -= sum_{i in block} l_ik x_i to the rows k in [blk - b, blk) above it.
+    float2 *Ls = Lb;                                  // b x NB: Ls[(k - (blk - b)) * NB + c] = l_{blk+c, k}
+    float2 *Ld = Lb + (size_t)b * NB;                 // NB x NB: Ld[c2 * NB + c] = l_{blk+c, blk+c2}
     const int64_t lastblk = ((n - 1) / NB) * NB;
     for (int e = tid; e < WR * SOLVE_COLS; e += nth) Y[e] = zero;
     __syncthreads();
-    for (int e = tid; e < (int)(n - lastblk) * SOLVE_COLS; e += nth) {
-        const int64_t i = lastblk + e / SOLVE_COLS;
+    for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
+        const int64_t i = lastblk - b + e / SOLVE_COLS;
         const int qq = e % SOLVE_COLS;
-        Y[slot(i) * SOLVE_COLS + qq] = qq < nrc ? Zs[i * ncol + qq] : zero;
+        if (i >= 0 && i < n && qq < nrc) Y[slot(i) * SOLVE_COLS + qq] = Zs[i * ncol + qq];
     }
     for (int64_t blk = lastblk; blk >= 0; blk -= NB) {
         const int nb = (int)min((int64_t)NB, n - blk);
         __syncthreads();
-        for (int e = tid; e < nb * B1; e += nth) Lb[e] = AB[blk * B1 + e];
-        __syncthreads();
-        // rows below the block: x_k -= sum_{i >= blk + nb, i <= k + b} l_ik x_i, thread = (k, q)
-        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
-            const int64_t k = blk + c;
-            const int64_t ihi = min(n - 1, k + b);
-            float2 acc = zero;
-            for (int64_t i = blk + nb; i <= ihi; ++i) {
-                const float2 l = Lb[c * B1 + (int)(i - k)];
-                const float2 x = Y[slot(i) * SOLVE_COLS + qq];
-                acc.x += l.x * x.x - l.y * x.y;
-                acc.y += l.x * x.y + l.y * x.x;
-            }
-            float2 &v = Y[slot(k) * SOLVE_COLS + qq];
-            v.x -= acc.x;
-            v.y -= acc.y;
+        // strip of L: columns k in [blk - b, blk), rows blk..blk+nb-1; and the in-block triangle
+        for (int e = tid; e < b * NB; e += nth) {
+            const int kk = e / NB, c = e % NB;
+            const int64_t k = blk - b + kk;
+            const int64_t off = blk + c - k;
+            Ls[e] = (k >= 0 && c < nb && off <= b) ? AB[k * B1 + off] : zero;
+        }
+        for (int e = tid; e < NB * NB; e += nth) {
+            const int c2 = e / NB, c = e % NB;
+            Ld[e] = (c < nb && c2 < c && c - c2 <= b) ? AB[(blk + c2) * B1 + (c - c2)] : zero;
         }
         __syncthreads();
         // in-block from the bottom: half-warp hw solves column hw
@@ -300,8 +305,8 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
             float2 x = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
             for (int c = nb - 1; c > 0; --c) {
                 const float xr = __shfl_sync(0xffffffffu, x.x, c, 16), xi = __shfl_sync(0xffffffffu, x.y, c, 16);
-                if (lane16 < c && c - lane16 <= b) {
-                    const float2 l = Lb[lane16 * B1 + (c - lane16)];
+                if (lane16 < c) {
+                    const float2 l = Ld[lane16 * NB + c];
                     x.x -= l.x * xr - l.y * xi;
                     x.y -= l.x * xi + l.y * xr;
                 }
@@ -309,26 +314,37 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
             if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = x;
         }
         __syncthreads();
-        // rows [blk + b, blk + b + NB) leave the window (all final); rows [blk - NB, blk) enter
-        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
-            const int64_t iout = blk + b + c;
-            if (iout < n && qq < nrc) Zs[iout * ncol + qq] = Y[slot(iout) * SOLVE_COLS + qq];
-        }
-        if (blk == 0) {
-            // flush the rows still in the window: [0, min(n, b))
-            for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
-                const int64_t i = e / SOLVE_COLS;
-                const int qq = e % SOLVE_COLS;
-                if (i < n && i < b && qq < nrc) Zs[i * ncol + qq] = Y[slot(i) * SOLVE_COLS + qq];
+        // push to the rows above inside the band; write the finished block
+        {
+            float2 xb[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) xb[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q] : zero;
+            const int64_t klo = max((int64_t)0, blk - b);
+            for (int64_t k = klo + tid / SOLVE_COLS; k < blk; k += nth / SOLVE_COLS) {
+                const int kk = (int)(k - (blk - b));
+                float2 acc = zero;
+#pragma unroll
+                for (int c = 0; c < NB; ++c) {
+                    const float2 l = Ls[kk * NB + c];
+                    acc.x += l.x * xb[c].x - l.y * xb[c].y;
+                    acc.y += l.x * xb[c].y + l.y * xb[c].x;
+                }
+                float2 &v = Y[slot(k) * SOLVE_COLS + q];
+                v.x -= acc.x;
+                v.y -= acc.y;
             }
-            break;
         }
+        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
+            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
+            if (qq < nrc) Zs[(blk + c) * ncol + qq] = Y[slot(blk + c) * SOLVE_COLS + qq];
+        }
+        if (blk == 0) break;
         __syncthreads();
+        // rows [blk - b - NB, blk - b) enter the slots of the finished block
         for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
             const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
-            const int64_t inew = blk - NB + c;
-            Y[slot(inew) * SOLVE_COLS + qq] = qq < nrc ? Zs[inew * ncol + qq] : zero;
+            const int64_t inew = blk - b - NB + c;
+            Y[slot(blk + c) * SOLVE_COLS + qq] = (inew >= 0 && qq < nrc) ? Zs[inew * ncol + qq] : zero;
         }
     }
 }
@@ -406,11 +422,16 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 }
 
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
-size_t band_smem_solve(int b) { return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + (size_t)NB * (b + 1)); }
+size_t band_smem_solve(int b)
+{
+    // window + max(forward L block NB x (b+1), backward strip b x NB + in-block NB x NB)
+    return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + std::max((size_t)NB * (b + 1), (size_t)b * NB + NB * NB));
+}
 
 bool band_feasible(const Ctx *c, int b)
 {
-    return band_smem_factor(b) <= c->smem_optin && band_smem_solve(b) <= c->smem_optin;
+    // one thread per row below the panel in the factorization: b < 1024 - NB
+    return b + NB <= 1024 && band_smem_factor(b) <= c->smem_optin && band_smem_solve(b) <= c->smem_optin;
 }
 
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
@@ -420,7 +441,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     const int64_t n = p->n;
     for (float2 *q : h_ABp) GCIE_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(float2) * (size_t)n * (b + 1), c->stream));
     {
-        LaunchScope ls(c, GCIE_K_PREC, (double)p->nnz * 20 + (double)nshift * n * (b + 1) * 8, 0);
+        LaunchScope ls(c, GCIE_K_FACTOR, (double)p->nnz * 20 + (double)nshift * n * (b + 1) * 8, 0);
         const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
         k_band_assemble<<<blocks, 256, 0, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z, nshift, b, d_ABp);
         GCIE_CUDA_TRY(cudaGetLastError());
@@ -432,7 +453,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
-        LaunchScope ls(c, GCIE_K_PREC, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
+        LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
         k_band_ldlt<<<nshift, 1024, smem, c->stream>>>(n, b, d_ABp, d_status);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
