@@ -1,0 +1,309 @@
+"""Benchmark: converged eigenpairs per second of the contour-integral eigensolver on the 2D P1-FEM
+pencil of a 500 x 500 grid (n = 249001, log-normal coefficient fields in K and M), eigenvalues
+101..400 (300 pairs) with 8 uniform contours x 16 trapezoid nodes, L = 64, 2 moments, FP32 COCG with
+FP64 refinement, residual tolerance 1e-10.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+
+One step = one complete solve (ingested pencil resident on the GPU; every step repeats the shifted
+solves, moments, basis, Rayleigh-Ritz and merge).  Prints one JSON line on rank 0.  Under torchrun
+each rank solves its own replica of the workload (independent problems, no collective).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import pencils as P  # noqa: E402
+
+METRIC = "converged eigenpairs/s at residual<=1e-10 (uniform contours)"
+UNIT = "eigenpairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="fem2d-p1-500")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ----------------------------------------------------------------------------- our path
+def solver_opts(spec, V):
+    return dict(nodes=spec["nodes"], moments=spec["moments"], nuniform=spec["contours"], V0=V, tol=1e-10,
+                lin_tol=1e-11, expected_count=spec["count"])
+
+
+def run_ours(args, rank, world):
+    import torch
+    import paper_2511_01927_gb300 as G
+
+    torch.cuda.set_device(0 if world == 1 else int(os.environ.get("LOCAL_RANK", rank)))
+    dev = torch.cuda.current_device()
+    K, M, spec = P.workload(args.workload)
+    if "count" not in spec:
+        raise SystemExit(f"workload {args.workload}: no stored interval (tests/golden)")
+    V = P.gaussian_block(K.n, spec["L"], 1)
+    stream = torch.cuda.current_stream()
+    ctx = G.gcie_create(dev, stream.cuda_stream)
+    pen = G.gcie_pencil_create(ctx, K, M)
+    opts = solver_opts(spec, V)
+
+    def step(profile):
+        return G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], profile=int(profile), **opts)
+
+    for _ in range(args.warmup):
+        step(False)
+    # timed region: device events on the library's stream (torch's current stream), max over ranks
+    G.gcie_reset_stats(ctx)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    count = 0
+    last = None
+    for _ in range(args.steps):
+        last = step(True)
+        count += len(last["evals"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    stats = G.gcie_get_stats(ctx)
+    if world > 1:
+        t = torch.tensor([ms, count], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+        tsum = t.clone()
+        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
+        ms, count = float(tmax[0]), int(tsum[1])
+    resid_max = float(np.max(last["resid"])) if len(last["resid"]) else None
+
+    # end to end through the public host-buffer call: CSR and V0 from pinned host memory in, the
+    # eigenpairs out, every step
+    e2e = e2e_measure(G, ctx, K, M, spec, opts, args.steps)
+    G.gcie_pencil_destroy(pen)
+    G.gcie_destroy(ctx)
+    return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e)
+
+
+def pinned(a):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    return t.numpy()
+
+
+def e2e_measure(G, ctx, K, M, spec, opts, steps):
+    import torch
+
+    Kp = P.Csr(K.n, pinned(K.rowptr), pinned(K.col), pinned(K.val))
+    Mp = P.Csr(M.n, pinned(M.rowptr), pinned(M.col), pinned(M.val))
+    o = dict(opts)
+    o["V0"] = pinned(opts["V0"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    cnt = 0
+    res = None
+    for _ in range(steps):
+        res = G.gcie_solve(ctx, Kp, Mp, spec["lo"], spec["hi"], **o)
+        cnt += len(res["evals"])
+    torch.cuda.synchronize()
+    sec = time.perf_counter() - t0
+    h2d = sum(a.nbytes for a in (Kp.rowptr, Kp.col, Kp.val, Mp.rowptr, Mp.col, Mp.val, o["V0"]))
+    d2h = res["evecs"].nbytes + res["evals"].nbytes + res["resid"].nbytes + res["contour_of"].nbytes
+    return {"value": cnt / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+
+# ----------------------------------------------------------------------------- CPU oracle baseline
+def oracle_sample(args, spec, K, M, seconds):
+    """The oracle on a bounded sample of the workload: its banded LU of one shifted matrix on the leading
+    rows of the pencil (cost linear in the rows at fixed bandwidth), timed on this host, extrapolated to
+    the full solve: (n / rows) x (factor + solve with L right-hand sides) per node x nodes x contours
+    x 2 FEAST passes (the second with twice the columns), plus nothing for the dense steps (a lower bound
+    on the oracle's time, so an upper bound on its eigenpairs/s)."""
+    import scipy.sparse as sp
+    import oracle as O
+
+    Ks, Ms = K.to_scipy(), M.to_scipy()
+    bw = O.bandwidth(Ks, Ms)
+    c = 0.5 * (spec["lo"] + spec["hi"])
+    R = 0.5 * (spec["hi"] - spec["lo"]) / spec["contours"]
+    z = O.trapezoid_nodes(c, R, spec["nodes"])[0][0]
+    rows = max(4 * bw, 2000)
+    while True:
+        Ksub, Msub = Ks[:rows, :rows], Ms[:rows, :rows]
+        B = (Msub @ P.gaussian_block(rows, spec["L"], 1)).astype(complex)
+        t0 = time.perf_counter()
+        sv = O.ShiftedSolver(Ksub, Msub, z, bw)
+        t1 = time.perf_counter()
+        sv.solve(B)
+        sv.solve(np.concatenate([B, B], axis=1))
+        t2 = time.perf_counter()
+        if t2 - t0 >= 0.2 * seconds or rows >= K.n:
+            break
+        rows = min(K.n, int(rows * max(2.0, 0.25 * seconds / max(t2 - t0, 1e-3))))
+    per_node = (t2 - t0) * K.n / rows
+    nodes_total = spec["contours"] * spec["nodes"] // 2
+    total = per_node * nodes_total
+    value = spec["count"] / total
+    sample = (f"oracle banded LU (bandwidth {bw}) of z M - K on the leading {rows} of {K.n} rows, one node, "
+              f"factor + solves with L and 2L right-hand sides ({t2 - t0:.1f} s), scaled by n/rows and by "
+              f"{nodes_total} nodes; dense steps not counted")
+    return value, total, sample
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------------------- main
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl" if args.impl == "ours" else "gloo")
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        K, M, spec = P.workload(args.workload)
+        vals, secs = [], []
+        for _ in range(args.warmup):
+            oracle_sample(args, spec, K, M, args.cpu_sample_seconds)
+        sample = ""
+        for _ in range(args.steps):
+            v, tot, sample = oracle_sample(args, spec, K, M, args.cpu_sample_seconds)
+            vals.append(v)
+            secs.append(tot)
+        value = float(np.mean(vals))
+        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+               "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+               "data": "synthetic", "config": {"workload": args.workload},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+               "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(out))
+        return
+
+    r = run_ours(args, rank, world)
+    if rank != 0:
+        return
+    spec, stats = r["spec"], r["stats"]
+    ms_step = r["ms"] / args.steps
+    value = r["count"] / (r["ms"] / 1e3)
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            peaks = json.load(fh)
+    except OSError:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    # dominant kernel class of the timed region
+    classes = {k: v for k, v in stats.items() if isinstance(v, dict)}
+    dom = max(classes, key=lambda k: classes[k]["ms"])
+    d = classes[dom]
+    launches = max(d["launches"], 1)
+    sm_mhz = r["clocks"].get("sm_max_mhz") or 2070.0
+    # FP32 CUDA-core peak: 152 SMs x 128 FMA lanes x 2 flops x clock
+    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    if dom in ("prec", "factor"):
+        achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        roof = {"kernel_class": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None,
+                "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
+    else:
+        achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
+        roof = {"kernel_class": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None,
+                "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
+    spmm_ms = stats["spmm_dir"]["ms"] + stats["spmm_upd"]["ms"]
+    spmm_gbs = (stats["spmm_dir"]["bytes"] + stats["spmm_upd"]["bytes"]) / max(spmm_ms, 1e-9) / 1e6
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
+           "config": {"workload": args.workload, "n": int(r["K"].n), "pairs_per_step": spec["count"],
+                      "contours": spec["contours"], "nodes": spec["nodes"], "L": spec["L"],
+                      "moments": spec["moments"], "tol": 1e-10, "l2": "inputs larger than L2 (16 GB block)",
+                      "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
+                      "cocg_iters": r["last"]["cocg_iters"]},
+           "roofline": roof,
+           "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
+                        "nameplate_frac": spmm_gbs / 8000.0},
+           "kernel_ms": {k: round(v["ms"], 2) for k, v in classes.items()},
+           "gpu_launches": int(stats["total_launches"]),
+           "clocks": r["clocks"], "e2e": r["e2e"]}
+    if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
+        v, tot, sample = oracle_sample(args, spec, *P.workload(args.workload)[:2], args.cpu_sample_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

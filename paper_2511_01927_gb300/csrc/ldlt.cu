@@ -206,8 +206,9 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
     const int WR = b + NB;
+    const int LD = B1 + NB;                           // padded column length of Lb (zeros past the band)
     float2 *Y = sm2;                                  // WR x SOLVE_COLS
-    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;         // NB x B1
+    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;         // NB x LD
     const int tid = threadIdx.x, nth = blockDim.x;
     const int lane16 = tid & 15;                      // row of the block handled in the in-block solve
     const int hw = tid >> 4;                          // half-warp index = column of the in-block solve
@@ -223,15 +224,18 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
     for (int64_t blk = 0; blk < n; blk += NB) {
         const int nb = (int)min((int64_t)NB, n - blk);
         __syncthreads();
-        for (int e = tid; e < nb * B1; e += nth) Lb[e] = AB[blk * B1 + e];
+        for (int e = tid; e < NB * LD; e += nth) {
+            const int c = e / LD, t = e % LD;
+            Lb[e] = (c < nb && t < B1) ? AB[(blk + c) * B1 + t] : zero;
+        }
         __syncthreads();
         // in-block: half-warp hw solves column hw (rows blk..blk+nb-1 in lanes)
         if (hw < SOLVE_COLS) {
             float2 y = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
             for (int c = 0; c < nb - 1; ++c) {
                 const float yr = __shfl_sync(0xffffffffu, y.x, c, 16), yi = __shfl_sync(0xffffffffu, y.y, c, 16);
-                if (lane16 > c && lane16 < nb && lane16 - c <= b) {
-                    const float2 l = Lb[c * B1 + (lane16 - c)];
+                if (lane16 > c && lane16 < nb) {
+                    const float2 l = Lb[c * LD + (lane16 - c)];
                     y.x -= l.x * yr - l.y * yi;
                     y.y -= l.x * yi + l.y * yr;
                 }
@@ -239,26 +243,34 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
             if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = y;
         }
         __syncthreads();
-        // rows below the block inside the band: thread (q, row group) keeps the block's y in registers
+        // rows below the block inside the band: each thread owns two columns (q2, q2 + 16) and keeps
+        // the block's y of both in registers; Lb is zero past the band, so the loop has no tests
         {
-            float2 yb[NB];
+            const int q2 = tid & 15, rg = tid >> 4, nrg = nth >> 4;
+            float2 ya[NB], yc[NB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) yb[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q] : zero;
-            const int64_t rlo = blk + nb, rhi = min(n, blk + nb + b);
-            for (int64_t i = rlo + tid / SOLVE_COLS; i < rhi; i += nth / SOLVE_COLS) {
-                float2 acc = zero;
+            for (int c = 0; c < NB; ++c) {
+                ya[c] = Y[slot(blk + c) * SOLVE_COLS + q2];
+                yc[c] = Y[slot(blk + c) * SOLVE_COLS + q2 + 16];
+            }
+            const int rlo = nb, rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
+            int sl = (int)((blk + rlo + rg) % WR);
+            for (int il = rlo + rg; il < rhi; il += nrg) {
+                float2 a0 = zero, a1 = zero;
+                const float2 *lrow = Lb + il;    // Lb[c * LD + il - c] = lrow[c * (LD - 1)]
 #pragma unroll
                 for (int c = 0; c < NB; ++c) {
-                    const int64_t t = i - (blk + c);
-                    if (c < nb && t <= b) {
-                        const float2 l = Lb[c * B1 + (int)t];
-                        acc.x += l.x * yb[c].x - l.y * yb[c].y;
-                        acc.y += l.x * yb[c].y + l.y * yb[c].x;
-                    }
+                    const float2 l = lrow[c * (LD - 1)];
+                    a0.x += l.x * ya[c].x - l.y * ya[c].y;
+                    a0.y += l.x * ya[c].y + l.y * ya[c].x;
+                    a1.x += l.x * yc[c].x - l.y * yc[c].y;
+                    a1.y += l.x * yc[c].y + l.y * yc[c].x;
                 }
-                float2 &v = Y[slot(i) * SOLVE_COLS + q];
-                v.x -= acc.x;
-                v.y -= acc.y;
+                float2 *yr = Y + sl * SOLVE_COLS;
+                yr[q2].x -= a0.x; yr[q2].y -= a0.y;
+                yr[q2 + 16].x -= a1.x; yr[q2 + 16].y -= a1.y;
+                sl += nrg;
+                if (sl >= WR) sl -= WR;
             }
         }
         __syncthreads();
@@ -266,7 +278,7 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
         for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
             const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
             const int64_t i = blk + c;
-            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SOLVE_COLS + qq], Lb[c * B1]);
+            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SOLVE_COLS + qq], Lb[c * LD]);
             const int64_t inew = i + WR;
             Y[slot(i) * SOLVE_COLS + qq] = (inew < n && qq < nrc) ? Rs[inew * ncol + qq] : zero;
         }
@@ -314,24 +326,33 @@ __global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, 
             if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = x;
         }
         __syncthreads();
-        // push to the rows above inside the band; write the finished block
+        // push to the rows above inside the band (two columns per thread); write the finished block
         {
-            float2 xb[NB];
+            const int q2 = tid & 15, rg = tid >> 4, nrg = nth >> 4;
+            float2 xa[NB], xc[NB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) xb[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q] : zero;
-            const int64_t klo = max((int64_t)0, blk - b);
-            for (int64_t k = klo + tid / SOLVE_COLS; k < blk; k += nth / SOLVE_COLS) {
-                const int kk = (int)(k - (blk - b));
-                float2 acc = zero;
+            for (int c = 0; c < NB; ++c) {
+                xa[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q2] : zero;
+                xc[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q2 + 16] : zero;
+            }
+            const int kklo = (int)(max((int64_t)0, blk - b) - (blk - b));
+            int sl = (int)(((blk - b + kklo + rg) % WR + WR) % WR);
+            for (int kk = kklo + rg; kk < b; kk += nrg) {
+                const float2 *lrow = Ls + kk * NB;
+                float2 a0 = zero, a1 = zero;
 #pragma unroll
                 for (int c = 0; c < NB; ++c) {
-                    const float2 l = Ls[kk * NB + c];
-                    acc.x += l.x * xb[c].x - l.y * xb[c].y;
-                    acc.y += l.x * xb[c].y + l.y * xb[c].x;
+                    const float2 l = lrow[c];
+                    a0.x += l.x * xa[c].x - l.y * xa[c].y;
+                    a0.y += l.x * xa[c].y + l.y * xa[c].x;
+                    a1.x += l.x * xc[c].x - l.y * xc[c].y;
+                    a1.y += l.x * xc[c].y + l.y * xc[c].x;
                 }
-                float2 &v = Y[slot(k) * SOLVE_COLS + q];
-                v.x -= acc.x;
-                v.y -= acc.y;
+                float2 *yr = Y + sl * SOLVE_COLS;
+                yr[q2].x -= a0.x; yr[q2].y -= a0.y;
+                yr[q2 + 16].x -= a1.x; yr[q2 + 16].y -= a1.y;
+                sl += nrg;
+                if (sl >= WR) sl -= WR;
             }
         }
         for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
@@ -424,8 +445,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
 size_t band_smem_solve(int b)
 {
-    // window + max(forward L block NB x (b+1), backward strip b x NB + in-block NB x NB)
-    return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + std::max((size_t)NB * (b + 1), (size_t)b * NB + NB * NB));
+    // window + max(forward L block NB x (b+1+NB), backward strip b x NB + in-block NB x NB)
+    return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + std::max((size_t)NB * (b + 1 + NB), (size_t)b * NB + NB * NB));
 }
 
 bool band_feasible(const Ctx *c, int b)
