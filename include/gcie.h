@@ -74,7 +74,7 @@ typedef struct {
     int32_t L;              /* columns of the random starting block V (default 32) */
     int32_t moments;        /* moments m: basis [S_0 .. S_{m-1}] (default 2) */
     int32_t max_outer;      /* FEAST iterations cap (default 8) */
-    int32_t max_iters;      /* COCG iteration cap per shifted solve (default 100000) */
+    int32_t max_iters;      /* COCG iteration cap per shifted solve (default 5000) */
     int32_t precision;      /* GCIE_MIXED (default) or GCIE_FP64 */
     double tol;             /* eigenpair tolerance on ||Kx - lambda Mx||_2 / (||K||_1 ||x||_2) (1e-10) */
     double lin_tol;         /* shifted-solve target on the diagonally scaled residual (default 1e-11) */
@@ -191,7 +191,8 @@ int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const d
  * GCIE_PREC_AMG applies the multigrid V-cycle (hierarchy built on the first call for this pencil and
  * kept with it), GCIE_PREC_AUTO picks the band factors when possible, GCIE_PREC_NONE runs plain COCG.
  * h_iters (host, may be NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol
- * within max_iters (d_X then holds the best iterate). */
+ * within max_iters, or its true residual stopped decreasing (no 4x drop over 4 refinements); d_X then
+ * holds the last iterate. */
 int gcie_shifted_solve(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const double *h_z,
                        int32_t ncol, const double *d_B, double *d_X, int32_t x0, double lin_tol,
                        int32_t max_iters, int32_t precision, int32_t precond, int64_t *h_iters);

@@ -270,7 +270,7 @@ def gcie_shifted_spmm_f64(ctx, pencil, z, ncol: int, d_P, d_Q):
 
 
 def gcie_shifted_solve(ctx, pencil, z, ncol: int, d_B, d_X, x0: bool = False, lin_tol: float = 1e-11,
-                       max_iters: int = 100000, precision: int = MIXED, precond: int = 1, allow_noconv: bool = False):
+                       max_iters: int = 5000, precision: int = MIXED, precond: int = 1, allow_noconv: bool = False):
     zz = _zarr(z)
     it = C.c_int64(0)
     rc = lib().gcie_shifted_solve(ctx, pencil, len(zz), zz.ctypes.data, int(ncol), _ptr(d_B), _ptr(d_X), int(bool(x0)),
@@ -302,3 +302,4 @@ def gcie_rayleigh_ritz(ctx, pencil, q: int, d_Q, d_Z):
 
 def gcie_jacobi_eig(ctx, p: int, d_A, d_w, d_V):
     _check(lib().gcie_jacobi_eig(ctx, int(p), _ptr(d_A), _ptr(d_w), _ptr(d_V)), "gcie_jacobi_eig")
+

@@ -199,7 +199,7 @@ void gcie_default_opts(gcie_opts *o)
     o->L = 32;
     o->moments = 2;
     o->max_outer = 8;
-    o->max_iters = 100000;
+    o->max_iters = 5000;
     o->precision = GCIE_MIXED;
     o->tol = 1e-10;
     o->lin_tol = 1e-11;
@@ -799,6 +799,17 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 s.iters = it + 1;
                 const bool last = (it + 1 == o->max_outer);
+                if (std::getenv("GCIE_VERBOSE")) {
+                    int nin = 0;
+                    double worst = 0.0, wth = 0.0;
+                    for (int l = 0; l < rank; ++l)
+                        if (th[l] >= s.lo && th[l] <= s.hi) {
+                            ++nin;
+                            if (rs[l] > worst) { worst = rs[l]; wth = th[l]; }
+                        }
+                    fprintf(stderr, "[gcie] contour %d it %d: rank %d, %d Ritz values inside [%.6g, %.6g], %zu converged, "
+                            "worst residual %.3e at %.10g\n", act[b0 + bi], it, rank, nin, s.lo, s.hi, keep.size(), worst, wth);
+                }
                 if (!unconverged_inside || last) {
                     // final: keep converged pairs
                     if (!keep.empty()) {

@@ -30,7 +30,8 @@
 
 namespace gcie {
 
-enum : int { F_ACTIVE = 1, F_CONV = 2, F_RESTART = 4 };
+enum : int { F_ACTIVE = 1, F_CONV = 2, F_RESTART = 4, F_STALL = 8 };
+constexpr int STALL_UPDATES = 4;   // updates without a 4x drop of the true residual before a column stops
 
 template <typename T, int CPT> struct V2;
 template <> struct V2<float, 2> {
@@ -301,8 +302,8 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
 // eta_ref are in the scaled FP32 system; eta_abs and bnorm2 are absolute FP64 squared norms.
 struct Scal {
     double2 *rho, *alpha, *beta;
-    double *eta, *eta_ref, *bnorm2, *scale, *scale_next;
-    int *flag, *shift_active, *shift_refine, *since_refine;
+    double *eta, *eta_ref, *bnorm2, *scale, *scale_next, *eta_best;
+    int *flag, *shift_active, *shift_refine, *since_refine, *stall;
     double2 *partA;
     double *partB;
 };
@@ -402,8 +403,19 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, const double2 *__res
         if (f & F_ACTIVE) {
             S.eta[sc] = eta_s;
             S.rho[sc] = rho;
+            // stagnation: the true residual has to drop 4x every few updates (FP64 rounding sets a
+            // floor that some columns cannot pass)
+            if (eta_abs < 0.0625 * S.eta_best[sc]) {
+                S.eta_best[sc] = eta_abs;
+                S.stall[sc] = 0;
+            } else {
+                S.stall[sc] += 1;
+            }
             if (eta_abs <= tol2 * S.bnorm2[sc]) {
                 f = F_CONV;
+                S.beta[sc] = make_double2(0, 0);
+            } else if (S.stall[sc] >= STALL_UPDATES || !isfinite(eta_abs)) {
+                f = F_STALL;
                 S.beta[sc] = make_double2(0, 0);
             } else if (f & F_RESTART) {
                 f &= ~F_RESTART;
@@ -462,6 +474,8 @@ __global__ void k_bnorm_init(int ncol, int chunks, const int *__restrict__ rhs_o
         S.eta_ref[sc] = 1.0;
         S.scale[sc] = 1.0;
         S.scale_next[sc] = 1.0;
+        S.eta_best[sc] = INFINITY;
+        S.stall[sc] = 0;
     }
     if (threadIdx.x == 0) { S.shift_active[s] = 1; S.shift_refine[s] = 1; S.since_refine[s] = 0; }
 }
@@ -500,7 +514,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     const size_t sizes[] = {blk * sizeof(C), blk * sizeof(C), blk * sizeof(C), blk * sizeof(C),
                             ns * sizeof(double2), ns * sizeof(double2), ns * sizeof(double2),
                             ns * sizeof(double), ns * sizeof(double), ns * sizeof(double), ns * sizeof(double),
-                            ns * sizeof(double), ns * sizeof(int), nshift * sizeof(int), nshift * sizeof(int),
+                            ns * sizeof(double), ns * sizeof(double), ns * sizeof(int), ns * sizeof(int),
+                            nshift * sizeof(int), nshift * sizeof(int),
                             nshift * sizeof(int), (size_t)nshift * maxch * ncol * sizeof(double2),
                             (size_t)nshift * maxch * ncol * sizeof(double), nshift * sizeof(double2),
                             nshift * sizeof(int),
@@ -531,7 +546,9 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     S.bnorm2 = (double *)take();
     S.scale = (double *)take();
     S.scale_next = (double *)take();
+    S.eta_best = (double *)take();
     S.flag = (int *)take();
+    S.stall = (int *)take();
     S.shift_active = (int *)take();
     S.shift_refine = (int *)take();
     S.since_refine = (int *)take();
@@ -690,7 +707,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         GCIE_CUDA_TRY(cudaMemcpyAsync(hf.data(), S.flag, ns * sizeof(int), cudaMemcpyDeviceToHost, c->stream));
         GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
         int unconv = 0;
-        for (size_t e = 0; e < ns; ++e) unconv += (hf[e] & F_ACTIVE) != 0;
+        for (size_t e = 0; e < ns; ++e) unconv += (hf[e] & (F_ACTIVE | F_STALL)) != 0;
         if (info) {
             info->iters += iters;
             info->unconverged_cols += unconv;
