@@ -221,6 +221,22 @@ int gcie_rayleigh_ritz(gcie_ctx *ctx, gcie_pencil *p, int32_t q, const double *d
  * d_V: p x p row-major, column j = eigenvector j. */
 int gcie_jacobi_eig(gcie_ctx *ctx, int32_t p, double *d_A, double *d_w, double *d_V);
 
+/* The same eigensolve for callers that must not allocate device memory.  (The paper has no
+ * counterpart; this entry point exists for integration only.)  Some callers cannot call cudaMalloc:
+ * a process that reserves all device memory for its own pool up front has none left to give, and a
+ * thread driving a latency-critical stream cannot accept the device-wide synchronisation that
+ * cudaMalloc/cudaFree may cause.  This variant takes no context and allocates nothing: its p x p
+ * workspace is a fixed array in the library's device memory (512 KB per GPU, held until exit).
+ *   stream: a cudaStream_t (NULL = legacy default stream); the call only enqueues the kernel, results
+ *           are ready when the stream has passed it.
+ *   p: 1..256; larger p returns GCIE_EINVAL ("exceeds the fixed workspace").
+ *   d_A, d_w, d_V: as in gcie_jacobi_eig (device, caller-owned).
+ * The first call on a device looks up the workspace's device address (once, with that device
+ * current); make that first call before any stream capture.  All calls on a device share the
+ * workspace, so calls that overlap on the GPU (other streams, other threads) race and must be
+ * ordered by the caller. */
+int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, double *d_V);
+
 #ifdef __cplusplus
 }
 #endif

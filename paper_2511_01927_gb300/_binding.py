@@ -18,7 +18,7 @@ EXPORTED_SYMBOLS = [
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
     "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
-    "gcie_rayleigh_ritz", "gcie_jacobi_eig",
+    "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
 
 
@@ -101,6 +101,7 @@ def lib():
         "gcie_m_orthonormalize": (C.c_int, [vp, vp, i32, vp, d, vp, C.POINTER(i32)]),
         "gcie_rayleigh_ritz": (C.c_int, [vp, vp, i32, vp, vp, vp, vp]),
         "gcie_jacobi_eig": (C.c_int, [vp, i32, vp, vp, vp]),
+        "gcie_jacobi_eig_noalloc": (C.c_int, [vp, i32, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -303,3 +304,8 @@ def gcie_rayleigh_ritz(ctx, pencil, q: int, d_Q, d_Z):
 def gcie_jacobi_eig(ctx, p: int, d_A, d_w, d_V):
     _check(lib().gcie_jacobi_eig(ctx, int(p), _ptr(d_A), _ptr(d_w), _ptr(d_V)), "gcie_jacobi_eig")
 
+
+def gcie_jacobi_eig_noalloc(stream, p: int, d_A, d_w, d_V):
+    """Allocation-free variant (stream: a cudaStream_t handle as int, or None)."""
+    _check(lib().gcie_jacobi_eig_noalloc(C.c_void_p(stream) if stream else None, int(p), _ptr(d_A), _ptr(d_w),
+                                         _ptr(d_V)), "gcie_jacobi_eig_noalloc")

@@ -525,6 +525,11 @@ int gcie_rayleigh_ritz(gcie_ctx *c, gcie_pencil *p, int32_t q, const double *d_Q
     return rayleigh_ritz(c, p, q, d_Q, d_Z, h_theta, h_res);
 }
 
+int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, double *d_V)
+{
+    return jacobi_noalloc((cudaStream_t)stream, p, d_A, d_w, d_V);
+}
+
 int gcie_jacobi_eig(gcie_ctx *c, int32_t p, double *d_A, double *d_w, double *d_V)
 {
     if (!c || !d_A || !d_w || !d_V || p <= 0 || p > 1024) { set_error("jacobi: bad argument"); return GCIE_EINVAL; }

@@ -8,6 +8,8 @@
 //                x <- Q u) and the residual ||K z - theta M z|| / (||K||_1 ||z||)
 #include <algorithm>
 #include <cmath>
+#include <mutex>
+#include <string>
 
 #include "kernels.cuh"
 
@@ -320,6 +322,62 @@ int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
     cudaError_t e = cudaGetLastError();
     cudaFreeAsync(wk, c->stream);
     if (e != cudaSuccess) { set_error(std::string("jacobi: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
+    return GCIE_OK;
+}
+
+// ------------------------------------------------------------------ Jacobi without allocation
+// gcie_jacobi_eig_noalloc (declared in gcie.h) runs the same kernel as gcie_jacobi_eig, but its
+// p x p workspace (the unsorted eigenvectors) lives in this fixed device array instead of memory
+// allocated per call.  Every GPU that loads the library holds the array (512 KB) until the process
+// exits; all calls on a device share it, so calls that overlap on that GPU (different streams,
+// different host threads) race on it and must be ordered by the caller.  The kernel overwrites the
+// whole workspace (identity start) before reading it, so nothing has to be cleared between calls.
+constexpr int kJacobiStaticMaxP = 256;
+static __device__ __align__(256) double g_jacobi_ws[kJacobiStaticMaxP * kJacobiStaticMaxP];
+static __device__ __align__(256) DbgRec g_jacobi_dbg;
+
+// Device addresses of the array, looked up once per device with that device current (in host code
+// the array's name is only a host-side stand-in, not a device address).
+static std::mutex g_jacobi_mu;
+static double *g_jacobi_ptr[64];
+static DbgRec *g_jacobi_dbg_ptr[64];
+
+static int jacobi_static_setup(int dev, double **ws, DbgRec **dbg)
+{
+    if (dev < 0 || dev >= 64) { set_error("jacobi_noalloc: device index out of range"); return GCIE_EINVAL; }
+    std::lock_guard<std::mutex> lk(g_jacobi_mu);
+    if (!g_jacobi_ptr[dev]) {
+        double *w = nullptr;
+        DbgRec *d = nullptr;
+        cudaError_t e = cudaGetSymbolAddress((void **)&w, g_jacobi_ws);
+        if (e == cudaSuccess) e = cudaGetSymbolAddress((void **)&d, g_jacobi_dbg);
+        if (e != cudaSuccess) {
+            set_error(std::string("jacobi_noalloc: workspace address lookup failed: ") + cudaGetErrorString(e));
+            return GCIE_ECUDA;
+        }
+        g_jacobi_ptr[dev] = w;
+        g_jacobi_dbg_ptr[dev] = d;
+    }
+    *ws = g_jacobi_ptr[dev];
+    *dbg = g_jacobi_dbg_ptr[dev];
+    return GCIE_OK;
+}
+
+int jacobi_noalloc(cudaStream_t stream, int p, double *A, double *w, double *V)
+{
+    if (p <= 0 || !A || !w || !V) { set_error("jacobi_noalloc: p must be >= 1 and pointers non-null"); return GCIE_EINVAL; }
+    if (p > kJacobiStaticMaxP) {
+        set_error("jacobi_noalloc: p = " + std::to_string(p) + " exceeds the fixed workspace (p <= " +
+                  std::to_string(kJacobiStaticMaxP) + ")");
+        return GCIE_EINVAL;
+    }
+    int dev = 0;
+    GCIE_CUDA_TRY(cudaGetDevice(&dev));
+    double *ws = nullptr;
+    DbgRec *dbg = nullptr;
+    GCIE_TRY(jacobi_static_setup(dev, &ws, &dbg));
+    k_jacobi<<<1, 1024, 0, stream>>>(p, A, w, V, ws, 1e-15, 60, dbg);
+    GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
 

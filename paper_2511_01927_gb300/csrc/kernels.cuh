@@ -45,6 +45,8 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G);
 int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const double *T, double *Z, int ldZ);
 // Batched cyclic Jacobi: nmat symmetric p x p matrices (A destroyed), ascending w, V columns.
 int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V);
+// The same for one matrix, with the workspace in a fixed device array (no allocation, p <= 256).
+int jacobi_noalloc(cudaStream_t stream, int p, double *A, double *w, double *V);
 // Column sums over rows: out[l] = sum_i (KZ_il - theta_l MZ_il)^2 and out2[l] = sum_i Z_il^2.
 int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, const double *Z,
                 const double *d_theta, double *d_r2, double *d_z2);
