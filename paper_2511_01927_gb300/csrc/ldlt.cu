@@ -28,7 +28,6 @@
 namespace gcie {
 
 constexpr int NB = 16;        // panel / block width
-constexpr int SOLVE_COLS = 32; // right-hand sides per CTA in the sweeps
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cdivf(float2 a, float2 b)
@@ -188,184 +187,183 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 }
 
 // ------------------------------------------------------------------ triangular sweeps
-// z = L^-T D^-1 L^-1 r for columns [c0, c0 + SOLVE_COLS) of shift s, 512 threads.  The window Y
-// holds b + NB consecutive rows (slot = row mod (b + NB)); Lb holds the NB columns of L of the
-// current block.  The triangular solve inside a block is done by half-warps (one column each,
-// lane = row of the block) with shuffles; the band parts are block-wide.
-__global__ void __launch_bounds__(512) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
+// z = L^-T D^-1 L^-1 r for SC right-hand sides of one shift per CTA (256 threads, two CTAs per SM).
+// The window Y holds b + SB consecutive rows (slot = row mod (b + SB)).  Per block of SB rows:
+//   forward : load the block's columns of L (zero-padded past the band), solve the SB x SB unit
+//             triangle with SB-lane groups (one column each, shuffles), subtract the block's
+//             contribution from the b rows below (each thread: two columns, a set of rows, the
+//             block's y in registers), write y / d, load the rows entering the window;
+//   backward: load the strip l_{block, k} for the b rows k above, solve the triangle from the
+//             bottom, push the block's x to the rows above, write x, load the rows entering.
+constexpr int SB = 8;         // rows per block of the sweeps
+constexpr int SC = 16;        // right-hand sides per CTA of the sweeps
+constexpr int ST = 256;       // threads per CTA of the sweeps
+
+__global__ void __launch_bounds__(ST, 2) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
 {
     extern __shared__ float2 sm2[];
-    const int ngrp = (ncol + SOLVE_COLS - 1) / SOLVE_COLS;
+    const int ngrp = (ncol + SC - 1) / SC;
     const int s = blockIdx.x / ngrp, g = blockIdx.x % ngrp;
     if (!mask[s]) return;
-    const int c0 = g * SOLVE_COLS;
-    const int nrc = min(SOLVE_COLS, ncol - c0);
+    const int c0 = g * SC;
+    const int nrc = min(SC, ncol - c0);
     const int B1 = b + 1;
     const float2 *AB = ABp[s];
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
-    const int WR = b + NB;
-    const int LD = B1 + NB;                           // padded column length of Lb (zeros past the band)
-    float2 *Y = sm2;                                  // WR x SOLVE_COLS
-    float2 *Lb = Y + (size_t)WR * SOLVE_COLS;         // NB x LD
-    const int tid = threadIdx.x, nth = blockDim.x;
-    const int lane16 = tid & 15;                      // row of the block handled in the in-block solve
-    const int hw = tid >> 4;                          // half-warp index = column of the in-block solve
-    const int q = tid % SOLVE_COLS;                   // column handled in the band parts
+    const int WR = b + SB;
+    const int LD = B1 + SB;                           // padded column length of Lb (zeros past the band)
+    float2 *Y = sm2;                                  // WR x SC
+    float2 *Lb = Y + (size_t)WR * SC;                 // SB x LD (forward) | b x SB strip + SB x SB (backward)
+    const int tid = threadIdx.x;
+    const int lg = tid & (SB - 1);                    // row of the block in the in-block solve
+    const int cg = tid / SB;                          // column of the in-block solve (cg < SC active)
+    const unsigned gmask = 0xffffffffu;
+    const int q2 = tid % (SC / 2), rg = tid / (SC / 2), nrg = ST / (SC / 2);
     auto slot = [&](int64_t i) { return (int)(i % WR); };
     const float2 zero = make_float2(0.f, 0.f);
 
     // ---------------- forward: L y = r, then y' = y / d written to Z
-    for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
-        const int t = e / SOLVE_COLS, c = e % SOLVE_COLS;
+    for (int e = tid; e < WR * SC; e += ST) {
+        const int t = e / SC, c = e % SC;
         Y[e] = (t < n && c < nrc) ? Rs[(int64_t)t * ncol + c] : zero;
     }
-    for (int64_t blk = 0; blk < n; blk += NB) {
-        const int nb = (int)min((int64_t)NB, n - blk);
+    for (int64_t blk = 0; blk < n; blk += SB) {
+        const int nb = (int)min((int64_t)SB, n - blk);
         __syncthreads();
-        for (int e = tid; e < NB * LD; e += nth) {
+        for (int e = tid; e < SB * LD; e += ST) {
             const int c = e / LD, t = e % LD;
             Lb[e] = (c < nb && t < B1) ? AB[(blk + c) * B1 + t] : zero;
         }
         __syncthreads();
-        // in-block: half-warp hw solves column hw (rows blk..blk+nb-1 in lanes)
-        if (hw < SOLVE_COLS) {
-            float2 y = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
-            for (int c = 0; c < nb - 1; ++c) {
-                const float yr = __shfl_sync(0xffffffffu, y.x, c, 16), yi = __shfl_sync(0xffffffffu, y.y, c, 16);
-                if (lane16 > c && lane16 < nb) {
-                    const float2 l = Lb[c * LD + (lane16 - c)];
+        if (cg < SC) {
+            float2 y = lg < nb ? Y[slot(blk + lg) * SC + cg] : zero;
+#pragma unroll
+            for (int c = 0; c < SB - 1; ++c) {
+                const float yr = __shfl_sync(gmask, y.x, c, SB), yi = __shfl_sync(gmask, y.y, c, SB);
+                if (lg > c) {
+                    const float2 l = Lb[c * LD + (lg - c)];
                     y.x -= l.x * yr - l.y * yi;
                     y.y -= l.x * yi + l.y * yr;
                 }
             }
-            if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = y;
+            if (lg < nb) Y[slot(blk + lg) * SC + cg] = y;
         }
         __syncthreads();
-        // rows below the block inside the band: each thread owns two columns (q2, q2 + 16) and keeps
-        // the block's y of both in registers; Lb is zero past the band, so the loop has no tests
         {
-            const int q2 = tid & 15, rg = tid >> 4, nrg = nth >> 4;
-            float2 ya[NB], yc[NB];
+            float2 ya[SB], yc[SB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) {
-                ya[c] = Y[slot(blk + c) * SOLVE_COLS + q2];
-                yc[c] = Y[slot(blk + c) * SOLVE_COLS + q2 + 16];
+            for (int c = 0; c < SB; ++c) {
+                ya[c] = Y[slot(blk + c) * SC + q2];
+                yc[c] = Y[slot(blk + c) * SC + q2 + SC / 2];
             }
-            const int rlo = nb, rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
-            int sl = (int)((blk + rlo + rg) % WR);
-            for (int il = rlo + rg; il < rhi; il += nrg) {
+            const int rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
+            int sl = (int)((blk + nb + rg) % WR);
+            for (int il = nb + rg; il < rhi; il += nrg) {
                 float2 a0 = zero, a1 = zero;
                 const float2 *lrow = Lb + il;    // Lb[c * LD + il - c] = lrow[c * (LD - 1)]
 #pragma unroll
-                for (int c = 0; c < NB; ++c) {
+                for (int c = 0; c < SB; ++c) {
                     const float2 l = lrow[c * (LD - 1)];
                     a0.x += l.x * ya[c].x - l.y * ya[c].y;
                     a0.y += l.x * ya[c].y + l.y * ya[c].x;
                     a1.x += l.x * yc[c].x - l.y * yc[c].y;
                     a1.y += l.x * yc[c].y + l.y * yc[c].x;
                 }
-                float2 *yr = Y + sl * SOLVE_COLS;
+                float2 *yr = Y + sl * SC;
                 yr[q2].x -= a0.x; yr[q2].y -= a0.y;
-                yr[q2 + 16].x -= a1.x; yr[q2 + 16].y -= a1.y;
+                yr[q2 + SC / 2].x -= a1.x; yr[q2 + SC / 2].y -= a1.y;
                 sl += nrg;
-                if (sl >= WR) sl -= WR;
+                while (sl >= WR) sl -= WR;
             }
         }
         __syncthreads();
-        // block rows are final: write y / d, load the rows entering the window into their slots
-        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
+        for (int e = tid; e < nb * SC; e += ST) {
+            const int c = e / SC, qq = e % SC;
             const int64_t i = blk + c;
-            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SOLVE_COLS + qq], Lb[c * LD]);
+            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SC + qq], Lb[c * LD]);
             const int64_t inew = i + WR;
-            Y[slot(i) * SOLVE_COLS + qq] = (inew < n && qq < nrc) ? Rs[inew * ncol + qq] : zero;
+            Y[slot(i) * SC + qq] = (inew < n && qq < nrc) ? Rs[inew * ncol + qq] : zero;
         }
     }
     __syncthreads();
-    // ---------------- backward: L^T x = y' (in place in Z), blocks from the last one up.  The window
-    // holds rows [blk - b, blk + NB) at block blk; a finished block pushes its contributions
-    // x_k -= sum_{i in block} l_ik x_i to the rows k in [blk - b, blk) above it.
-    float2 *Ls = Lb;                                  // b x NB: Ls[(k - (blk - b)) * NB + c] = l_{blk+c, k}
-    float2 *Ld = Lb + (size_t)b * NB;                 // NB x NB: Ld[c2 * NB + c] = l_{blk+c, blk+c2}
-    const int64_t lastblk = ((n - 1) / NB) * NB;
-    for (int e = tid; e < WR * SOLVE_COLS; e += nth) Y[e] = zero;
+    // ---------------- backward: L^T x = y' (in place in Z); window holds rows [blk - b, blk + SB)
+    float2 *Ls = Lb;                                  // b x SB: Ls[(k - (blk - b)) * SB + c] = l_{blk+c, k}
+    float2 *Ld = Lb + (size_t)b * SB;                 // SB x SB: Ld[c2 * SB + c] = l_{blk+c, blk+c2}
+    const int64_t lastblk = ((n - 1) / SB) * SB;
+    for (int e = tid; e < WR * SC; e += ST) Y[e] = zero;
     __syncthreads();
-    for (int e = tid; e < WR * SOLVE_COLS; e += nth) {
-        const int64_t i = lastblk - b + e / SOLVE_COLS;
-        const int qq = e % SOLVE_COLS;
-        if (i >= 0 && i < n && qq < nrc) Y[slot(i) * SOLVE_COLS + qq] = Zs[i * ncol + qq];
+    for (int e = tid; e < WR * SC; e += ST) {
+        const int64_t i = lastblk - b + e / SC;
+        const int qq = e % SC;
+        if (i >= 0 && i < n && qq < nrc) Y[slot(i) * SC + qq] = Zs[i * ncol + qq];
     }
-    for (int64_t blk = lastblk; blk >= 0; blk -= NB) {
-        const int nb = (int)min((int64_t)NB, n - blk);
+    for (int64_t blk = lastblk; blk >= 0; blk -= SB) {
+        const int nb = (int)min((int64_t)SB, n - blk);
         __syncthreads();
-        // strip of L: columns k in [blk - b, blk), rows blk..blk+nb-1; and the in-block triangle
-        for (int e = tid; e < b * NB; e += nth) {
-            const int kk = e / NB, c = e % NB;
+        for (int e = tid; e < b * SB; e += ST) {
+            const int kk = e / SB, c = e % SB;
             const int64_t k = blk - b + kk;
             const int64_t off = blk + c - k;
             Ls[e] = (k >= 0 && c < nb && off <= b) ? AB[k * B1 + off] : zero;
         }
-        for (int e = tid; e < NB * NB; e += nth) {
-            const int c2 = e / NB, c = e % NB;
+        for (int e = tid; e < SB * SB; e += ST) {
+            const int c2 = e / SB, c = e % SB;
             Ld[e] = (c < nb && c2 < c && c - c2 <= b) ? AB[(blk + c2) * B1 + (c - c2)] : zero;
         }
         __syncthreads();
-        // in-block from the bottom: half-warp hw solves column hw
-        if (hw < SOLVE_COLS) {
-            float2 x = lane16 < nb ? Y[slot(blk + lane16) * SOLVE_COLS + hw] : zero;
-            for (int c = nb - 1; c > 0; --c) {
-                const float xr = __shfl_sync(0xffffffffu, x.x, c, 16), xi = __shfl_sync(0xffffffffu, x.y, c, 16);
-                if (lane16 < c) {
-                    const float2 l = Ld[lane16 * NB + c];
+        if (cg < SC) {
+            float2 x = lg < nb ? Y[slot(blk + lg) * SC + cg] : zero;
+#pragma unroll
+            for (int c = SB - 1; c > 0; --c) {
+                const float xr = __shfl_sync(gmask, x.x, c, SB), xi = __shfl_sync(gmask, x.y, c, SB);
+                if (lg < c) {
+                    const float2 l = Ld[lg * SB + c];
                     x.x -= l.x * xr - l.y * xi;
                     x.y -= l.x * xi + l.y * xr;
                 }
             }
-            if (lane16 < nb) Y[slot(blk + lane16) * SOLVE_COLS + hw] = x;
+            if (lg < nb) Y[slot(blk + lg) * SC + cg] = x;
         }
         __syncthreads();
-        // push to the rows above inside the band (two columns per thread); write the finished block
         {
-            const int q2 = tid & 15, rg = tid >> 4, nrg = nth >> 4;
-            float2 xa[NB], xc[NB];
+            float2 xa[SB], xc[SB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) {
-                xa[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q2] : zero;
-                xc[c] = c < nb ? Y[slot(blk + c) * SOLVE_COLS + q2 + 16] : zero;
+            for (int c = 0; c < SB; ++c) {
+                xa[c] = c < nb ? Y[slot(blk + c) * SC + q2] : zero;
+                xc[c] = c < nb ? Y[slot(blk + c) * SC + q2 + SC / 2] : zero;
             }
             const int kklo = (int)(max((int64_t)0, blk - b) - (blk - b));
             int sl = (int)(((blk - b + kklo + rg) % WR + WR) % WR);
             for (int kk = kklo + rg; kk < b; kk += nrg) {
-                const float2 *lrow = Ls + kk * NB;
+                const float2 *lrow = Ls + kk * SB;
                 float2 a0 = zero, a1 = zero;
 #pragma unroll
-                for (int c = 0; c < NB; ++c) {
+                for (int c = 0; c < SB; ++c) {
                     const float2 l = lrow[c];
                     a0.x += l.x * xa[c].x - l.y * xa[c].y;
                     a0.y += l.x * xa[c].y + l.y * xa[c].x;
                     a1.x += l.x * xc[c].x - l.y * xc[c].y;
                     a1.y += l.x * xc[c].y + l.y * xc[c].x;
                 }
-                float2 *yr = Y + sl * SOLVE_COLS;
+                float2 *yr = Y + sl * SC;
                 yr[q2].x -= a0.x; yr[q2].y -= a0.y;
-                yr[q2 + 16].x -= a1.x; yr[q2 + 16].y -= a1.y;
+                yr[q2 + SC / 2].x -= a1.x; yr[q2 + SC / 2].y -= a1.y;
                 sl += nrg;
-                if (sl >= WR) sl -= WR;
+                while (sl >= WR) sl -= WR;
             }
         }
-        for (int e = tid; e < nb * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
-            if (qq < nrc) Zs[(blk + c) * ncol + qq] = Y[slot(blk + c) * SOLVE_COLS + qq];
+        for (int e = tid; e < nb * SC; e += ST) {
+            const int c = e / SC, qq = e % SC;
+            if (qq < nrc) Zs[(blk + c) * ncol + qq] = Y[slot(blk + c) * SC + qq];
         }
         if (blk == 0) break;
         __syncthreads();
-        // rows [blk - b - NB, blk - b) enter the slots of the finished block
-        for (int e = tid; e < NB * SOLVE_COLS; e += nth) {
-            const int c = e / SOLVE_COLS, qq = e % SOLVE_COLS;
-            const int64_t inew = blk - b - NB + c;
-            Y[slot(blk + c) * SOLVE_COLS + qq] = (inew >= 0 && qq < nrc) ? Zs[inew * ncol + qq] : zero;
+        for (int e = tid; e < SB * SC; e += ST) {
+            const int c = e / SC, qq = e % SC;
+            const int64_t inew = blk - b - SB + c;
+            Y[slot(blk + c) * SC + qq] = (inew >= 0 && qq < nrc) ? Zs[inew * ncol + qq] : zero;
         }
     }
 }
@@ -445,8 +443,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
 size_t band_smem_solve(int b)
 {
-    // window + max(forward L block NB x (b+1+NB), backward strip b x NB + in-block NB x NB)
-    return sizeof(float2) * ((size_t)(b + NB) * SOLVE_COLS + std::max((size_t)NB * (b + 1 + NB), (size_t)b * NB + NB * NB));
+    // window + max(forward L block SB x (b + 1 + SB), backward strip b x SB + in-block SB x SB)
+    return sizeof(float2) * ((size_t)(b + SB) * SC + std::max((size_t)SB * (b + 1 + SB), (size_t)b * SB + SB * SB));
 }
 
 bool band_feasible(const Ctx *c, int b)
@@ -493,10 +491,10 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     const int64_t n = p->n;
     const size_t smem = band_smem_solve(b);
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int ngrp = (ncol + SOLVE_COLS - 1) / SOLVE_COLS;
+    const int ngrp = (ncol + SC - 1) / SC;
     const double macs = 2.0 * nact * n * b * ncol;
     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
-    k_band_solve<<<nshift * ngrp, 512, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
+    k_band_solve<<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
