@@ -781,8 +781,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Y, pY));
                 int rank = 0;
-                // directions below 1e-10 of the largest Gram eigenvalue carry mostly solve noise (spurious Ritz values)
-                GCIE_TRY(m_orthonormalize(c, p, n, pY, Y, 1e-10, Q, &rank));
+                GCIE_TRY(m_orthonormalize(c, p, n, pY, Y, 1e-14, Q, &rank));
                 double *Qc = nullptr, *Z = nullptr;
                 GCIE_CUDA_TRY(cudaMalloc(&Qc, sizeof(double) * (size_t)n * rank));
                 guard.ptrs.push_back(Qc);

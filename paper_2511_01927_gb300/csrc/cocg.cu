@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
 // eta_ref are in the scaled FP32 system; eta_abs and bnorm2 are absolute FP64 squared norms.
 struct Scal {
     double2 *rho, *alpha, *beta;
-    double *eta, *eta_ref, *bnorm2, *scale, *scale_next, *eta_best;
+    double *eta, *eta_ref, *bnorm2, *scale, *scale_next, *eta_best, *sratio;
     int *flag, *shift_active, *shift_refine, *since_refine, *stall;
     double2 *partA;
     double *partB;
@@ -331,8 +331,10 @@ __global__ void k_scal_alpha(int ncol, int chunks, Scal S)
     S.alpha[sc] = a;
 }
 
-__global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int rho_chunks,
-                            double delta2, double tol2, int max_since)
+// After the update sweep: decide per shift whether to refine now (all active columns want it, or too
+// many iterations since the last update) and the scale of that update.  Columns want an update when
+// the recursive residual fell by delta since the last one, looks converged, or broke down.
+__global__ void k_scal_check(int ncol, int chunks, Scal S, double delta2, double tol2, int max_since)
 {
     __shared__ int all_want;
     const int s = blockIdx.x, l = threadIdx.x;
@@ -341,24 +343,12 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restr
     __syncthreads();
     if (l < ncol) {
         const int64_t sc = (int64_t)s * ncol + l;
-        int f = S.flag[sc];
+        const int f = S.flag[sc];
         int want = 1;
         if (f & F_ACTIVE) {
-            double2 rho = make_double2(0, 0);
             double eta = 0;
             for (int c = 0; c < chunks; ++c) eta += S.partB[((int64_t)s * chunks + c) * ncol + l];
-            for (int c = 0; c < rho_chunks; ++c) {
-                double2 v = rho_part[((int64_t)s * rho_chunks + c) * ncol + l];
-                rho.x += v.x; rho.y += v.y;
-            }
-            double2 ro = S.rho[sc];
-            double2 b = make_double2(0, 0);
-            if (fabs(ro.x) + fabs(ro.y) > 0) b = cdiv(rho, ro);
-            if (!(isfinite(b.x) && isfinite(b.y))) { b = make_double2(0, 0); f |= F_RESTART; }
-            S.beta[sc] = b;
-            S.rho[sc] = rho;
             S.eta[sc] = eta;
-            S.flag[sc] = f;
             const double sc2 = S.scale[sc] * S.scale[sc];
             want = (eta <= delta2 * S.eta_ref[sc]) || (eta * sc2 <= tol2 * S.bnorm2[sc]) || (f & F_RESTART) ||
                    !isfinite(eta);
@@ -376,10 +366,38 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restr
     }
 }
 
-// After the update: absolute residual norms decide convergence; the scaled system restarts at
-// eta = eta_abs / scale^2 with the new scale.
-__global__ void k_scal_refine(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int rho_chunks,
-                              double tol2)
+// After the (optional) update and the (optional) preconditioner: rho' = r^T z (z = r without
+// preconditioner), beta = rho'/rho with the scale change of an update folded in: the old direction is
+// in units of the old scale, so in the new units beta picks up the factor s_new / s_old.
+__global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int first)
+{
+    const int s = blockIdx.x, l = threadIdx.x;
+    if (!S.shift_active[s] || l >= ncol) return;
+    const int64_t sc = (int64_t)s * ncol + l;
+    int f = S.flag[sc];
+    if (!(f & F_ACTIVE)) { S.beta[sc] = make_double2(0, 0); S.sratio[sc] = 1.0; return; }
+    double2 rho = make_double2(0, 0);
+    for (int c = 0; c < chunks; ++c) {
+        const double2 v = rho_part[((int64_t)s * chunks + c) * ncol + l];
+        rho.x += v.x; rho.y += v.y;
+    }
+    const double2 ro = S.rho[sc];
+    double2 b = make_double2(0, 0);
+    if (!first && !(f & F_RESTART) && (fabs(ro.x) + fabs(ro.y)) > 0) {
+        b = cdiv(rho, ro);
+        b.x *= S.sratio[sc];
+        b.y *= S.sratio[sc];
+        if (!(isfinite(b.x) && isfinite(b.y))) b = make_double2(0, 0);
+    }
+    if (f & F_RESTART) S.flag[sc] = f & ~F_RESTART;
+    S.beta[sc] = b;
+    S.rho[sc] = rho;
+    S.sratio[sc] = 1.0;
+}
+
+// After an update: absolute residual norms decide convergence (or stagnation); the scaled system
+// restarts at eta = eta_abs / scale^2 with the new scale, and the ratio of the scales is kept for beta.
+__global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
 {
     __shared__ int any_active;
     const int s = blockIdx.x, l = threadIdx.x;
@@ -388,22 +406,17 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, const double2 *__res
     __syncthreads();
     if (l < ncol) {
         const int64_t sc = (int64_t)s * ncol + l;
-        double2 rho = make_double2(0, 0);
         double eta_abs = 0;
         for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
-        for (int c = 0; c < rho_chunks; ++c) {
-            double2 v = rho_part[((int64_t)s * rho_chunks + c) * ncol + l];
-            rho.x += v.x; rho.y += v.y;
-        }
         int f = S.flag[sc];
         const double sn = S.scale_next[sc];
+        S.sratio[sc] = sn / S.scale[sc];
         S.scale[sc] = sn;
         const double eta_s = eta_abs / (sn * sn);
         S.eta_ref[sc] = eta_s;
         if (f & F_ACTIVE) {
             S.eta[sc] = eta_s;
-            S.rho[sc] = rho;
-            // stagnation: the true residual has to drop 4x every few updates (FP64 rounding sets a
+            // stagnation: the true residual has to drop 16x every few updates (FP64 rounding sets a
             // floor that some columns cannot pass)
             if (eta_abs < 0.0625 * S.eta_best[sc]) {
                 S.eta_best[sc] = eta_abs;
@@ -411,16 +424,8 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, const double2 *__res
             } else {
                 S.stall[sc] += 1;
             }
-            if (eta_abs <= tol2 * S.bnorm2[sc]) {
-                f = F_CONV;
-                S.beta[sc] = make_double2(0, 0);
-            } else if (S.stall[sc] >= STALL_UPDATES || !isfinite(eta_abs)) {
-                f = F_STALL;
-                S.beta[sc] = make_double2(0, 0);
-            } else if (f & F_RESTART) {
-                f &= ~F_RESTART;
-                S.beta[sc] = make_double2(0, 0);
-            }
+            if (eta_abs <= tol2 * S.bnorm2[sc]) f = F_CONV;
+            else if (S.stall[sc] >= STALL_UPDATES || !isfinite(eta_abs)) f = F_STALL;
             S.flag[sc] = f;
         }
         if (f & F_ACTIVE) atomicOr(&any_active, 1);
@@ -475,6 +480,7 @@ __global__ void k_bnorm_init(int ncol, int chunks, const int *__restrict__ rhs_o
         S.scale[sc] = 1.0;
         S.scale_next[sc] = 1.0;
         S.eta_best[sc] = INFINITY;
+        S.sratio[sc] = 1.0;
         S.stall[sc] = 0;
     }
     if (threadIdx.x == 0) { S.shift_active[s] = 1; S.shift_refine[s] = 1; S.since_refine[s] = 0; }
@@ -505,7 +511,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     const int64_t n = p->n;
     if (ncol % CPT || ncol > 1024 || ncol <= 0) { set_error("cocg: ncol must be even and <= 1024"); return GCIE_EINVAL; }
     Geo g = make_geo(c, n, nshift, ncol, CPT);
-    Geo gr = make_geo(c, n, nshift, ncol, ncol % 2 ? 1 : 2);  // refinement sweep
+    const Geo &gr = g;   // refinement sweep: same tiles, so partial sums of both land in the same slots
     const int64_t blk = (int64_t)nshift * n * ncol;
     const int ntiles = nshift * g.chunks, ntiles_r = nshift * gr.chunks;
     const int maxch = std::max(g.chunks, gr.chunks);
@@ -514,8 +520,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     const size_t sizes[] = {blk * sizeof(C), blk * sizeof(C), blk * sizeof(C), blk * sizeof(C),
                             ns * sizeof(double2), ns * sizeof(double2), ns * sizeof(double2),
                             ns * sizeof(double), ns * sizeof(double), ns * sizeof(double), ns * sizeof(double),
-                            ns * sizeof(double), ns * sizeof(double), ns * sizeof(int), ns * sizeof(int),
-                            nshift * sizeof(int), nshift * sizeof(int),
+                            ns * sizeof(double), ns * sizeof(double), ns * sizeof(double), ns * sizeof(int),
+                            ns * sizeof(int), nshift * sizeof(int), nshift * sizeof(int),
                             nshift * sizeof(int), (size_t)nshift * maxch * ncol * sizeof(double2),
                             (size_t)nshift * maxch * ncol * sizeof(double), nshift * sizeof(double2),
                             nshift * sizeof(int),
@@ -547,6 +553,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     S.scale = (double *)take();
     S.scale_next = (double *)take();
     S.eta_best = (double *)take();
+    S.sratio = (double *)take();
     S.flag = (int *)take();
     S.stall = (int *)take();
     S.shift_active = (int *)take();
@@ -615,14 +622,9 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     auto refine_r = [&](int nact, int norm_only) -> int {
         LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
                        (double)nact * p->nnz * ncol * 8.0);
-        if (ncol % 2 == 0)
-            k_refine_r<T, 2><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
-                ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
-                S.partA, S.partB);
-        else
-            k_refine_r<T, 1><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
-                ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
-                S.partA, S.partB);
+        k_refine_r<T, CPT><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
+            ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
+            S.partA, S.partB);
         GCIE_CUDA_TRY(cudaGetLastError());
         return GCIE_OK;
     };
@@ -633,12 +635,19 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         GCIE_TRY(refine_r(nact, 0));
-        if (prec) GCIE_TRY(apply_prec(S.shift_refine, nact));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, rho_part, prec ? g.chunks : gr.chunks, tol2);
+            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
+        return GCIE_OK;
+    };
+    // z = M^-1 r on the active shifts and the new beta (first: no previous direction)
+    auto precond_beta = [&](int nact, int first) -> int {
+        if (prec) GCIE_TRY(apply_prec(S.shift_active, nact));
+        LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
+        k_scal_beta<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, rho_part, first);
+        GCIE_CUDA_TRY(cudaGetLastError());
         return GCIE_OK;
     };
     // first update: exact scale from a norm-only residual pass, then the scaled residual
@@ -650,6 +659,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     rc = refine(nshift);
+    if (rc) goto done;
+    rc = precond_beta(nshift, 1);
     if (rc) goto done;
     {
         const int check_every = 8;
@@ -681,17 +692,14 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                         g.rows_per_chunk, g.chunks, S.shift_active, S.alpha, Pnew, D, R, S.partA, S.partB);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
-                if (prec) {
-                    rc = apply_prec(S.shift_active, active_shifts);
-                    if (rc) goto done;
-                }
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-                    k_scal_beta<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, rho_part, g.chunks, delta2, tol2,
-                                                                    max_since);
+                    k_scal_check<<<nshift, sthreads, 0, c->stream>>>(ncol, g.chunks, S, delta2, tol2, max_since);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 rc = refine(0);
+                if (rc) goto done;
+                rc = precond_beta(active_shifts, 0);
                 if (rc) goto done;
             }
         }
