@@ -30,7 +30,7 @@
 
 namespace gcie {
 
-enum : int { F_ACTIVE = 1, F_CONV = 2, F_RESTART = 4, F_STALL = 8 };
+enum : int { F_ACTIVE = 1, F_CONV = 2, F_RESTART = 4, F_STALL = 8, F_UPDATED = 16 };
 constexpr int STALL_UPDATES = 4;   // updates without a 4x drop of the true residual before a column stops
 
 template <typename T, int CPT> struct V2;
@@ -367,8 +367,9 @@ __global__ void k_scal_check(int ncol, int chunks, Scal S, double delta2, double
 }
 
 // After the (optional) update and the (optional) preconditioner: rho' = r^T z (z = r without
-// preconditioner), beta = rho'/rho with the scale change of an update folded in: the old direction is
-// in units of the old scale, so in the new units beta picks up the factor s_new / s_old.
+// preconditioner) and beta = rho'/rho.  A column whose residual was just replaced by the true one
+// restarts its direction (beta = 0): continuing the COCG recurrence across the replacement diverges
+// on these indefinite systems in FP32.
 __global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restrict__ rho_part, int first)
 {
     const int s = blockIdx.x, l = threadIdx.x;
@@ -383,13 +384,11 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restr
     }
     const double2 ro = S.rho[sc];
     double2 b = make_double2(0, 0);
-    if (!first && !(f & F_RESTART) && (fabs(ro.x) + fabs(ro.y)) > 0) {
+    if (!first && !(f & (F_RESTART | F_UPDATED)) && (fabs(ro.x) + fabs(ro.y)) > 0) {
         b = cdiv(rho, ro);
-        b.x *= S.sratio[sc];
-        b.y *= S.sratio[sc];
         if (!(isfinite(b.x) && isfinite(b.y))) b = make_double2(0, 0);
     }
-    if (f & F_RESTART) S.flag[sc] = f & ~F_RESTART;
+    if (f & (F_RESTART | F_UPDATED)) S.flag[sc] = f & ~(F_RESTART | F_UPDATED);
     S.beta[sc] = b;
     S.rho[sc] = rho;
     S.sratio[sc] = 1.0;
@@ -426,6 +425,7 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
             }
             if (eta_abs <= tol2 * S.bnorm2[sc]) f = F_CONV;
             else if (S.stall[sc] >= STALL_UPDATES || !isfinite(eta_abs)) f = F_STALL;
+            else f |= F_UPDATED;
             S.flag[sc] = f;
         }
         if (f & F_ACTIVE) atomicOr(&any_active, 1);
