@@ -604,6 +604,8 @@ struct ContourState {
     int iters = 0;
     bool done = false;
     int status = GCIE_OK;
+    int prev_conv = -1;        // converged pairs inside I_k after the previous FEAST iteration
+    double prev_worst = 0.0;   // worst residual of the unconverged ones
     // kept pairs
     std::vector<double> kv, kr;
     std::vector<double> kvec;   // column-major n x kept
@@ -795,13 +797,24 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 rc = rayleigh_ritz(c, p, rank, Qc, Z, th.data(), rs.data());
                 if (rc) { cudaFree(Z); return rc; }
                 bool unconverged_inside = false;
+                double worst = 0.0;
                 std::vector<int> keep;
                 for (int l = 0; l < rank; ++l) {
                     const bool inside = th[l] >= s.lo && th[l] <= s.hi;
                     if (!inside) continue;
                     if (rs[l] <= o->tol) keep.push_back(l);
-                    else unconverged_inside = true;
+                    else { unconverged_inside = true; worst = std::max(worst, rs[l]); }
                 }
+                // An iteration that adds no converged pair and does not improve the worst remaining
+                // residual 10x leaves only Ritz values that do not converge: spurious ones, built from
+                // basis directions dominated by solve noise, which move from one iteration to the next.
+                // The contour stops; remaining residuals above 1e-6 are taken as spurious (status OK),
+                // lower ones as a stalled eigenpair (GCIE_ENOCONV).
+                bool stalled = false;
+                if (unconverged_inside && it > 0 && (int)keep.size() <= s.prev_conv && worst >= 0.1 * s.prev_worst)
+                    stalled = true;
+                s.prev_conv = (int)keep.size();
+                s.prev_worst = worst;
                 s.iters = it + 1;
                 const bool last = (it + 1 == o->max_outer);
                 if (std::getenv("GCIE_VERBOSE")) {
@@ -815,7 +828,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     fprintf(stderr, "[gcie] contour %d it %d: rank %d, %d Ritz values inside [%.6g, %.6g], %zu converged, "
                             "worst residual %.3e at %.10g\n", act[b0 + bi], it, rank, nin, s.lo, s.hi, keep.size(), worst, wth);
                 }
-                if (!unconverged_inside || last) {
+                if (!unconverged_inside || last || stalled) {
                     // final: keep converged pairs
                     if (!keep.empty()) {
                         int *didx = nullptr;
@@ -838,7 +851,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                         for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
                     }
                     s.done = true;
-                    s.status = unconverged_inside ? GCIE_ENOCONV : GCIE_OK;
+                    s.status = (unconverged_inside && !(stalled && worst > 1e-6)) ? GCIE_ENOCONV : GCIE_OK;
                     cudaFree(Z);
                     if (s.Z) { cudaFree(s.Z); s.Z = nullptr; }
                 } else {

@@ -588,7 +588,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     for (int s = 0; s < nshift; ++s) hz[s] = make_double2(h_z[2 * s], h_z[2 * s + 1]);
     std::vector<int> hact(nshift, 1);
     int64_t iters = 0;
-    const double delta2 = sizeof(T) == 4 ? 1e-8 : 0.0;   // FP32: update after a 1e4 drop
+    const double delta2 = sizeof(T) == 4 ? 1e-10 : 0.0;  // FP32: update after a 1e5 drop
     const double tol2 = lin_tol * lin_tol;
     const int max_since = sizeof(T) == 4 ? 4000 : 1 << 30;
     const size_t smem = (size_t)256 * CPT * 3 * sizeof(double) + 64;
