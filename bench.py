@@ -39,7 +39,34 @@ def parse():
     ap.add_argument("--workload", default="fem2d-p1-500")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",
+                    help="run only a small shifted solve (NODES nodes of the first contour, L columns, band "
+                         "preconditioner, 4 iterations) for kernel profiling, then exit")
     return ap.parse_args()
+
+
+def profile_case(args):
+    """A reduced launch of the hot kernels for ncu: the shifted solves of a few nodes of the workload
+    (same pencil, bandwidth and column count as the full solve, fewer nodes)."""
+    import torch
+    import paper_2511_01927_gb300 as G
+
+    K, M, spec = P.workload(args.workload)
+    V = P.gaussian_block(K.n, spec["L"], 1)
+    B = torch.from_numpy(M.to_scipy() @ V).cuda()
+    c = spec["lo"] + 0.5 * (spec["hi"] - spec["lo"]) / spec["contours"]
+    r = 0.5 * (spec["hi"] - spec["lo"]) / spec["contours"]
+    z, _ = G.gcie_trapezoid_nodes(c, r, spec["nodes"])
+    z = z[:args.profile_case]
+    ctx = G.gcie_create(0, torch.cuda.current_stream().cuda_stream)
+    pen = G.gcie_pencil_create(ctx, K, M)
+    X = torch.zeros((len(z), K.n, spec["L"]), dtype=torch.complex128, device="cuda")
+    it, rc = G.gcie_shifted_solve(ctx, pen, z, spec["L"], B, X, lin_tol=1e-11, max_iters=4, precond=3,
+                                  allow_noconv=True)
+    torch.cuda.synchronize()
+    G.gcie_pencil_destroy(pen)
+    G.gcie_destroy(ctx)
+    print(json.dumps({"profile_case": args.workload, "nodes": len(z), "iters": it, "rc": rc}))
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -225,6 +252,9 @@ def cpu_cores():
 # ----------------------------------------------------------------------------- main
 def main():
     args = parse()
+    if args.profile_case:
+        profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1:
@@ -292,6 +322,7 @@ def main():
                       "contours": spec["contours"], "nodes": spec["nodes"], "L": spec["L"],
                       "moments": spec["moments"], "tol": 1e-10, "l2": "inputs larger than L2 (16 GB block)",
                       "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
+                      "feast_iters_per_contour": r["last"]["iters"],
                       "cocg_iters": r["last"]["cocg_iters"]},
            "roofline": roof,
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
