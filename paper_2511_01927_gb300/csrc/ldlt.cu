@@ -19,7 +19,8 @@
 //                    is factored in shared memory, then the trailing b x b triangle receives the
 //                    rank-NB update L_p D_p L_p^T (tiles of 4 x 4 per thread);
 //   k_band_solve     z = L^-T D^-1 L^-1 r for a group of right-hand sides, with a sliding window of
-//                    b + NB rows in shared memory for each sweep.
+//                    b + 2 SB rows in shared memory for each sweep and the factor columns of the
+//                    next block step copied in asynchronously.
 #include <algorithm>
 #include <cmath>
 
@@ -187,58 +188,110 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 }
 
 // ------------------------------------------------------------------ triangular sweeps
-// z = L^-T D^-1 L^-1 r for SC right-hand sides of one shift per CTA (256 threads, two CTAs per SM).
-// The window Y holds b + SB consecutive rows (slot = row mod (b + SB)).  Per block of SB rows:
-//   forward : load the block's columns of L (zero-padded past the band), solve the SB x SB unit
-//             triangle with SB-lane groups (one column each, shuffles), subtract the block's
-//             contribution from the b rows below (each thread: two columns, a set of rows, the
-//             block's y in registers), write y / d, load the rows entering the window;
-//   backward: load the strip l_{block, k} for the b rows k above, solve the triangle from the
-//             bottom, push the block's x to the rows above, write x, load the rows entering.
+// z = L^-T D^-1 L^-1 r for SC right-hand sides of one shift per CTA (ST threads).  The window Y
+// holds b + 2 SB consecutive rows (slot = row mod (b + 2 SB)): the b + SB rows a block step works
+// on and SB more that are being loaded for the next step.  Per block of SB rows:
+//   forward : solve the SB x SB unit triangle with SB-lane groups (one column each, shuffles),
+//             write y / d, subtract the block's contribution from the b rows below (each thread:
+//             two columns, a set of rows, the block's y in registers);
+//   backward: solve the triangle from the bottom with the SB x SB diagonal block, write x, push the
+//             block's x to the b rows above through the strip l_{block, k}.
+// Everything a step reads from global memory (its columns of L, the rows entering the window) is
+// copied with cp.async during the previous step into a second buffer, so a step waits on no global
+// load and needs two barriers.
 constexpr int SB = 8;         // rows per block of the sweeps
-constexpr int SC = 16;        // right-hand sides per CTA of the sweeps
-constexpr int ST = 256;       // threads per CTA of the sweeps
+constexpr int ST = 512;       // threads per CTA of the sweeps
 
-__global__ void __launch_bounds__(ST, 2) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
+__device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+template <int SC>
+__global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
 {
-    extern __shared__ float2 sm2[];
+    constexpr int QT = SC / 2;                        // threads per row in the updates (columns q, q + QT)
+    constexpr int RG = ST / QT;                       // row groups of the updates
+    static_assert(SB * SC <= ST, "in-block solve needs SB x SC threads");
+    extern __shared__ float4 sm4[];                   // 16-byte aligned: the backward strip is read as float4
+    float2 *sm2 = reinterpret_cast<float2 *>(sm4);
     const int ngrp = (ncol + SC - 1) / SC;
     const int s = blockIdx.x / ngrp, g = blockIdx.x % ngrp;
     if (!mask[s]) return;
     const int c0 = g * SC;
     const int nrc = min(SC, ncol - c0);
     const int B1 = b + 1;
+    const int LD = B1 + SB;                           // padded column length of the forward slab
+    const int WR = b + 2 * SB;
+    const int LBS = SB * LD;                          // one slab buffer (>= b SB + SB SB of the backward)
     const float2 *AB = ABp[s];
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
-    const int WR = b + SB;
-    const int LD = B1 + SB;                           // padded column length of Lb (zeros past the band)
     float2 *Y = sm2;                                  // WR x SC
-    float2 *Lb = Y + (size_t)WR * SC;                 // SB x LD (forward) | b x SB strip + SB x SB (backward)
+    float2 *Lbuf = Y + (size_t)WR * SC;               // 2 x LBS
     const int tid = threadIdx.x;
-    const int lg = tid & (SB - 1);                    // row of the block in the in-block solve
-    const int cg = tid / SB;                          // column of the in-block solve (cg < SC active)
+    const int lg = tid % SB, cg = tid / SB;           // in-block solve: row lg of the block, column cg
     const unsigned gmask = 0xffffffffu;
-    const int q2 = tid % (SC / 2), rg = tid / (SC / 2), nrg = ST / (SC / 2);
-    auto slot = [&](int64_t i) { return (int)(i % WR); };
+    const int q2 = tid % QT, rg = tid / QT;
     const float2 zero = make_float2(0.f, 0.f);
+    const int64_t nblk = (n + SB - 1) / SB;
 
-    // ---------------- forward: L y = r, then y' = y / d written to Z
-    for (int e = tid; e < WR * SC; e += ST) {
-        const int t = e / SC, c = e % SC;
-        Y[e] = (t < n && c < nrc) ? Rs[(int64_t)t * ncol + c] : zero;
-    }
-    for (int64_t blk = 0; blk < n; blk += SB) {
-        const int nb = (int)min((int64_t)SB, n - blk);
-        __syncthreads();
-        for (int e = tid; e < SB * LD; e += ST) {
-            const int c = e / LD, t = e % LD;
-            Lb[e] = (c < nb && t < B1) ? AB[(blk + c) * B1 + t] : zero;
+    // rows [r0, r0 + SB) of src (zero outside [0, n) and past the CTA's columns) into the window,
+    // row r0 + c at slot slot0 + c (mod WR)
+    auto rows_async = [&](int64_t r0, int slot0, const float2 *src) {
+        for (int e = tid; e < SB * SC; e += ST) {
+            const int c = e / SC, qq = e % SC;
+            const int64_t i = r0 + c;
+            int sl = slot0 + c;
+            if (sl >= WR) sl -= WR;
+            float2 *dst = Y + sl * SC + qq;
+            if (i >= 0 && i < n && qq < nrc) cp_async8(dst, src + i * ncol + qq);
+            else *dst = zero;
         }
+    };
+
+    // ---------------- forward: L y = r, then y / d written to Z
+    // slab of block blk: L[c * LD + t] = l_{blk+c+t, blk+c} (t <= b); t in (b, LD) stays zero
+    auto fwd_slab = [&](int64_t blk, float2 *L) {
+        const int nb = (int)min((int64_t)SB, n - blk);
+        for (int c = 0; c < SB; ++c) {
+            if (c < nb)
+                for (int t = tid; t < B1; t += ST) cp_async8(L + c * LD + t, AB + (blk + c) * B1 + t);
+            else
+                for (int t = tid; t < B1; t += ST) L[c * LD + t] = zero;
+        }
+    };
+    for (int c = 0; c < 2 * SB; ++c)
+        for (int t = B1 + tid; t < LD; t += ST) Lbuf[c * LD + t] = zero;
+    for (int e = tid; e < (b + SB) * SC; e += ST) {
+        const int t = e / SC, qq = e % SC;
+        if (t < n && qq < nrc) cp_async8(Y + e, Rs + (int64_t)t * ncol + qq);
+        else Y[e] = zero;
+    }
+    fwd_slab(0, Lbuf);
+    cp_async_commit();
+    int bs = 0;                                       // slot of row blk
+    for (int64_t kb = 0; kb < nblk; ++kb) {
+        const int64_t blk = kb * SB;
+        const int nb = (int)min((int64_t)SB, n - blk);
+        const float2 *Lb = Lbuf + (kb & 1) * LBS;
+        auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
+        cp_async_wait_all();
         __syncthreads();
+        // next step's slab and the rows entering the window then (slots of the previous block)
+        if (kb + 1 < nblk) fwd_slab(blk + SB, Lbuf + ((kb + 1) & 1) * LBS);
+        {
+            int s0 = bs + b + SB;
+            while (s0 >= WR) s0 -= WR;
+            rows_async(blk + b + SB, s0, Rs);
+        }
+        cp_async_commit();
         if (cg < SC) {
-            float2 y = lg < nb ? Y[slot(blk + lg) * SC + cg] : zero;
+            float2 y = lg < nb ? Y[bslot(lg) * SC + cg] : zero;
 #pragma unroll
             for (int c = 0; c < SB - 1; ++c) {
                 const float yr = __shfl_sync(gmask, y.x, c, SB), yi = __shfl_sync(gmask, y.y, c, SB);
@@ -248,19 +301,23 @@ __global__ void __launch_bounds__(ST, 2) k_band_solve(int64_t n, int b, int ncol
                     y.y -= l.x * yi + l.y * yr;
                 }
             }
-            if (lg < nb) Y[slot(blk + lg) * SC + cg] = y;
+            if (lg < nb) {
+                Y[bslot(lg) * SC + cg] = y;
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cdivf(y, Lb[lg * LD]);
+            }
         }
         __syncthreads();
         {
             float2 ya[SB], yc[SB];
 #pragma unroll
             for (int c = 0; c < SB; ++c) {
-                ya[c] = Y[slot(blk + c) * SC + q2];
-                yc[c] = Y[slot(blk + c) * SC + q2 + SC / 2];
+                ya[c] = c < nb ? Y[bslot(c) * SC + q2] : zero;
+                yc[c] = c < nb ? Y[bslot(c) * SC + q2 + QT] : zero;
             }
             const int rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
-            int sl = (int)((blk + nb + rg) % WR);
-            for (int il = nb + rg; il < rhi; il += nrg) {
+            int sl = bs + nb + rg;
+            while (sl >= WR) sl -= WR;
+            for (int il = nb + rg; il < rhi; il += RG) {
                 float2 a0 = zero, a1 = zero;
                 const float2 *lrow = Lb + il;    // Lb[c * LD + il - c] = lrow[c * (LD - 1)]
 #pragma unroll
@@ -272,49 +329,69 @@ __global__ void __launch_bounds__(ST, 2) k_band_solve(int64_t n, int b, int ncol
                     a1.y += l.x * yc[c].y + l.y * yc[c].x;
                 }
                 float2 *yr = Y + sl * SC;
-                yr[q2].x -= a0.x; yr[q2].y -= a0.y;
-                yr[q2 + SC / 2].x -= a1.x; yr[q2 + SC / 2].y -= a1.y;
-                sl += nrg;
+                float2 v0 = yr[q2], v1 = yr[q2 + QT];
+                v0.x -= a0.x; v0.y -= a0.y;
+                v1.x -= a1.x; v1.y -= a1.y;
+                yr[q2] = v0;
+                yr[q2 + QT] = v1;
+                sl += RG;
                 while (sl >= WR) sl -= WR;
             }
         }
-        __syncthreads();
-        for (int e = tid; e < nb * SC; e += ST) {
-            const int c = e / SC, qq = e % SC;
-            const int64_t i = blk + c;
-            if (qq < nrc) Zs[i * ncol + qq] = cdivf(Y[slot(i) * SC + qq], Lb[c * LD]);
-            const int64_t inew = i + WR;
-            Y[slot(i) * SC + qq] = (inew < n && qq < nrc) ? Rs[inew * ncol + qq] : zero;
-        }
+        bs += SB;
+        if (bs >= WR) bs -= WR;
     }
+    cp_async_wait_all();
     __syncthreads();
-    // ---------------- backward: L^T x = y' (in place in Z); window holds rows [blk - b, blk + SB)
-    float2 *Ls = Lb;                                  // b x SB: Ls[(k - (blk - b)) * SB + c] = l_{blk+c, k}
-    float2 *Ld = Lb + (size_t)b * SB;                 // SB x SB: Ld[c2 * SB + c] = l_{blk+c, blk+c2}
-    const int64_t lastblk = ((n - 1) / SB) * SB;
-    for (int e = tid; e < WR * SC; e += ST) Y[e] = zero;
-    __syncthreads();
-    for (int e = tid; e < WR * SC; e += ST) {
-        const int64_t i = lastblk - b + e / SC;
-        const int qq = e % SC;
-        if (i >= 0 && i < n && qq < nrc) Y[slot(i) * SC + qq] = Zs[i * ncol + qq];
-    }
-    for (int64_t blk = lastblk; blk >= 0; blk -= SB) {
+
+    // ---------------- backward: L^T x = y' (in place in Z); window rows [blk - b, blk + SB)
+    // slab of block blk: Ls[kk * SB + c] = l_{blk+c, blk-b+kk} (b x SB), Ld[c2 * SB + c] = l_{blk+c, blk+c2}
+    auto bwd_slab = [&](int64_t blk, float2 *L) {
         const int nb = (int)min((int64_t)SB, n - blk);
-        __syncthreads();
+        float2 *Ls = L, *Ld = L + (size_t)b * SB;
         for (int e = tid; e < b * SB; e += ST) {
             const int kk = e / SB, c = e % SB;
-            const int64_t k = blk - b + kk;
-            const int64_t off = blk + c - k;
-            Ls[e] = (k >= 0 && c < nb && off <= b) ? AB[k * B1 + off] : zero;
+            const int64_t k = blk - b + kk;           // column k, row blk + c = k + (b - kk + c)
+            if (k >= 0 && c < nb && c <= kk) cp_async8(Ls + e, AB + k * B1 + (b - kk + c));
+            else Ls[e] = zero;
         }
         for (int e = tid; e < SB * SB; e += ST) {
             const int c2 = e / SB, c = e % SB;
-            Ld[e] = (c < nb && c2 < c && c - c2 <= b) ? AB[(blk + c2) * B1 + (c - c2)] : zero;
+            if (c < nb && c2 < c && c - c2 <= b) cp_async8(Ld + e, AB + (blk + c2) * B1 + (c - c2));
+            else Ld[e] = zero;
         }
+    };
+    const int64_t lastblk = (nblk - 1) * SB;
+    bs = (int)(lastblk % WR);
+    for (int e = tid; e < (b + SB) * SC; e += ST) {
+        const int t = e / SC, qq = e % SC;
+        const int64_t i = lastblk - b + t;
+        int sl = bs + WR - b + t;                     // slot of row i = lastblk + (t - b)
+        while (sl >= WR) sl -= WR;
+        float2 *dst = Y + sl * SC + qq;
+        if (i >= 0 && i < n && qq < nrc) cp_async8(dst, Zs + i * ncol + qq);
+        else *dst = zero;
+    }
+    bwd_slab(lastblk, Lbuf);
+    cp_async_commit();
+    for (int64_t j = 0; j < nblk; ++j) {
+        const int64_t blk = lastblk - j * SB;
+        const int nb = (int)min((int64_t)SB, n - blk);
+        const float2 *Ls = Lbuf + (j & 1) * LBS;
+        const float2 *Ld = Ls + (size_t)b * SB;
+        auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
+        cp_async_wait_all();
         __syncthreads();
+        if (blk > 0) bwd_slab(blk - SB, Lbuf + ((j + 1) & 1) * LBS);
+        {
+            // rows [blk - b - SB, blk - b) go to the slots of rows [blk + SB, blk + 2 SB)
+            int s0 = bs + SB;
+            if (s0 >= WR) s0 -= WR;
+            rows_async(blk - b - SB, s0, Zs);
+        }
+        cp_async_commit();
         if (cg < SC) {
-            float2 x = lg < nb ? Y[slot(blk + lg) * SC + cg] : zero;
+            float2 x = lg < nb ? Y[bslot(lg) * SC + cg] : zero;
 #pragma unroll
             for (int c = SB - 1; c > 0; --c) {
                 const float xr = __shfl_sync(gmask, x.x, c, SB), xi = __shfl_sync(gmask, x.y, c, SB);
@@ -324,48 +401,54 @@ __global__ void __launch_bounds__(ST, 2) k_band_solve(int64_t n, int b, int ncol
                     x.y -= l.x * xi + l.y * xr;
                 }
             }
-            if (lg < nb) Y[slot(blk + lg) * SC + cg] = x;
+            if (lg < nb) {
+                Y[bslot(lg) * SC + cg] = x;
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = x;
+            }
         }
         __syncthreads();
         {
             float2 xa[SB], xc[SB];
 #pragma unroll
             for (int c = 0; c < SB; ++c) {
-                xa[c] = c < nb ? Y[slot(blk + c) * SC + q2] : zero;
-                xc[c] = c < nb ? Y[slot(blk + c) * SC + q2 + SC / 2] : zero;
+                xa[c] = c < nb ? Y[bslot(c) * SC + q2] : zero;
+                xc[c] = c < nb ? Y[bslot(c) * SC + q2 + QT] : zero;
             }
             const int kklo = (int)(max((int64_t)0, blk - b) - (blk - b));
-            int sl = (int)(((blk - b + kklo + rg) % WR + WR) % WR);
-            for (int kk = kklo + rg; kk < b; kk += nrg) {
-                const float2 *lrow = Ls + kk * SB;
+            // row blk - b + kk sits in slot bs + 2 SB + kk (mod WR), since WR = b + 2 SB
+            int sl = bs + 2 * SB + kklo + rg;
+            while (sl >= WR) sl -= WR;
+            for (int kk = kklo + rg; kk < b; kk += RG) {
+                const float4 *lrow = reinterpret_cast<const float4 *>(Ls + kk * SB);
                 float2 a0 = zero, a1 = zero;
 #pragma unroll
-                for (int c = 0; c < SB; ++c) {
-                    const float2 l = lrow[c];
-                    a0.x += l.x * xa[c].x - l.y * xa[c].y;
-                    a0.y += l.x * xa[c].y + l.y * xa[c].x;
-                    a1.x += l.x * xc[c].x - l.y * xc[c].y;
-                    a1.y += l.x * xc[c].y + l.y * xc[c].x;
+                for (int c2 = 0; c2 < SB / 2; ++c2) {
+                    const float4 l2 = lrow[c2];
+                    const float2 la = make_float2(l2.x, l2.y), lb = make_float2(l2.z, l2.w);
+                    const int c = 2 * c2;
+                    a0.x += la.x * xa[c].x - la.y * xa[c].y;
+                    a0.y += la.x * xa[c].y + la.y * xa[c].x;
+                    a1.x += la.x * xc[c].x - la.y * xc[c].y;
+                    a1.y += la.x * xc[c].y + la.y * xc[c].x;
+                    a0.x += lb.x * xa[c + 1].x - lb.y * xa[c + 1].y;
+                    a0.y += lb.x * xa[c + 1].y + lb.y * xa[c + 1].x;
+                    a1.x += lb.x * xc[c + 1].x - lb.y * xc[c + 1].y;
+                    a1.y += lb.x * xc[c + 1].y + lb.y * xc[c + 1].x;
                 }
                 float2 *yr = Y + sl * SC;
-                yr[q2].x -= a0.x; yr[q2].y -= a0.y;
-                yr[q2 + SC / 2].x -= a1.x; yr[q2 + SC / 2].y -= a1.y;
-                sl += nrg;
+                float2 v0 = yr[q2], v1 = yr[q2 + QT];
+                v0.x -= a0.x; v0.y -= a0.y;
+                v1.x -= a1.x; v1.y -= a1.y;
+                yr[q2] = v0;
+                yr[q2 + QT] = v1;
+                sl += RG;
                 while (sl >= WR) sl -= WR;
             }
         }
-        for (int e = tid; e < nb * SC; e += ST) {
-            const int c = e / SC, qq = e % SC;
-            if (qq < nrc) Zs[(blk + c) * ncol + qq] = Y[slot(blk + c) * SC + qq];
-        }
-        if (blk == 0) break;
-        __syncthreads();
-        for (int e = tid; e < SB * SC; e += ST) {
-            const int c = e / SC, qq = e % SC;
-            const int64_t inew = blk - b - SB + c;
-            Y[slot(blk + c) * SC + qq] = (inew >= 0 && qq < nrc) ? Zs[inew * ncol + qq] : zero;
-        }
+        bs -= SB;
+        if (bs < 0) bs += WR;
     }
+    cp_async_wait_all();
 }
 
 // partial sums of r^T z (unconjugated) per (shift, chunk, column), geometry of the COCG sweeps
@@ -441,16 +524,16 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 }
 
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
-size_t band_smem_solve(int b)
+size_t band_smem_solve(int b, int sc)
 {
-    // window + max(forward L block SB x (b + 1 + SB), backward strip b x SB + in-block SB x SB)
-    return sizeof(float2) * ((size_t)(b + SB) * SC + std::max((size_t)SB * (b + 1 + SB), (size_t)b * SB + SB * SB));
+    // window (b + 2 SB) x sc + two slabs SB x (b + 1 + SB) (the backward strip b x SB + SB x SB is smaller)
+    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + 1 + SB));
 }
 
 bool band_feasible(const Ctx *c, int b)
 {
     // one thread per row below the panel in the factorization: b < 1024 - NB
-    return b + NB <= 1024 && band_smem_factor(b) <= c->smem_optin && band_smem_solve(b) <= c->smem_optin;
+    return b + NB <= 1024 && band_smem_factor(b) <= c->smem_optin && band_smem_solve(b, 8) <= c->smem_optin;
 }
 
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
@@ -484,25 +567,47 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     return GCIE_OK;
 }
 
+template <int SC>
+static int launch_band_solve(Ctx *c, int64_t n, int b, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
+                             const float2 *R, float2 *Z)
+{
+    const size_t smem = band_smem_solve(b, SC);
+    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int ngrp = (ncol + SC - 1) / SC;
+    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
+    GCIE_CUDA_TRY(cudaGetLastError());
+    return GCIE_OK;
+}
+
 int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
                const float2 *R, float2 *Z, int nact)
 {
     const int b = p->bw;
     const int64_t n = p->n;
-    const size_t smem = band_smem_solve(b);
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    const int ngrp = (ncol + SC - 1) / SC;
+    // Columns per CTA: a CTA's block step costs about SC columns of work and one CTA runs per SM,
+    // so take the SC with the fewest (waves x SC) over the active shifts; ties go to the wider CTA,
+    // which reads each column of L once for more right-hand sides.
+    int best = 0;
+    int64_t best_cost = 0;
+    for (int sc : {32, 16, 8}) {
+        if (band_smem_solve(b, sc) > c->smem_optin) continue;
+        const int64_t ctas = (int64_t)std::max(1, nact) * ((ncol + sc - 1) / sc);
+        const int64_t cost = ((ctas + c->num_sms - 1) / c->num_sms) * sc;
+        if (!best || cost < best_cost) { best = sc; best_cost = cost; }
+    }
+    if (!best) { set_error("band sweep: bandwidth too large for shared memory"); return GCIE_EINVAL; }
+    const int ngrp = (ncol + best - 1) / best;
     const double macs = 2.0 * nact * n * b * ncol;
     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
-    k_band_solve<<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
-    GCIE_CUDA_TRY(cudaGetLastError());
-    return GCIE_OK;
+    if (best == 32) return launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
+    if (best == 16) return launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
+    return launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
 }
 
 int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,
                 const float2 *R, const float2 *Z, double2 *part, int nact)
 {
-    LaunchScope ls(c, GCIE_K_PREC, (double)nact * n * ncol * 16.0, 0);
+    LaunchScope ls(c, GCIE_K_OTHER, (double)nact * n * ncol * 16.0, 0);
     k_rz_partials<<<nshift * chunks, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(n, ncol, rows_per_chunk,
                                                                                             chunks, mask, R, Z, part);
     GCIE_CUDA_TRY(cudaGetLastError());

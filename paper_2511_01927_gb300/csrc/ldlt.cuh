@@ -17,7 +17,7 @@ struct BandCache {
 
 bool band_feasible(const Ctx *c, int b);
 size_t band_smem_factor(int b);
-size_t band_smem_solve(int b);
+size_t band_smem_solve(int b, int sc);
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
                 const std::vector<float2 *> &h_ABp);
 int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
