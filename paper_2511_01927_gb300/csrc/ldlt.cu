@@ -30,6 +30,24 @@ namespace gcie {
 
 constexpr int NB = 16;        // panel / block width
 
+// v -= l y with explicit FMAs (four per complex multiply-add; a plain expression compiles to
+// separate multiplies, fused multiply-adds and adds)
+__device__ __forceinline__ void cmsubf(float2 &v, float lx, float ly, float2 y)
+{
+    v.x = fmaf(-lx, y.x, v.x);
+    v.x = fmaf(ly, y.y, v.x);
+    v.y = fmaf(-lx, y.y, v.y);
+    v.y = fmaf(-ly, y.x, v.y);
+}
+// a += l w
+__device__ __forceinline__ void cmaddf(float2 &a, float2 l, float2 w)
+{
+    a.x = fmaf(l.x, w.x, a.x);
+    a.x = fmaf(-l.y, w.y, a.x);
+    a.y = fmaf(l.x, w.y, a.y);
+    a.y = fmaf(l.y, w.x, a.y);
+}
+
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 __device__ __forceinline__ float2 cdivf(float2 a, float2 b)
 {
@@ -130,8 +148,7 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 #pragma unroll
                 for (int c2 = c + 1; c2 < NB; ++c2) {
                     const float2 lc = PT[c * R + c2];     // l_{c2, c} of the diagonal block
-                    a[c2].x -= ld.x * lc.x - ld.y * lc.y;
-                    a[c2].y -= ld.x * lc.y + ld.y * lc.x;
+                    cmsubf(a[c2], ld.x, ld.y, lc);
                 }
             }
 #pragma unroll
@@ -164,8 +181,7 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 #pragma unroll
                             for (int q = 0; q < 4; ++q) {
                                 const float2 w = W[(J0 + q < tr ? J0 + q : 0) * NB + c];
-                                acc[q].x += l.x * w.x - l.y * w.y;
-                                acc[q].y += l.x * w.y + l.y * w.x;
+                                cmaddf(acc[q], l, w);
                             }
                         }
 #pragma unroll
@@ -198,7 +214,9 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 //             block's x to the b rows above through the strip l_{block, k}.
 // Everything a step reads from global memory (its columns of L, the rows entering the window) is
 // copied with cp.async during the previous step into a second buffer, so a step waits on no global
-// load and needs two barriers.
+// load and needs two barriers.  Both sweeps keep the factor entries a step needs row by row, SB
+// consecutive values per row of the window (row il: l_{blk+il, blk+c} forward, l_{blk+c, k}
+// backward), so every row update reads them as four 16-byte loads at fixed offsets.
 constexpr int SB = 8;         // rows per block of the sweeps
 constexpr int ST = 512;       // threads per CTA of the sweeps
 
@@ -209,6 +227,25 @@ __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// one window row: yr[q] -= sum_c l[c] ya[c], yr[q + QT] -= sum_c l[c] yc[c] (l: SB values, 16-byte aligned)
+template <int QT>
+__device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 *yr, int q, const float2 (&ya)[SB],
+                                           const float2 (&yc)[SB])
+{
+    const float4 *l4 = reinterpret_cast<const float4 *>(l);
+    float2 v0 = yr[q], v1 = yr[q + QT];
+#pragma unroll
+    for (int c2 = 0; c2 < SB / 2; ++c2) {
+        const float4 w = l4[c2];
+        cmsubf(v0, w.x, w.y, ya[2 * c2]);
+        cmsubf(v1, w.x, w.y, yc[2 * c2]);
+        cmsubf(v0, w.z, w.w, ya[2 * c2 + 1]);
+        cmsubf(v1, w.z, w.w, yc[2 * c2 + 1]);
+    }
+    yr[q] = v0;
+    yr[q + QT] = v1;
+}
 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
@@ -225,9 +262,8 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int c0 = g * SC;
     const int nrc = min(SC, ncol - c0);
     const int B1 = b + 1;
-    const int LD = B1 + SB;                           // padded column length of the forward slab
     const int WR = b + 2 * SB;
-    const int LBS = SB * LD;                          // one slab buffer (>= b SB + SB SB of the backward)
+    const int LBS = (b + SB) * SB;                    // one slab buffer (forward rows; backward strip + block)
     const float2 *AB = ABp[s];
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
@@ -255,18 +291,17 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     };
 
     // ---------------- forward: L y = r, then y / d written to Z
-    // slab of block blk: L[c * LD + t] = l_{blk+c+t, blk+c} (t <= b); t in (b, LD) stays zero
+    // slab of block blk: L[il * SB + c] = l_{blk+il, blk+c} for 0 <= il - c <= b, else 0 (il < b + SB);
+    // consecutive threads fill consecutive shared addresses
     auto fwd_slab = [&](int64_t blk, float2 *L) {
         const int nb = (int)min((int64_t)SB, n - blk);
-        for (int c = 0; c < SB; ++c) {
-            if (c < nb)
-                for (int t = tid; t < B1; t += ST) cp_async8(L + c * LD + t, AB + (blk + c) * B1 + t);
-            else
-                for (int t = tid; t < B1; t += ST) L[c * LD + t] = zero;
+        for (int e = tid; e < (b + SB) * SB; e += ST) {
+            const int il = e / SB, c = e % SB;
+            const int t = il - c;
+            if (c < nb && t >= 0 && t <= b) cp_async8(L + e, AB + (blk + c) * B1 + t);
+            else L[e] = zero;
         }
     };
-    for (int c = 0; c < 2 * SB; ++c)
-        for (int t = B1 + tid; t < LD; t += ST) Lbuf[c * LD + t] = zero;
     for (int e = tid; e < (b + SB) * SC; e += ST) {
         const int t = e / SC, qq = e % SC;
         if (t < n && qq < nrc) cp_async8(Y + e, Rs + (int64_t)t * ncol + qq);
@@ -296,14 +331,13 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             for (int c = 0; c < SB - 1; ++c) {
                 const float yr = __shfl_sync(gmask, y.x, c, SB), yi = __shfl_sync(gmask, y.y, c, SB);
                 if (lg > c) {
-                    const float2 l = Lb[c * LD + (lg - c)];
-                    y.x -= l.x * yr - l.y * yi;
-                    y.y -= l.x * yi + l.y * yr;
+                    const float2 l = Lb[lg * SB + c];
+                    cmsubf(y, l.x, l.y, make_float2(yr, yi));
                 }
             }
             if (lg < nb) {
                 Y[bslot(lg) * SC + cg] = y;
-                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cdivf(y, Lb[lg * LD]);
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cdivf(y, Lb[lg * SB + lg]);
             }
         }
         __syncthreads();
@@ -318,22 +352,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             int sl = bs + nb + rg;
             while (sl >= WR) sl -= WR;
             for (int il = nb + rg; il < rhi; il += RG) {
-                float2 a0 = zero, a1 = zero;
-                const float2 *lrow = Lb + il;    // Lb[c * LD + il - c] = lrow[c * (LD - 1)]
-#pragma unroll
-                for (int c = 0; c < SB; ++c) {
-                    const float2 l = lrow[c * (LD - 1)];
-                    a0.x += l.x * ya[c].x - l.y * ya[c].y;
-                    a0.y += l.x * ya[c].y + l.y * ya[c].x;
-                    a1.x += l.x * yc[c].x - l.y * yc[c].y;
-                    a1.y += l.x * yc[c].y + l.y * yc[c].x;
-                }
-                float2 *yr = Y + sl * SC;
-                float2 v0 = yr[q2], v1 = yr[q2 + QT];
-                v0.x -= a0.x; v0.y -= a0.y;
-                v1.x -= a1.x; v1.y -= a1.y;
-                yr[q2] = v0;
-                yr[q2 + QT] = v1;
+                row_update<QT>(Lb + il * SB, Y + sl * SC, q2, ya, yc);
                 sl += RG;
                 while (sl >= WR) sl -= WR;
             }
@@ -397,8 +416,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
                 const float xr = __shfl_sync(gmask, x.x, c, SB), xi = __shfl_sync(gmask, x.y, c, SB);
                 if (lg < c) {
                     const float2 l = Ld[lg * SB + c];
-                    x.x -= l.x * xr - l.y * xi;
-                    x.y -= l.x * xi + l.y * xr;
+                    cmsubf(x, l.x, l.y, make_float2(xr, xi));
                 }
             }
             if (lg < nb) {
@@ -419,28 +437,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             int sl = bs + 2 * SB + kklo + rg;
             while (sl >= WR) sl -= WR;
             for (int kk = kklo + rg; kk < b; kk += RG) {
-                const float4 *lrow = reinterpret_cast<const float4 *>(Ls + kk * SB);
-                float2 a0 = zero, a1 = zero;
-#pragma unroll
-                for (int c2 = 0; c2 < SB / 2; ++c2) {
-                    const float4 l2 = lrow[c2];
-                    const float2 la = make_float2(l2.x, l2.y), lb = make_float2(l2.z, l2.w);
-                    const int c = 2 * c2;
-                    a0.x += la.x * xa[c].x - la.y * xa[c].y;
-                    a0.y += la.x * xa[c].y + la.y * xa[c].x;
-                    a1.x += la.x * xc[c].x - la.y * xc[c].y;
-                    a1.y += la.x * xc[c].y + la.y * xc[c].x;
-                    a0.x += lb.x * xa[c + 1].x - lb.y * xa[c + 1].y;
-                    a0.y += lb.x * xa[c + 1].y + lb.y * xa[c + 1].x;
-                    a1.x += lb.x * xc[c + 1].x - lb.y * xc[c + 1].y;
-                    a1.y += lb.x * xc[c + 1].y + lb.y * xc[c + 1].x;
-                }
-                float2 *yr = Y + sl * SC;
-                float2 v0 = yr[q2], v1 = yr[q2 + QT];
-                v0.x -= a0.x; v0.y -= a0.y;
-                v1.x -= a1.x; v1.y -= a1.y;
-                yr[q2] = v0;
-                yr[q2 + QT] = v1;
+                row_update<QT>(Ls + kk * SB, Y + sl * SC, q2, xa, xc);
                 sl += RG;
                 while (sl >= WR) sl -= WR;
             }
@@ -526,8 +523,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
 size_t band_smem_solve(int b, int sc)
 {
-    // window (b + 2 SB) x sc + two slabs SB x (b + 1 + SB) (the backward strip b x SB + SB x SB is smaller)
-    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + 1 + SB));
+    // window (b + 2 SB) x sc + two slabs (b + SB) x SB
+    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + SB));
 }
 
 bool band_feasible(const Ctx *c, int b)
