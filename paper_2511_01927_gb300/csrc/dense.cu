@@ -2,14 +2,17 @@
 //   moments      S_k = 2 Re sum_s w_s ((z_s - c)/r)^k X_s           (Appendix A.3.3, moment method)
 //   gram         G = Y^T W, tall-skinny (row chunks -> per-CTA partial p x p -> ordered sum)
 //   gemm_tall    Z = Y T with a small T held in shared memory
-//   jacobi       cyclic Jacobi, one CTA per matrix, round-robin (tournament) pair ordering so
-//                each round applies p/2 disjoint rotations in parallel
+//   jacobi       cyclic Jacobi, round-robin (tournament) pair ordering so each round applies
+//                p/2 disjoint rotations in parallel; one 8-CTA cluster per matrix (rows spread
+//                over the cluster's shared memory), or one CTA in global memory for p > 256
 //   m_orthonormalize, rayleigh_ritz   (Algorithm 1: Q <- orth(Y); Q^T A Q, Q^T B Q; reduced GEP;
 //                x <- Q u) and the residual ||K z - theta M z|| / (||K||_1 ||z||)
 #include <algorithm>
 #include <cmath>
 #include <mutex>
 #include <string>
+
+#include <cooperative_groups.h>
 
 #include "kernels.cuh"
 
@@ -311,10 +314,235 @@ __global__ void __launch_bounds__(1024) k_jacobi(int p, double *__restrict__ Aal
     }
 }
 
+// ------------------------------------------------------------------ Jacobi on a cluster
+// The same sweeps, rounds, rotations and stopping rule as k_jacobi, for p <= 256, with the FP64
+// arithmetic spread over the JCL SMs of a thread-block cluster (FP64 throughput per SM is low, so a
+// single CTA is bound by it).  Pair k of a round belongs to CTA k mod JCL, which holds the two rows
+// (q, r) of the pair in its shared memory.  A round:
+//   1. each CTA computes the rotations of its pairs from its rows and stores (c, s) into the
+//      rotation table of every CTA of the cluster (distributed shared memory); cluster barrier;
+//   2. each CTA forms the 2 x 2 blocks J_k^T A[{q,r},{q',r'}] J_k' of its rows for every pair k'
+//      (that is A <- A J, then A <- J^T A, as in k_jacobi) and writes them straight into the
+//      row buffer of the CTA that owns the row in the next round (double-buffered); V <- V J on
+//      the CTA's own rows of V (row i on CTA i mod JCL, never moved); cluster barrier.
+// The rows return to their round-0 owners at the end of every sweep, where the off-diagonal norm
+// is summed (per-CTA partials exchanged through distributed shared memory, added in rank order, so
+// every CTA takes the same decision).  Barriers are the hardware cluster barrier.
+constexpr int JCL = 8;       // CTAs per cluster (one matrix per cluster)
+constexpr int JT = 256;      // threads per CTA
+constexpr int JCL_MAXP = 256;
+
+__device__ __forceinline__ int jac_who(int pos, int round, int pe) { return pos == 0 ? 0 : 1 + (pos - 1 + round) % (pe - 1); }
+__device__ __forceinline__ int jac_pos(int i, int round, int pe)
+{
+    if (i == 0) return 0;
+    int m = (i - 1 - round) % (pe - 1);
+    if (m < 0) m += pe - 1;
+    return m + 1;
+}
+
+static size_t jacobi_cl_smem(int p)
+{
+    const int pe = p + (p & 1), h = pe / 2, npl = (h + JCL - 1) / JCL, nvl = (p + JCL - 1) / JCL;
+    const size_t nd = (size_t)4 * npl * pe + (size_t)nvl * pe + 2 * (size_t)h + 3 * JCL + pe;
+    const size_t ni = 2 * (size_t)h + 2 * (size_t)npl + pe;
+    return nd * sizeof(double) + ni * sizeof(int);
+}
+
+__global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
+k_jacobi_cl(int p, const double *__restrict__ Aall, double *__restrict__ wall, double *__restrict__ Vall, double tol,
+            int maxsweep)
+{
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int mat = blockIdx.x / JCL;
+    const double *A = Aall + (int64_t)mat * p * p;
+    double *Vo = Vall + (int64_t)mat * p * p;
+    double *w = wall + (int64_t)mat * p;
+    const int pe = p + (p & 1), h = pe / 2;
+    const int npl = (h + JCL - 1) / JCL, nvl = (p + JCL - 1) / JCL;
+    extern __shared__ double jsm[];
+    double *Rb = jsm;                                 // 2 buffers x (2 npl rows) x pe
+    double *Vl = Rb + (size_t)4 * npl * pe;           // nvl x pe: rows rank, rank + JCL, ... of V
+    double *cs = Vl + (size_t)nvl * pe, *sn = cs + h; // rotation table of the round (all pairs)
+    double *part = sn + h;                            // 3 x JCL partial sums (slot x source rank)
+    double *diag = part + 3 * JCL;                    // pe
+    int *qi = reinterpret_cast<int *>(diag + pe), *ri = qi + h;
+    int *dst = ri + h;                                // 2 npl: (next-round CTA << 16) | row slot
+    int *rnk = dst + 2 * npl;                         // pe
+    __shared__ double red[JT / 32];
+    const int tid = threadIdx.x;
+
+    // matrix index of local row slot sl (pair lp = sl / 2, q row if even) in round `round`
+    auto row_index = [&](int sl, int round) {
+        const int k = (sl / 2) * JCL + rank;
+        if (k >= h) return -1;
+        const int a = jac_who(k, round, pe), b = jac_who(pe - 1 - k, round, pe);
+        return (sl & 1) ? max(a, b) : min(a, b);
+    };
+    // cluster-wide sum, identical in every CTA (partials added in rank order)
+    auto cluster_sum = [&](double v, int slot) -> double {
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) red[tid >> 5] = v;
+        __syncthreads();
+        if (tid < JCL) {
+            double t = 0.0;
+            for (int i = 0; i < JT / 32; ++i) t += red[i];
+            double *remote = cl.map_shared_rank(part, tid);
+            remote[slot * JCL + rank] = t;
+        }
+        cl.sync();
+        double tot = 0.0;
+        for (int i = 0; i < JCL; ++i) tot += part[slot * JCL + i];
+        return tot;
+    };
+
+    // rows of round 0 and V = I
+    double loc = 0.0;
+    for (int e = tid; e < 2 * npl * pe; e += JT) {
+        const int sl = e / pe, j = e % pe;
+        const int i = row_index(sl, 0);
+        const double v = (i >= 0 && i < p && j < p) ? A[(int64_t)i * p + j] : 0.0;
+        Rb[e] = v;
+        loc += v * v;
+    }
+    for (int e = tid; e < nvl * pe; e += JT) {
+        const int i = (e / pe) * JCL + rank, j = e % pe;
+        Vl[e] = (i < p && j == i) ? 1.0 : 0.0;
+    }
+    const double fro2 = cluster_sum(loc, 0);
+    int cur = 0;
+    for (int sweep = 0; sweep <= maxsweep; ++sweep) {
+        const double *Rc = Rb + (size_t)cur * 2 * npl * pe;
+        loc = 0.0;
+        for (int e = tid; e < 2 * npl * pe; e += JT) {
+            const int sl = e / pe, j = e % pe;
+            const int i = row_index(sl, 0);
+            if (i >= 0 && i < p && j < p && j != i) loc += Rc[e] * Rc[e];
+        }
+        const double off2 = cluster_sum(loc, 1 + (sweep & 1));
+        if (off2 <= tol * tol * fro2 || fro2 == 0.0 || sweep == maxsweep) break;
+        for (int round = 0; round < pe - 1; ++round) {
+            const int nr = round + 1 == pe - 1 ? 0 : round + 1;
+            double *Rcur = Rb + (size_t)cur * 2 * npl * pe;
+            double *Rnext = Rb + (size_t)(cur ^ 1) * 2 * npl * pe;
+            for (int k = tid; k < h; k += JT) {
+                const int a = jac_who(k, round, pe), b = jac_who(pe - 1 - k, round, pe);
+                qi[k] = min(a, b);
+                ri[k] = max(a, b);
+            }
+            for (int t = tid; t < 2 * npl; t += JT) {
+                const int i = row_index(t, round);
+                int code = -1;
+                if (i >= 0) {
+                    const int pos = jac_pos(i, nr, pe);
+                    const int k2 = pos < h ? pos : pe - 1 - pos;
+                    const int partner = jac_who(pe - 1 - pos, nr, pe);
+                    code = ((k2 % JCL) << 16) | (2 * (k2 / JCL) + (i < partner ? 0 : 1));
+                }
+                dst[t] = code;
+            }
+            for (int lp = tid; lp < npl; lp += JT) {
+                const int k = lp * JCL + rank;
+                if (k >= h) continue;
+                const int q = row_index(2 * lp, round), r = row_index(2 * lp + 1, round);
+                double c = 1.0, s = 0.0;
+                if (r < p) {
+                    const double aqr = Rcur[(size_t)(2 * lp) * pe + r];
+                    if (aqr != 0.0) {
+                        const double aqq = Rcur[(size_t)(2 * lp) * pe + q], arr = Rcur[(size_t)(2 * lp + 1) * pe + r];
+                        const double tau = (arr - aqq) / (2.0 * aqr);
+                        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+                        c = 1.0 / sqrt(1.0 + t * t);
+                        s = t * c;
+                    }
+                }
+                for (int d = 0; d < JCL; ++d) {
+                    cl.map_shared_rank(cs, d)[k] = c;
+                    cl.map_shared_rank(sn, d)[k] = s;
+                }
+            }
+            cl.sync();
+            // A <- J^T A J on the local rows, written to the rows' owners in the next round
+            for (int e = tid; e < npl * h; e += JT) {
+                const int lp = e / h, k2 = e % h;
+                const int k = lp * JCL + rank;
+                if (k >= h) continue;
+                const int q2 = qi[k2], r2 = ri[k2];
+                const double c = cs[k], s = sn[k], c2 = cs[k2], s2 = sn[k2];
+                const double *rq = Rcur + (size_t)(2 * lp) * pe, *rr = rq + pe;
+                const double b00 = rq[q2], b01 = rq[r2], b10 = rr[q2], b11 = rr[r2];
+                const double x00 = c2 * b00 - s2 * b01, x01 = s2 * b00 + c2 * b01;
+                const double x10 = c2 * b10 - s2 * b11, x11 = s2 * b10 + c2 * b11;
+                double y00 = c * x00 - s * x10, y01 = c * x01 - s * x11;
+                double y10 = s * x00 + c * x10, y11 = s * x01 + c * x11;
+                if (k2 == k) { y01 = 0.0; y10 = 0.0; }
+                const int dq = dst[2 * lp], dr = dst[2 * lp + 1];
+                double *Pq = cl.map_shared_rank(Rnext, dq >> 16) + (size_t)(dq & 0xffff) * pe;
+                double *Pr = cl.map_shared_rank(Rnext, dr >> 16) + (size_t)(dr & 0xffff) * pe;
+                Pq[q2] = y00;
+                Pq[r2] = y01;
+                Pr[q2] = y10;
+                Pr[r2] = y11;
+            }
+            // V <- V J on this CTA's rows of V
+            for (int e = tid; e < nvl * h; e += JT) {
+                const int li = e / h, k2 = e % h;
+                const int r2 = ri[k2];
+                if (li * JCL + rank >= p || r2 >= p) continue;
+                const int q2 = qi[k2];
+                const double c2 = cs[k2], s2 = sn[k2];
+                double *vr = Vl + (size_t)li * pe;
+                const double vq = vr[q2], vv = vr[r2];
+                vr[q2] = c2 * vq - s2 * vv;
+                vr[r2] = s2 * vq + c2 * vv;
+            }
+            cl.sync();
+            cur ^= 1;
+        }
+    }
+    // eigenvalues: the diagonal, gathered in every CTA; ascending ranks (ties by index)
+    {
+        const double *Rc = Rb + (size_t)cur * 2 * npl * pe;
+        for (int t = tid; t < 2 * npl * JCL; t += JT) {
+            const int sl = t / JCL, d = t % JCL;
+            const int i = row_index(sl, 0);
+            if (i >= 0 && i < p) cl.map_shared_rank(diag, d)[i] = Rc[(size_t)sl * pe + i];
+        }
+    }
+    cl.sync();
+    for (int j = tid; j < p; j += JT) {
+        const double dj = diag[j];
+        int r = 0;
+        for (int m = 0; m < p; ++m) {
+            const double dm = diag[m];
+            r += (dm < dj) || (dm == dj && m < j);
+        }
+        rnk[j] = r;
+        if (rank == 0) w[r] = dj;
+    }
+    __syncthreads();
+    for (int e = tid; e < nvl * p; e += JT) {
+        const int li = e / p, j = e % p;
+        const int i = li * JCL + rank;
+        if (i < p) Vo[(int64_t)i * p + rnk[j]] = Vl[(size_t)li * pe + j];
+    }
+    cl.sync();   // no CTA leaves while others may still write into its shared memory
+}
+
 int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
 {
     if (nmat <= 0 || p <= 0) return GCIE_OK;
     if (p > 1024) { set_error("jacobi: p > 1024"); return GCIE_EINVAL; }
+    if (p <= JCL_MAXP && jacobi_cl_smem(p) <= c->smem_optin) {
+        const size_t smem = jacobi_cl_smem(p);
+        GCIE_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
+        k_jacobi_cl<<<nmat * JCL, JT, smem, c->stream>>>(p, A, w, V, 1e-15, 60);
+        GCIE_CUDA_TRY(cudaGetLastError());
+        return GCIE_OK;
+    }
     double *wk = nullptr;
     GCIE_CUDA_TRY(cudaMallocAsync((void **)&wk, sizeof(double) * (size_t)nmat * p * p, c->stream));
     LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
@@ -326,9 +554,9 @@ int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
 }
 
 // ------------------------------------------------------------------ Jacobi without allocation
-// gcie_jacobi_eig_noalloc (declared in gcie.h) runs the same kernel as gcie_jacobi_eig, but its
-// p x p workspace (the unsorted eigenvectors) lives in this fixed device array instead of memory
-// allocated per call.  Every GPU that loads the library holds the array (512 KB) until the process
+// gcie_jacobi_eig_noalloc (declared in gcie.h) runs the one-CTA Jacobi kernel (k_jacobi: the same
+// sweeps and rotations as the cluster kernel, in global memory), and its p x p workspace (the
+// unsorted eigenvectors) lives in this fixed device array instead of memory allocated per call.  Every GPU that loads the library holds the array (512 KB) until the process
 // exits; all calls on a device share it, so calls that overlap on that GPU (different streams,
 // different host threads) race on it and must be ordered by the caller.  The kernel overwrites the
 // whole workspace (identity start) before reading it, so nothing has to be cleared between calls.
