@@ -691,7 +691,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 const bool band = o->precision == GCIE_MIXED && o->precond != GCIE_PREC_NONE &&
                                   o->precond != GCIE_PREC_AMG && band_feasible(c, p->bw);
                 const size_t per = (size_t)half * n * nn * (7 * esz + 16) + (size_t)n * nn * 8 * 4 +
-                                   (band ? (size_t)half * n * (p->bw + 1) * 8 : 0);
+                                   (band ? (size_t)half * band_elems(n, p->bw) * 8 : 0);
                 if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
                 ncol = nn;
                 ++b1;

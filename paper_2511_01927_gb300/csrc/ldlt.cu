@@ -9,9 +9,15 @@
 // few iterations, and they depend only on the node, so one factorization serves every FEAST
 // iteration.
 //
-// Storage: per shift, column-oriented band AB[j][t] = A[j + t][j] for t = 0..b (b + 1 complex
-// values per column), so column j of L is contiguous.  After the factorization AB[j][0] = d_j
-// and AB[j][t] = l_{j+t, j}.
+// Storage, per shift, one buffer of nblk SB (b + SB) complex values (nblk = ceil(n / SB)):
+//   AB (working band, at the end of the buffer): column-oriented, AB[j][t] = A[j + t][j] for
+//      t = 0..b, so column j is contiguous; assembled and updated in place by the factorization;
+//   G  (the factor, from the start of the buffer): block-column layout, block kb (columns
+//      kb SB .. kb SB + SB - 1) is a dense (b + SB) x SB array G_kb[il][c] = l_{kb SB + il, kb SB + c}
+//      (d_j on the diagonal, zero outside the band).  The factorization writes each finished panel
+//      there; G's block kb ends before the AB columns still being factored begin, so the two share
+//      one buffer.  In this layout the forward sweep reads one contiguous block per step and the
+//      backward sweep contiguous SB x SB pieces.
 //
 // Kernels (one CTA per shift for the factorization, nshift x column groups for the sweeps):
 //   k_band_assemble  A_s from the union CSR pattern;
@@ -28,7 +34,11 @@
 
 namespace gcie {
 
-constexpr int NB = 16;        // panel / block width
+constexpr int NB = 16;        // panel width of the factorization
+constexpr int SB = 8;         // rows per block of the sweeps and columns per block of G (NB = 2 SB)
+
+size_t band_elems(int64_t n, int b) { return (size_t)((n + SB - 1) / SB) * SB * (size_t)(b + SB); }
+static size_t band_ab_offset(int64_t n, int b) { return band_elems(n, b) - (size_t)n * (b + 1); }
 
 // v -= l y with explicit FMAs (four per complex multiply-add; a plain expression compiles to
 // separate multiplies, fused multiply-adds and adds)
@@ -58,7 +68,8 @@ __device__ __forceinline__ float2 cdivf(float2 a, float2 b)
 // ------------------------------------------------------------------ assembly
 __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
                                 const double *__restrict__ kv, const double *__restrict__ mv,
-                                const double2 *__restrict__ z, int nshift, int b, float2 *const *__restrict__ ABp)
+                                const double2 *__restrict__ z, int nshift, int b, float2 *const *__restrict__ ABp,
+                                size_t ab_off)
 {
     const int64_t B1 = b + 1;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -68,7 +79,7 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
             const double a = kv[k], m = mv[k];
             for (int s = 0; s < nshift; ++s) {
                 const double2 zs = z[s];
-                ABp[s][j * B1 + (i - j)] = make_float2((float)(zs.x * m - a), (float)(zs.y * m));
+                ABp[s][ab_off + j * B1 + (i - j)] = make_float2((float)(zs.x * m - a), (float)(zs.y * m));
             }
         }
     }
@@ -82,17 +93,20 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 //   2. warp 0 factors the NB x NB diagonal block (lane = row, __syncwarp between columns);
 //   3. every row t >= NB of the panel is solved against the diagonal block by one thread
 //      (l_tc = (a_tc - sum_{c'<c} l_tc' d_c' l_cc') / d_c), no block-wide synchronisation;
-//   4. the panel goes back to global memory and W = L D is formed;
+//   4. the panel goes to its two blocks of G (all (b + SB) x SB entries, zeros outside the band)
+//      and W = L D is formed;
 //   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel:
 //      each warp owns groups of 4 columns J and its lanes walk consecutive rows I, so the shared
 //      reads of PT are conflict-free, W is a broadcast and the read-modify-writes of the band are
 //      coalesced.
-__global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp,
+__global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
                                                     int *__restrict__ status)
 {
     extern __shared__ float2 sm2[];
     const int64_t B1 = b + 1;
-    float2 *AB = ABp[blockIdx.x];
+    float2 *Gf = ABp[blockIdx.x];
+    float2 *AB = Gf + ab_off;
+    const int64_t nblk = (n + SB - 1) / SB, GB = (int64_t)(b + SB) * SB;
     const int R = NB + b;
     float2 *PT = sm2;                  // NB x R
     float2 *W = PT + (size_t)NB * R;   // b x NB
@@ -156,9 +170,15 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
         }
         __syncthreads();
         // 4. write back (D on the diagonal) and W = L D for the rows below the panel
-        for (int e = tid; e < NB * R; e += nth) {
-            const int c = e / R, t = e % R;
-            if (c < nc && t >= c && t < rows && t - c <= b) AB[(p0 + c) * B1 + (t - c)] = t == c ? D[c] : PT[e];
+        for (int e = tid; e < (NB / SB) * (int)GB; e += nth) {
+            const int h = e / (int)GB, r = e % (int)GB;
+            const int il = r / SB, cp = r % SB;
+            const int64_t kb = p0 / SB + h;
+            if (kb >= nblk) continue;
+            const int c = h * SB + cp, t = h * SB + il;      // panel column, panel row
+            float2 v = zero;
+            if (c < nc && t >= c && t < rows && t - c <= b) v = t == c ? D[c] : PT[c * R + t];
+            Gf[kb * GB + r] = v;
         }
         for (int e = tid; e < b * NB; e += nth) {
             const int J = e / NB, c = e % NB;
@@ -217,13 +237,17 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 // load and needs two barriers.  Both sweeps keep the factor entries a step needs row by row, SB
 // consecutive values per row of the window (row il: l_{blk+il, blk+c} forward, l_{blk+c, k}
 // backward), so every row update reads them as four 16-byte loads at fixed offsets.
-constexpr int SB = 8;         // rows per block of the sweeps
 constexpr int ST = 512;       // threads per CTA of the sweeps
 
 __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(sdst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gsrc) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
@@ -246,6 +270,21 @@ __device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 
     yr[q] = v0;
     yr[q + QT] = v1;
 }
+// the same with the SB values of l at stride SB
+template <int QT>
+__device__ __forceinline__ void row_update_strided(const float2 *__restrict__ l, float2 *yr, int q,
+                                                   const float2 (&ya)[SB], const float2 (&yc)[SB])
+{
+    float2 v0 = yr[q], v1 = yr[q + QT];
+#pragma unroll
+    for (int c = 0; c < SB; ++c) {
+        const float2 w = l[c * SB];
+        cmsubf(v0, w.x, w.y, ya[c]);
+        cmsubf(v1, w.x, w.y, yc[c]);
+    }
+    yr[q] = v0;
+    yr[q + QT] = v1;
+}
 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
@@ -261,10 +300,11 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     if (!mask[s]) return;
     const int c0 = g * SC;
     const int nrc = min(SC, ncol - c0);
-    const int B1 = b + 1;
     const int WR = b + 2 * SB;
-    const int LBS = (b + SB) * SB;                    // one slab buffer (forward rows; backward strip + block)
-    const float2 *AB = ABp[s];
+    const int GB = (b + SB) * SB;                     // elements of one block of G
+    const int DOFF = (b / SB + 1) * SB * SB;          // backward: diagonal block after the strip pieces
+    const int LBS = (b + 2 * SB) * SB;                // one slab buffer (>= GB and >= DOFF + SB SB)
+    const float2 *Gf = ABp[s];
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
     float2 *Y = sm2;                                  // WR x SC
@@ -291,16 +331,11 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     };
 
     // ---------------- forward: L y = r, then y / d written to Z
-    // slab of block blk: L[il * SB + c] = l_{blk+il, blk+c} for 0 <= il - c <= b, else 0 (il < b + SB);
-    // consecutive threads fill consecutive shared addresses
-    auto fwd_slab = [&](int64_t blk, float2 *L) {
-        const int nb = (int)min((int64_t)SB, n - blk);
-        for (int e = tid; e < (b + SB) * SB; e += ST) {
-            const int il = e / SB, c = e % SB;
-            const int t = il - c;
-            if (c < nb && t >= 0 && t <= b) cp_async8(L + e, AB + (blk + c) * B1 + t);
-            else L[e] = zero;
-        }
+    // slab of block kb: block kb of G as it is, L[il * SB + c] = l_{blk+il, blk+c}
+    auto fwd_slab = [&](int64_t kb, float2 *L) {
+        const float4 *src = reinterpret_cast<const float4 *>(Gf + kb * GB);
+        float4 *dst = reinterpret_cast<float4 *>(L);
+        for (int e = tid; e < GB / 2; e += ST) cp_async16(dst + e, src + e);
     };
     for (int e = tid; e < (b + SB) * SC; e += ST) {
         const int t = e / SC, qq = e % SC;
@@ -318,7 +353,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         cp_async_wait_all();
         __syncthreads();
         // next step's slab and the rows entering the window then (slots of the previous block)
-        if (kb + 1 < nblk) fwd_slab(blk + SB, Lbuf + ((kb + 1) & 1) * LBS);
+        if (kb + 1 < nblk) fwd_slab(kb + 1, Lbuf + ((kb + 1) & 1) * LBS);
         {
             int s0 = bs + b + SB;
             while (s0 >= WR) s0 -= WR;
@@ -364,21 +399,26 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     __syncthreads();
 
     // ---------------- backward: L^T x = y' (in place in Z); window rows [blk - b, blk + SB)
-    // slab of block blk: Ls[kk * SB + c] = l_{blk+c, blk-b+kk} (b x SB), Ld[c2 * SB + c] = l_{blk+c, blk+c2}
-    auto bwd_slab = [&](int64_t blk, float2 *L) {
-        const int nb = (int)min((int64_t)SB, n - blk);
-        float2 *Ls = L, *Ld = L + (size_t)b * SB;
-        for (int e = tid; e < b * SB; e += ST) {
-            const int kk = e / SB, c = e % SB;
-            const int64_t k = blk - b + kk;           // column k, row blk + c = k + (b - kk + c)
-            if (k >= 0 && c < nb && c <= kk) cp_async8(Ls + e, AB + k * B1 + (b - kk + c));
-            else Ls[e] = zero;
+    // slab of block kb (blk = kb SB): piece i (i < kb - kbs, kbs = max(0, blk - b) / SB) is rows
+    // blk - (kbs + i) SB .. + SB of block kbs + i of G, so L[(i SB + c) SB + c'] = l_{blk+c, (kbs+i) SB + c'}
+    // (rows past the block's b + SB are out of the band: zero); at DOFF the block's own first SB
+    // rows, L[DOFF + c SB + c'] = l_{blk+c, blk+c'}
+    auto bwd_slab = [&](int64_t kb, float2 *L) {
+        const int64_t blk = kb * SB;
+        const int64_t kbs = max((int64_t)0, blk - b) / SB;
+        const int npc = (int)(kb - kbs);
+        float4 *dst = reinterpret_cast<float4 *>(L);
+        constexpr int Q = SB / 2;                     // float4 per row of a piece
+        for (int e = tid; e < npc * SB * Q; e += ST) {
+            const int i = e / (SB * Q), r = e % (SB * Q);
+            const int c = r / Q, h4 = r % Q;
+            const int64_t kbp = kbs + i;
+            const int64_t il = blk - kbp * SB + c;
+            if (il < b + SB) cp_async16(dst + e, reinterpret_cast<const float4 *>(Gf + kbp * GB + il * SB) + h4);
+            else dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int e = tid; e < SB * SB; e += ST) {
-            const int c2 = e / SB, c = e % SB;
-            if (c < nb && c2 < c && c - c2 <= b) cp_async8(Ld + e, AB + (blk + c2) * B1 + (c - c2));
-            else Ld[e] = zero;
-        }
+        for (int e = tid; e < SB * Q; e += ST)
+            cp_async16(dst + DOFF / 2 + e, reinterpret_cast<const float4 *>(Gf + kb * GB) + e);
     };
     const int64_t lastblk = (nblk - 1) * SB;
     bs = (int)(lastblk % WR);
@@ -391,17 +431,18 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         if (i >= 0 && i < n && qq < nrc) cp_async8(dst, Zs + i * ncol + qq);
         else *dst = zero;
     }
-    bwd_slab(lastblk, Lbuf);
+    bwd_slab(nblk - 1, Lbuf);
     cp_async_commit();
     for (int64_t j = 0; j < nblk; ++j) {
         const int64_t blk = lastblk - j * SB;
         const int nb = (int)min((int64_t)SB, n - blk);
         const float2 *Ls = Lbuf + (j & 1) * LBS;
-        const float2 *Ld = Ls + (size_t)b * SB;
+        const float2 *Ld = Ls + DOFF;
+        const int64_t kbs = max((int64_t)0, blk - b) / SB;
         auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
         cp_async_wait_all();
         __syncthreads();
-        if (blk > 0) bwd_slab(blk - SB, Lbuf + ((j + 1) & 1) * LBS);
+        if (blk > 0) bwd_slab(blk / SB - 1, Lbuf + ((j + 1) & 1) * LBS);
         {
             // rows [blk - b - SB, blk - b) go to the slots of rows [blk + SB, blk + 2 SB)
             int s0 = bs + SB;
@@ -415,7 +456,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             for (int c = SB - 1; c > 0; --c) {
                 const float xr = __shfl_sync(gmask, x.x, c, SB), xi = __shfl_sync(gmask, x.y, c, SB);
                 if (lg < c) {
-                    const float2 l = Ld[lg * SB + c];
+                    const float2 l = Ld[c * SB + lg];     // l_{blk+c, blk+lg}
                     cmsubf(x, l.x, l.y, make_float2(xr, xi));
                 }
             }
@@ -437,7 +478,8 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             int sl = bs + 2 * SB + kklo + rg;
             while (sl >= WR) sl -= WR;
             for (int kk = kklo + rg; kk < b; kk += RG) {
-                row_update<QT>(Ls + kk * SB, Y + sl * SC, q2, xa, xc);
+                const int64_t k = blk - b + kk;        // column k: piece k / SB - kbs, position k % SB
+                row_update_strided<QT>(Ls + ((int)(k / SB - kbs) * SB) * SB + (int)(k % SB), Y + sl * SC, q2, xa, xc);
                 sl += RG;
                 while (sl >= WR) sl -= WR;
             }
@@ -482,7 +524,7 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
             if (e.z.x == h_z[2 * s] && e.z.y == h_z[2 * s + 1]) { ptr[s] = e.AB; break; }
         if (!ptr[s]) missing.push_back(s);
     }
-    const size_t per = sizeof(float2) * (size_t)p->n * (p->bw + 1);
+    const size_t per = sizeof(float2) * band_elems(p->n, p->bw);
     if (!missing.empty()) {
         std::vector<float2 *> newp;
         std::vector<double2> hz;
@@ -523,8 +565,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
 size_t band_smem_solve(int b, int sc)
 {
-    // window (b + 2 SB) x sc + two slabs (b + SB) x SB
-    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + SB));
+    // window (b + 2 SB) x sc + two slabs (b + 2 SB) x SB
+    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + 2 * SB));
 }
 
 bool band_feasible(const Ctx *c, int b)
@@ -538,11 +580,12 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
 {
     const int b = p->bw;
     const int64_t n = p->n;
-    for (float2 *q : h_ABp) GCIE_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(float2) * (size_t)n * (b + 1), c->stream));
+    for (float2 *q : h_ABp) GCIE_CUDA_TRY(cudaMemsetAsync(q, 0, sizeof(float2) * band_elems(n, b), c->stream));
     {
         LaunchScope ls(c, GCIE_K_FACTOR, (double)p->nnz * 20 + (double)nshift * n * (b + 1) * 8, 0);
         const int blocks = (int)std::min<int64_t>((n + 255) / 256, (int64_t)c->num_sms * 8);
-        k_band_assemble<<<blocks, 256, 0, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z, nshift, b, d_ABp);
+        k_band_assemble<<<blocks, 256, 0, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z, nshift, b, d_ABp,
+                                                        band_ab_offset(n, b));
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int *d_status = nullptr;
@@ -553,7 +596,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     {
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
         LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
-        k_band_ldlt<<<nshift, 1024, smem, c->stream>>>(n, b, d_ABp, d_status);
+        k_band_ldlt<<<nshift, 1024, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int hs = 0;

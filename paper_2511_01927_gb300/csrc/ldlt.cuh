@@ -16,6 +16,7 @@ struct BandCache {
 };
 
 bool band_feasible(const Ctx *c, int b);
+size_t band_elems(int64_t n, int b);        // complex values of one shift's factor storage
 size_t band_smem_factor(int b);
 size_t band_smem_solve(int b, int sc);
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
