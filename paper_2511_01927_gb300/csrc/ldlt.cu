@@ -229,7 +229,8 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
 // on and SB more that are being loaded for the next step.  Per block of SB rows:
 //   forward : solve the SB x SB unit triangle with SB-lane groups (one column each, shuffles),
 //             write y / d, subtract the block's contribution from the b rows below (each thread:
-//             two columns, a set of rows, the block's y in registers);
+//             four columns, a set of rows, the block's y in registers; four columns per thread
+//             keep the shared-memory traffic per FMA within what the SM's shared memory delivers);
 //   backward: solve the triangle from the bottom with the SB x SB diagonal block, write x, push the
 //             block's x to the b rows above through the strip l_{block, k}.
 // Everything a step reads from global memory (its columns of L, the rows entering the window) is
@@ -252,45 +253,42 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// one window row: yr[q] -= sum_c l[c] ya[c], yr[q + QT] -= sum_c l[c] yc[c] (l: SB values, 16-byte aligned)
-template <int QT>
-__device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 *yr, int q, const float2 (&ya)[SB],
-                                           const float2 (&yc)[SB])
+// One window row, the four columns of a thread: (2q, 2q + 1) and (2q + H, 2q + H + 1), H = SC / 2,
+// so that each 16-byte access of a quarter warp covers 128 contiguous bytes.
+// yr[cols] -= sum_c l[c * LS] yb[c][cols], with the block's values yb in registers.
+struct Quad { float4 a, b; };   // columns (2q, 2q+1) and (2q+H, 2q+H+1) as two float2 pairs each
+
+template <int H, int LS>
+__device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 *yr, int q, const Quad (&yb)[SB])
 {
-    const float4 *l4 = reinterpret_cast<const float4 *>(l);
-    float2 v0 = yr[q], v1 = yr[q + QT];
-#pragma unroll
-    for (int c2 = 0; c2 < SB / 2; ++c2) {
-        const float4 w = l4[c2];
-        cmsubf(v0, w.x, w.y, ya[2 * c2]);
-        cmsubf(v1, w.x, w.y, yc[2 * c2]);
-        cmsubf(v0, w.z, w.w, ya[2 * c2 + 1]);
-        cmsubf(v1, w.z, w.w, yc[2 * c2 + 1]);
-    }
-    yr[q] = v0;
-    yr[q + QT] = v1;
-}
-// the same with the SB values of l at stride SB
-template <int QT>
-__device__ __forceinline__ void row_update_strided(const float2 *__restrict__ l, float2 *yr, int q,
-                                                   const float2 (&ya)[SB], const float2 (&yc)[SB])
-{
-    float2 v0 = yr[q], v1 = yr[q + QT];
+    float4 *pa = reinterpret_cast<float4 *>(yr + 2 * q), *pb = reinterpret_cast<float4 *>(yr + 2 * q + H);
+    float4 va = *pa, vb = *pb;
+    float2 v0 = make_float2(va.x, va.y), v1 = make_float2(va.z, va.w), v2 = make_float2(vb.x, vb.y),
+           v3 = make_float2(vb.z, vb.w);
 #pragma unroll
     for (int c = 0; c < SB; ++c) {
-        const float2 w = l[c * SB];
-        cmsubf(v0, w.x, w.y, ya[c]);
-        cmsubf(v1, w.x, w.y, yc[c]);
+        float2 w;
+        if (LS == 1) {
+            const float4 w2 = reinterpret_cast<const float4 *>(l)[c / 2];
+            w = (c & 1) ? make_float2(w2.z, w2.w) : make_float2(w2.x, w2.y);
+        } else {
+            w = l[c * LS];
+        }
+        cmsubf(v0, w.x, w.y, make_float2(yb[c].a.x, yb[c].a.y));
+        cmsubf(v1, w.x, w.y, make_float2(yb[c].a.z, yb[c].a.w));
+        cmsubf(v2, w.x, w.y, make_float2(yb[c].b.x, yb[c].b.y));
+        cmsubf(v3, w.x, w.y, make_float2(yb[c].b.z, yb[c].b.w));
     }
-    yr[q] = v0;
-    yr[q + QT] = v1;
+    *pa = make_float4(v0.x, v0.y, v1.x, v1.y);
+    *pb = make_float4(v2.x, v2.y, v3.x, v3.y);
 }
 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
 {
-    constexpr int QT = SC / 2;                        // threads per row in the updates (columns q, q + QT)
+    constexpr int H = SC / 2;
+    constexpr int QT = SC / 4;                        // threads per row in the updates (four columns each)
     constexpr int RG = ST / QT;                       // row groups of the updates
     static_assert(SB * SC <= ST, "in-block solve needs SB x SC threads");
     extern __shared__ float4 sm4[];                   // 16-byte aligned: the backward strip is read as float4
@@ -312,7 +310,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int tid = threadIdx.x;
     const int lg = tid % SB, cg = tid / SB;           // in-block solve: row lg of the block, column cg
     const unsigned gmask = 0xffffffffu;
-    const int q2 = tid % QT, rg = tid / QT;
+    const int q4 = tid % QT, rg = tid / QT;
     const float2 zero = make_float2(0.f, 0.f);
     const int64_t nblk = (n + SB - 1) / SB;
 
@@ -377,17 +375,19 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         }
         __syncthreads();
         {
-            float2 ya[SB], yc[SB];
+            Quad yb[SB];
 #pragma unroll
             for (int c = 0; c < SB; ++c) {
-                ya[c] = c < nb ? Y[bslot(c) * SC + q2] : zero;
-                yc[c] = c < nb ? Y[bslot(c) * SC + q2 + QT] : zero;
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 *yrow = Y + bslot(c) * SC;
+                yb[c].a = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4) : z4;
+                yb[c].b = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4 + H) : z4;
             }
             const int rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
             int sl = bs + nb + rg;
             while (sl >= WR) sl -= WR;
             for (int il = nb + rg; il < rhi; il += RG) {
-                row_update<QT>(Lb + il * SB, Y + sl * SC, q2, ya, yc);
+                row_update<H, 1>(Lb + il * SB, Y + sl * SC, q4, yb);
                 sl += RG;
                 while (sl >= WR) sl -= WR;
             }
@@ -467,11 +467,13 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         }
         __syncthreads();
         {
-            float2 xa[SB], xc[SB];
+            Quad xb[SB];
 #pragma unroll
             for (int c = 0; c < SB; ++c) {
-                xa[c] = c < nb ? Y[bslot(c) * SC + q2] : zero;
-                xc[c] = c < nb ? Y[bslot(c) * SC + q2 + QT] : zero;
+                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                const float2 *yrow = Y + bslot(c) * SC;
+                xb[c].a = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4) : z4;
+                xb[c].b = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4 + H) : z4;
             }
             const int kklo = (int)(max((int64_t)0, blk - b) - (blk - b));
             // row blk - b + kk sits in slot bs + 2 SB + kk (mod WR), since WR = b + 2 SB
@@ -479,7 +481,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             while (sl >= WR) sl -= WR;
             for (int kk = kklo + rg; kk < b; kk += RG) {
                 const int64_t k = blk - b + kk;        // column k: piece k / SB - kbs, position k % SB
-                row_update_strided<QT>(Ls + ((int)(k / SB - kbs) * SB) * SB + (int)(k % SB), Y + sl * SC, q2, xa, xc);
+                row_update<H, SB>(Ls + ((int)(k / SB - kbs) * SB) * SB + (int)(k % SB), Y + sl * SC, q4, xb);
                 sl += RG;
                 while (sl >= WR) sl -= WR;
             }
