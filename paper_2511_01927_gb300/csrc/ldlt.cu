@@ -86,58 +86,69 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 }
 
 // ------------------------------------------------------------------ factorization
-// One CTA (1024 threads) per shift walks the band by panels of NB columns.  Shared memory:
-// PT[c][t] = A[p0 + t][p0 + c] (panel transposed: NB x R, R = NB + b), W[J][c] = l_{p0+NB+J, p0+c} d_c
-// (b x NB), D[NB].  Per panel:
-//   1. load the panel (coalesced along the columns of the band);
+// One CTA (KT threads) per shift walks the band by panels of NB columns.  Shared memory:
+// PT[c][t] = A[p0 + t][p0 + c] (panel transposed: NB x R, R = NB + b, row stride RP),
+// WT[c][J] = l_{p0+NB+J, p0+c} d_c (NB x b, row stride WS), D[NB].  Per panel:
+//   1. load the panel with cp.async (every element in flight at once);
 //   2. warp 0 factors the NB x NB diagonal block (lane = row, __syncwarp between columns);
 //   3. every row t >= NB of the panel is solved against the diagonal block by one thread
 //      (l_tc = (a_tc - sum_{c'<c} l_tc' d_c' l_cc') / d_c), no block-wide synchronisation;
 //   4. the panel goes to its two blocks of G (all (b + SB) x SB entries, zeros outside the band)
-//      and W = L D is formed;
-//   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel:
-//      each warp owns groups of 4 columns J and its lanes walk consecutive rows I, so the shared
-//      reads of PT are conflict-free, W is a broadcast and the read-modify-writes of the band are
-//      coalesced.
-__global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
-                                                    int *__restrict__ status)
+//      and WT = (L D)^T is formed;
+//   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel,
+//      4 x 4 tiles per thread: a warp owns a group of 4 columns J, its lanes consecutive groups of
+//      4 rows I; per c one 16-byte load gives two rows of PT (two columns of WT), so the shared
+//      traffic is one byte per FMA; the old band values are loaded before the products.
+constexpr int KT = 512;       // threads per CTA of the factorization
+
+static int factor_rp(int b) { return ((NB + b + 4) + 3) & ~3; }
+static int factor_ws(int b) { return ((b + 4) + 3) & ~3; }
+
+__global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
+                                                  int *__restrict__ status)
 {
-    extern __shared__ float2 sm2[];
+    extern __shared__ float4 smf4[];
+    float2 *sm2 = reinterpret_cast<float2 *>(smf4);
     const int64_t B1 = b + 1;
     float2 *Gf = ABp[blockIdx.x];
     float2 *AB = Gf + ab_off;
     const int64_t nblk = (n + SB - 1) / SB, GB = (int64_t)(b + SB) * SB;
     const int R = NB + b;
-    float2 *PT = sm2;                  // NB x R
-    float2 *W = PT + (size_t)NB * R;   // b x NB
-    float2 *D = W + (size_t)b * NB;    // NB
+    const int RP = ((NB + b + 4) + 3) & ~3, WS = ((b + 4) + 3) & ~3;
+    float2 *PT = sm2;                   // NB x RP
+    float2 *WT = PT + (size_t)NB * RP;  // NB x WS
+    float2 *D = WT + (size_t)NB * WS;   // NB
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const float2 zero = make_float2(0.f, 0.f);
     for (int64_t p0 = 0; p0 < n; p0 += NB) {
         const int nc = (int)min((int64_t)NB, n - p0);
         const int rows = (int)min((int64_t)R, n - p0);
         // 1. load
-        for (int e = tid; e < NB * R; e += nth) {
-            const int c = e / R, t = e % R;
-            float2 v = zero;
-            if (c < nc && t >= c && t < rows && t - c <= b) v = AB[(p0 + c) * B1 + (t - c)];
-            PT[e] = v;
+        for (int e = tid; e < NB * RP; e += nth) {
+            const int c = e / RP, t = e % RP;
+            if (c < nc && t >= c && t < rows && t - c <= b) {
+                const unsigned sa = (unsigned)__cvta_generic_to_shared(PT + e);
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(AB + (p0 + c) * B1 + (t - c)) : "memory");
+            } else {
+                PT[e] = zero;
+            }
         }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+        asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
         // 2. diagonal block (warp 0, lane = row)
         if (warp == 0) {
             for (int c = 0; c < nc; ++c) {
-                const float2 d = PT[c * R + c];
-                if (lane > c && lane < nc && lane - c <= b) PT[c * R + lane] = cdivf(PT[c * R + lane], d);
+                const float2 d = PT[c * RP + c];
+                if (lane > c && lane < nc && lane - c <= b) PT[c * RP + lane] = cdivf(PT[c * RP + lane], d);
                 __syncwarp();
                 if (lane > c && lane < nc) {
-                    const float2 l = PT[c * R + lane];
+                    const float2 l = PT[c * RP + lane];
                     for (int c2 = c + 1; c2 <= lane; ++c2) {
-                        const float2 w = cmulf(d, PT[c * R + c2]);
-                        float2 v = PT[c2 * R + lane];
-                        v.x -= l.x * w.x - l.y * w.y;
-                        v.y -= l.x * w.y + l.y * w.x;
-                        PT[c2 * R + lane] = v;
+                        const float2 w = cmulf(d, PT[c * RP + c2]);
+                        float2 v = PT[c2 * RP + lane];
+                        cmsubf(v, l.x, l.y, w);
+                        PT[c2 * RP + lane] = v;
                     }
                 }
                 if (lane == 0) {
@@ -152,7 +163,7 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
         for (int t = NB + tid; t < rows; t += nth) {
             float2 a[NB];
 #pragma unroll
-            for (int c = 0; c < NB; ++c) a[c] = PT[c * R + t];
+            for (int c = 0; c < NB; ++c) a[c] = PT[c * RP + t];
 #pragma unroll
             for (int c = 0; c < NB; ++c) {
                 if (c >= nc) break;
@@ -161,15 +172,15 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
                 const float2 ld = cmulf(l, D[c]);
 #pragma unroll
                 for (int c2 = c + 1; c2 < NB; ++c2) {
-                    const float2 lc = PT[c * R + c2];     // l_{c2, c} of the diagonal block
+                    const float2 lc = PT[c * RP + c2];    // l_{c2, c} of the diagonal block
                     cmsubf(a[c2], ld.x, ld.y, lc);
                 }
             }
 #pragma unroll
-            for (int c = 0; c < NB; ++c) PT[c * R + t] = c < nc ? a[c] : zero;
+            for (int c = 0; c < NB; ++c) PT[c * RP + t] = c < nc ? a[c] : zero;
         }
         __syncthreads();
-        // 4. write back (D on the diagonal) and W = L D for the rows below the panel
+        // 4. write back (D on the diagonal) and WT = (L D)^T for the rows below the panel
         for (int e = tid; e < (NB / SB) * (int)GB; e += nth) {
             const int h = e / (int)GB, r = e % (int)GB;
             const int il = r / SB, cp = r % SB;
@@ -177,12 +188,12 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
             if (kb >= nblk) continue;
             const int c = h * SB + cp, t = h * SB + il;      // panel column, panel row
             float2 v = zero;
-            if (c < nc && t >= c && t < rows && t - c <= b) v = t == c ? D[c] : PT[c * R + t];
+            if (c < nc && t >= c && t < rows && t - c <= b) v = t == c ? D[c] : PT[c * RP + t];
             Gf[kb * GB + r] = v;
         }
-        for (int e = tid; e < b * NB; e += nth) {
-            const int J = e / NB, c = e % NB;
-            W[e] = (c < nc && NB + J < rows) ? cmulf(PT[c * R + NB + J], D[c]) : zero;
+        for (int e = tid; e < NB * WS; e += nth) {
+            const int c = e / WS, J = e % WS;
+            WT[e] = (c < nc && J < b && NB + J < rows) ? cmulf(PT[c * RP + NB + J], D[c]) : zero;
         }
         __syncthreads();
         // 5. trailing update
@@ -191,31 +202,40 @@ __global__ void __launch_bounds__(1024) k_band_ldlt(int64_t n, int b, float2 *co
             const int njb = (tr + 3) / 4;
             for (int jb = warp; jb < njb; jb += nwarp) {
                 const int J0 = 4 * jb;
-                for (int I0 = J0; I0 < tr; I0 += 32) {
-                    const int I = I0 + lane;
-                    float2 acc[4] = {zero, zero, zero, zero};
-                    if (I < tr) {
+                for (int I0 = J0 + 4 * lane; I0 < tr; I0 += 128) {
+                    float2 old[4][4], acc[4][4];
 #pragma unroll
-                        for (int c = 0; c < NB; ++c) {
-                            const float2 l = PT[c * R + NB + I];
+                    for (int q = 0; q < 4; ++q)
 #pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                const float2 w = W[(J0 + q < tr ? J0 + q : 0) * NB + c];
-                                cmaddf(acc[q], l, w);
-                            }
+                        for (int r = 0; r < 4; ++r) {
+                            const int I = I0 + r, J = J0 + q;
+                            old[q][r] = (I < tr && J < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                            acc[q][r] = zero;
                         }
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            const int J = J0 + q;
-                            if (J < tr && J <= I) {
-                                float2 *pv = AB + (p0 + NB + J) * B1 + (I - J);
-                                float2 v = *pv;
-                                v.x -= acc[q].x;
-                                v.y -= acc[q].y;
-                                *pv = v;
-                            }
-                        }
+                    for (int c = 0; c < NB; ++c) {
+                        const float4 la = *reinterpret_cast<const float4 *>(PT + c * RP + NB + I0);
+                        const float4 lb = *reinterpret_cast<const float4 *>(PT + c * RP + NB + I0 + 2);
+                        const float4 wa = *reinterpret_cast<const float4 *>(WT + c * WS + J0);
+                        const float4 wb = *reinterpret_cast<const float4 *>(WT + c * WS + J0 + 2);
+                        const float2 l[4] = {make_float2(la.x, la.y), make_float2(la.z, la.w), make_float2(lb.x, lb.y),
+                                             make_float2(lb.z, lb.w)};
+                        const float2 w[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
+                                             make_float2(wb.z, wb.w)};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q)
+#pragma unroll
+                            for (int r = 0; r < 4; ++r) cmaddf(acc[q][r], l[r], w[q]);
                     }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int I = I0 + r, J = J0 + q;
+                            if (I < tr && J < tr && J <= I)
+                                AB[(p0 + NB + J) * B1 + (I - J)] =
+                                    make_float2(old[q][r].x - acc[q][r].x, old[q][r].y - acc[q][r].y);
+                        }
                 }
             }
         }
@@ -564,7 +584,7 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
     return GCIE_OK;
 }
 
-size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)(NB + b) * NB + (size_t)b * NB + NB); }
+size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)NB * factor_rp(b) + (size_t)NB * factor_ws(b) + NB); }
 size_t band_smem_solve(int b, int sc)
 {
     // window (b + 2 SB) x sc + two slabs (b + 2 SB) x SB
@@ -598,7 +618,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     {
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
         LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
-        k_band_ldlt<<<nshift, 1024, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
+        k_band_ldlt<<<nshift, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int hs = 0;
