@@ -14,7 +14,7 @@
 //      t = 0..b, so column j is contiguous; assembled and updated in place by the factorization;
 //   G  (the factor, from the start of the buffer): block-column layout, block kb (columns
 //      kb SB .. kb SB + SB - 1) is a dense (b + SB) x SB array G_kb[il][c] = l_{kb SB + il, kb SB + c}
-//      (d_j on the diagonal, zero outside the band).  The factorization writes each finished panel
+//      (1 / d_j on the diagonal, so the sweeps never divide; zero outside the band).  The factorization writes each finished panel
 //      there; G's block kb ends before the AB columns still being factored begin, so the two share
 //      one buffer.  In this layout the forward sweep reads one contiguous block per step and the
 //      backward sweep contiguous SB x SB pieces.
@@ -59,11 +59,6 @@ __device__ __forceinline__ void cmaddf(float2 &a, float2 l, float2 w)
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
-__device__ __forceinline__ float2 cdivf(float2 a, float2 b)
-{
-    const float den = b.x * b.x + b.y * b.y;
-    return make_float2((a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den);
-}
 
 // ------------------------------------------------------------------ assembly
 __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
@@ -88,21 +83,32 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 // ------------------------------------------------------------------ factorization
 // One CTA (KT threads) per shift walks the band by panels of NB columns.  Shared memory:
 // PT[c][t] = A[p0 + t][p0 + c] (panel transposed: NB x R, R = NB + b, row stride RP),
-// WT[c][J] = l_{p0+NB+J, p0+c} d_c (NB x b, row stride WS), D[NB].  Per panel:
+// WT[c][J] = l_{p0+NB+J, p0+c} d_c (NB x b, row stride WS), D[NB], DI[NB] = 1 / D.  Per panel:
 //   1. load the panel with cp.async (every element in flight at once);
-//   2. warp 0 factors the NB x NB diagonal block (lane = row, __syncwarp between columns);
+//   2. warp 0 factors the NB x NB diagonal block in registers (lane = row, the column entries
+//      l_{c2,c} passed by shuffles);
 //   3. every row t >= NB of the panel is solved against the diagonal block by one thread
 //      (l_tc = (a_tc - sum_{c'<c} l_tc' d_c' l_cc') / d_c), no block-wide synchronisation;
-//   4. the panel goes to its two blocks of G (all (b + SB) x SB entries, zeros outside the band)
+//   4. the panel goes to its two blocks of G (all (b + SB) x SB entries: 1 / d on the diagonal,
+//      zeros outside the band)
 //      and WT = (L D)^T is formed;
-//   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel,
-//      4 x 4 tiles per thread: a warp owns a group of 4 columns J, its lanes consecutive groups of
-//      4 rows I; per c one 16-byte load gives two rows of PT (two columns of WT), so the shared
-//      traffic is one byte per FMA; the old band values are loaded before the products.
+//   5. trailing update A[i][j] -= sum_c l_ic d_c l_jc on the b x b lower triangle below the panel.
+//      Work items of 4 columns x 128 rows are dealt to the warps in turn; a lane takes rows
+//      I0 + lane + 32 r (r < 4), so its reads of PT are conflict-free across the warp, the WT reads
+//      are broadcasts, and the read-modify-writes of the band are coalesced; the old band values
+//      are loaded before the products so that their latency overlaps them.
 constexpr int KT = 512;       // threads per CTA of the factorization
+constexpr int TJ = 4;         // columns of a trailing-update item
+constexpr int TR = 4;         // rows per lane of a trailing-update item (128 rows per item)
 
 static int factor_rp(int b) { return ((NB + b + 4) + 3) & ~3; }
-static int factor_ws(int b) { return ((b + 4) + 3) & ~3; }
+static int factor_ws(int b) { return ((b + TJ) + 3) & ~3; }
+
+__device__ __forceinline__ float2 cinvf(float2 d)
+{
+    const float r = 1.0f / (d.x * d.x + d.y * d.y);
+    return make_float2(d.x * r, -d.y * r);
+}
 
 __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
                                                   int *__restrict__ status)
@@ -112,51 +118,62 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
     const int64_t B1 = b + 1;
     float2 *Gf = ABp[blockIdx.x];
     float2 *AB = Gf + ab_off;
-    const int64_t nblk = (n + SB - 1) / SB, GB = (int64_t)(b + SB) * SB;
+    const int64_t nblk = (n + SB - 1) / SB;
+    const int GB = (b + SB) * SB;
     const int R = NB + b;
-    const int RP = ((NB + b + 4) + 3) & ~3, WS = ((b + 4) + 3) & ~3;
+    const int RP = ((NB + b + 4) + 3) & ~3, WS = ((b + TJ) + 3) & ~3;
     float2 *PT = sm2;                   // NB x RP
     float2 *WT = PT + (size_t)NB * RP;  // NB x WS
     float2 *D = WT + (size_t)NB * WS;   // NB
+    float2 *DI = D + NB;                // NB
     const int tid = threadIdx.x, nth = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nth >> 5;
     const float2 zero = make_float2(0.f, 0.f);
     for (int64_t p0 = 0; p0 < n; p0 += NB) {
         const int nc = (int)min((int64_t)NB, n - p0);
         const int rows = (int)min((int64_t)R, n - p0);
         // 1. load
-        for (int e = tid; e < NB * RP; e += nth) {
-            const int c = e / RP, t = e % RP;
-            if (c < nc && t >= c && t < rows && t - c <= b) {
-                const unsigned sa = (unsigned)__cvta_generic_to_shared(PT + e);
-                asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(AB + (p0 + c) * B1 + (t - c)) : "memory");
-            } else {
-                PT[e] = zero;
+        for (int c = 0; c < NB; ++c)
+            for (int t = tid; t < RP; t += nth) {
+                float2 *dst = PT + c * RP + t;
+                if (c < nc && t >= c && t < rows && t - c <= b) {
+                    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sa), "l"(AB + (p0 + c) * B1 + (t - c)) : "memory");
+                } else {
+                    *dst = zero;
+                }
             }
-        }
         asm volatile("cp.async.commit_group;" ::: "memory");
         asm volatile("cp.async.wait_group 0;" ::: "memory");
         __syncthreads();
-        // 2. diagonal block (warp 0, lane = row)
+        // 2. diagonal block (warp 0; lane r holds row r: a[c] = A[p0 + r][p0 + c], c <= r)
         if (warp == 0) {
-            for (int c = 0; c < nc; ++c) {
-                const float2 d = PT[c * RP + c];
-                if (lane > c && lane < nc && lane - c <= b) PT[c * RP + lane] = cdivf(PT[c * RP + lane], d);
-                __syncwarp();
-                if (lane > c && lane < nc) {
-                    const float2 l = PT[c * RP + lane];
-                    for (int c2 = c + 1; c2 <= lane; ++c2) {
-                        const float2 w = cmulf(d, PT[c * RP + c2]);
-                        float2 v = PT[c2 * RP + lane];
-                        cmsubf(v, l.x, l.y, w);
-                        PT[c2 * RP + lane] = v;
+            const int r = lane;
+            float2 a[NB];
+#pragma unroll
+            for (int c = 0; c < NB; ++c) a[c] = (r < NB && c <= r) ? PT[c * RP + r] : zero;
+#pragma unroll 16
+            for (int c = 0; c < NB; ++c) {
+                const float2 d = make_float2(__shfl_sync(0xffffffffu, a[c].x, c), __shfl_sync(0xffffffffu, a[c].y, c));
+                const float2 di = cinvf(d);
+                const bool below = r > c && r < nc;
+                if (below) a[c] = cmulf(a[c], di);                          // l_rc
+                const float2 ld = cmulf(a[c], d);
+#pragma unroll 16
+                for (int c2 = 1; c2 < NB; ++c2) {
+                    if (c2 > c) {
+                        const float2 w = make_float2(__shfl_sync(0xffffffffu, a[c].x, c2), __shfl_sync(0xffffffffu, a[c].y, c2));
+                        if (below && c2 <= r) cmsubf(a[c2], ld.x, ld.y, w);
                     }
                 }
-                if (lane == 0) {
+                if (r == 0 && c < nc) {
                     D[c] = d;
+                    DI[c] = di;
                     if (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)) atomicExch(status, 1);
                 }
-                __syncwarp();
             }
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (r < nc && c < r) PT[c * RP + r] = a[c];
         }
         __syncthreads();
         // 3. rows below the diagonal block: one thread per row
@@ -166,14 +183,15 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
             for (int c = 0; c < NB; ++c) a[c] = PT[c * RP + t];
 #pragma unroll
             for (int c = 0; c < NB; ++c) {
-                if (c >= nc) break;
-                const float2 l = cdivf(a[c], D[c]);
-                a[c] = l;
-                const float2 ld = cmulf(l, D[c]);
+                if (c < nc) {
+                    const float2 l = cmulf(a[c], DI[c]);
+                    a[c] = l;
+                    const float2 ld = cmulf(l, D[c]);
 #pragma unroll
-                for (int c2 = c + 1; c2 < NB; ++c2) {
-                    const float2 lc = PT[c * RP + c2];    // l_{c2, c} of the diagonal block
-                    cmsubf(a[c2], ld.x, ld.y, lc);
+                    for (int c2 = c + 1; c2 < NB; ++c2) {
+                        const float2 lc = PT[c * RP + c2];    // l_{c2, c} of the diagonal block
+                        cmsubf(a[c2], ld.x, ld.y, lc);
+                    }
                 }
             }
 #pragma unroll
@@ -181,62 +199,78 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
         }
         __syncthreads();
         // 4. write back (D on the diagonal) and WT = (L D)^T for the rows below the panel
-        for (int e = tid; e < (NB / SB) * (int)GB; e += nth) {
-            const int h = e / (int)GB, r = e % (int)GB;
-            const int il = r / SB, cp = r % SB;
+#pragma unroll
+        for (int h = 0; h < NB / SB; ++h) {
             const int64_t kb = p0 / SB + h;
-            if (kb >= nblk) continue;
-            const int c = h * SB + cp, t = h * SB + il;      // panel column, panel row
-            float2 v = zero;
-            if (c < nc && t >= c && t < rows && t - c <= b) v = t == c ? D[c] : PT[c * RP + t];
-            Gf[kb * GB + r] = v;
+            if (kb >= nblk) break;
+            float2 *g = Gf + kb * GB;
+            for (int e = tid; e < GB; e += nth) {
+                const int il = e / SB, cp = e % SB;
+                const int c = h * SB + cp, t = h * SB + il;  // panel column, panel row
+                float2 v = zero;
+                if (c < nc && t >= c && t < rows && t - c <= b) v = t == c ? DI[c] : PT[c * RP + t];
+                g[e] = v;
+            }
         }
-        for (int e = tid; e < NB * WS; e += nth) {
-            const int c = e / WS, J = e % WS;
-            WT[e] = (c < nc && J < b && NB + J < rows) ? cmulf(PT[c * RP + NB + J], D[c]) : zero;
-        }
+        for (int c = 0; c < NB; ++c)
+            for (int J = tid; J < WS; J += nth)
+                WT[c * WS + J] = (c < nc && J < b && NB + J < rows) ? cmulf(PT[c * RP + NB + J], D[c]) : zero;
         __syncthreads();
         // 5. trailing update
         if (nc == NB) {
             const int tr = (int)min((int64_t)b, n - p0 - NB);
-            const int njb = (tr + 3) / 4;
-            for (int jb = warp; jb < njb; jb += nwarp) {
-                const int J0 = 4 * jb;
-                for (int I0 = J0 + 4 * lane; I0 < tr; I0 += 128) {
-                    float2 old[4][4], acc[4][4];
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const int I = I0 + r, J = J0 + q;
-                            old[q][r] = (I < tr && J < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
-                            acc[q][r] = zero;
-                        }
-#pragma unroll
-                    for (int c = 0; c < NB; ++c) {
-                        const float4 la = *reinterpret_cast<const float4 *>(PT + c * RP + NB + I0);
-                        const float4 lb = *reinterpret_cast<const float4 *>(PT + c * RP + NB + I0 + 2);
-                        const float4 wa = *reinterpret_cast<const float4 *>(WT + c * WS + J0);
-                        const float4 wb = *reinterpret_cast<const float4 *>(WT + c * WS + J0 + 2);
-                        const float2 l[4] = {make_float2(la.x, la.y), make_float2(la.z, la.w), make_float2(lb.x, lb.y),
-                                             make_float2(lb.z, lb.w)};
-                        const float2 w[4] = {make_float2(wa.x, wa.y), make_float2(wa.z, wa.w), make_float2(wb.x, wb.y),
-                                             make_float2(wb.z, wb.w)};
-#pragma unroll
-                        for (int q = 0; q < 4; ++q)
-#pragma unroll
-                            for (int r = 0; r < 4; ++r) cmaddf(acc[q][r], l[r], w[q]);
-                    }
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-#pragma unroll
-                        for (int r = 0; r < 4; ++r) {
-                            const int I = I0 + r, J = J0 + q;
-                            if (I < tr && J < tr && J <= I)
-                                AB[(p0 + NB + J) * B1 + (I - J)] =
-                                    make_float2(old[q][r].x - acc[q][r].x, old[q][r].y - acc[q][r].y);
-                        }
+            const int njg = (tr + TJ - 1) / TJ;
+            // items (column group g, row chunk k): rows J0 + 128 k .. + 128; enumerate group by group
+            int item = warp, g = 0, kbase = 0;
+            for (;;) {
+                while (g < njg) {
+                    const int nk = (tr - g * TJ + 32 * TR - 1) / (32 * TR);
+                    if (item < kbase + nk) break;
+                    kbase += nk;
+                    ++g;
                 }
+                if (g >= njg) break;
+                const int J0 = g * TJ, I0 = J0 + (item - kbase) * 32 * TR;
+                float2 acc[TR][TJ], old[TR][TJ];
+#pragma unroll
+                for (int r = 0; r < TR; ++r)
+#pragma unroll
+                    for (int q = 0; q < TJ; ++q) {
+                        const int I = I0 + lane + 32 * r, J = J0 + q;
+                        acc[r][q] = zero;
+                        old[r][q] = (I < tr && J < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                    }
+#pragma unroll 2
+                for (int c = 0; c < NB; ++c) {
+                    float2 l[TR];
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        const int I = I0 + lane + 32 * r;
+                        l[r] = I < tr ? PT[c * RP + NB + I] : zero;
+                    }
+                    const float4 *w4 = reinterpret_cast<const float4 *>(WT + c * WS + J0);
+#pragma unroll
+                    for (int q2 = 0; q2 < TJ / 2; ++q2) {
+                        const float4 w = w4[q2];
+#pragma unroll
+                        for (int r = 0; r < TR; ++r) {
+                            cmaddf(acc[r][2 * q2], l[r], make_float2(w.x, w.y));
+                            cmaddf(acc[r][2 * q2 + 1], l[r], make_float2(w.z, w.w));
+                        }
+                    }
+                }
+#pragma unroll
+                for (int q = 0; q < TJ; ++q) {
+                    const int J = J0 + q;
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        const int I = I0 + lane + 32 * r;
+                        if (I < tr && J < tr && J <= I)
+                            AB[(p0 + NB + J) * B1 + (I - J)] =
+                                make_float2(old[r][q].x - acc[r][q].x, old[r][q].y - acc[r][q].y);
+                    }
+                }
+                item += nwarp;
             }
         }
         __syncthreads();
@@ -390,7 +424,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             }
             if (lg < nb) {
                 Y[bslot(lg) * SC + cg] = y;
-                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cdivf(y, Lb[lg * SB + lg]);
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmulf(y, Lb[lg * SB + lg]);   // y / d
             }
         }
         __syncthreads();
@@ -584,7 +618,7 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
     return GCIE_OK;
 }
 
-size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)NB * factor_rp(b) + (size_t)NB * factor_ws(b) + NB); }
+size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)NB * factor_rp(b) + (size_t)NB * factor_ws(b) + 2 * NB); }
 size_t band_smem_solve(int b, int sc)
 {
     // window (b + 2 SB) x sc + two slabs (b + 2 SB) x SB
