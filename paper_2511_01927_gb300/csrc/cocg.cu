@@ -782,7 +782,20 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
                                    nullptr, info)
                  : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
                                   bandAB, info);
-    if (bandAB) cudaFreeAsync(bandAB, c->stream);
+    if (bandAB) {
+        cudaFreeAsync(bandAB, c->stream);
+        // the band sweeps give up (and count it) when an asynchronous copy never completes
+        unsigned int to = 0;
+        if (cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+            set_error("cocg: status read failed");
+            rc = GCIE_ECUDA;
+        } else if (to) {
+            cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(to), c->stream);
+            set_error("band sweep: an asynchronous copy did not complete in time");
+            rc = GCIE_ECUDA;
+        }
+    }
     if (rc == GCIE_OK || rc == GCIE_ENOCONV) {
         LaunchScope ls(c, GCIE_K_OTHER, 32.0 * nshift * n * ncol, 0);
         k_scale_rows<<<grid((int64_t)nshift * n * ncol * 2), 256, 0, c->stream>>>(n, ncol, nshift, 2, p->dsc, 0,

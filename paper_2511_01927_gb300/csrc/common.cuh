@@ -36,6 +36,7 @@ void set_error(const std::string &msg);
 struct DbgRec {
     unsigned long long count;
     long long tag, idx, bound;
+    unsigned int wait_timeouts;   // bounded waits that gave up (any build); checked after each solve
 };
 #ifdef GCIE_CHECKED
 __device__ __forceinline__ bool gchk(DbgRec *d, long long idx, long long bound, int tag)

@@ -307,6 +307,40 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// bulk (TMA) copies global -> shared, completed on an mbarrier that expects their byte count
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
+{
+    unsigned ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// waits for the phase with the given parity; gives up (false) after about 2^31 SM clock cycles
+// (one second at 2 GHz), far beyond any copy's duration
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+// orders this thread's earlier shared-memory accesses before later async-proxy (TMA) writes
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
 // One window row, the four columns of a thread: (2q, 2q + 1) and (2q + H, 2q + H + 1), H = SC / 2,
 // so that each 16-byte access of a quarter warp covers 128 contiguous bytes.
 // yr[cols] -= sum_c l[c * LS] yb[c][cols], with the block's values yb in registers.
@@ -339,7 +373,8 @@ __device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 
 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
-        const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
+        const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall,
+        DbgRec *__restrict__ dbg)
 {
     constexpr int H = SC / 2;
     constexpr int QT = SC / 4;                        // threads per row in the updates (four columns each)
@@ -367,6 +402,28 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int q4 = tid % QT, rg = tid / QT;
     const float2 zero = make_float2(0.f, 0.f);
     const int64_t nblk = (n + SB - 1) / SB;
+    __shared__ unsigned long long bars[2];            // completion of the bulk copies into slab buffer 0 / 1
+    int uses0 = 0, uses1 = 0;                         // completed phases of each barrier
+    if (tid == 0) {
+        mbar_init(&bars[0]);
+        mbar_init(&bars[1]);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // wait for slab buffer `buf`; false (in every thread) if some thread's wait gave up
+    auto slab_wait = [&](int buf) -> bool {
+        const int par = (buf ? uses1 : uses0) & 1;
+        const bool ok = mbar_wait(&bars[buf], par);
+        if (buf) ++uses1; else ++uses0;
+        return !__syncthreads_or(!ok);
+    };
+    // after a failed wait: record it, let the copies still in flight land (bounded), leave
+    auto give_up = [&]() {
+        if (tid == 0) atomicAdd(&dbg->wait_timeouts, 1u);
+        mbar_wait(&bars[0], uses0 & 1);
+        mbar_wait(&bars[1], uses1 & 1);
+        cp_async_wait_all();
+    };
 
     // rows [r0, r0 + SB) of src (zero outside [0, n) and past the CTA's columns) into the window,
     // row r0 + c at slot slot0 + c (mod WR)
@@ -383,18 +440,21 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     };
 
     // ---------------- forward: L y = r, then y / d written to Z
-    // slab of block kb: block kb of G as it is, L[il * SB + c] = l_{blk+il, blk+c}
-    auto fwd_slab = [&](int64_t kb, float2 *L) {
-        const float4 *src = reinterpret_cast<const float4 *>(Gf + kb * GB);
-        float4 *dst = reinterpret_cast<float4 *>(L);
-        for (int e = tid; e < GB / 2; e += ST) cp_async16(dst + e, src + e);
+    // slab of block kb: block kb of G as it is, L[il * SB + c] = l_{blk+il, blk+c}; one bulk copy
+    // issued by thread 0
+    auto fwd_slab = [&](int64_t kb, int buf) {
+        if (tid == 0) {
+            fence_proxy_async();
+            mbar_expect(&bars[buf], (unsigned)(GB * sizeof(float2)));
+            bulk_g2s(Lbuf + buf * LBS, Gf + kb * GB, (unsigned)(GB * sizeof(float2)), &bars[buf]);
+        }
     };
     for (int e = tid; e < (b + SB) * SC; e += ST) {
         const int t = e / SC, qq = e % SC;
         if (t < n && qq < nrc) cp_async8(Y + e, Rs + (int64_t)t * ncol + qq);
         else Y[e] = zero;
     }
-    fwd_slab(0, Lbuf);
+    fwd_slab(0, 0);
     cp_async_commit();
     int bs = 0;                                       // slot of row blk
     for (int64_t kb = 0; kb < nblk; ++kb) {
@@ -403,9 +463,9 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         const float2 *Lb = Lbuf + (kb & 1) * LBS;
         auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
         cp_async_wait_all();
-        __syncthreads();
+        if (!slab_wait((int)(kb & 1))) { give_up(); return; }
         // next step's slab and the rows entering the window then (slots of the previous block)
-        if (kb + 1 < nblk) fwd_slab(kb + 1, Lbuf + ((kb + 1) & 1) * LBS);
+        if (kb + 1 < nblk) fwd_slab(kb + 1, (int)((kb + 1) & 1));
         {
             int s0 = bs + b + SB;
             while (s0 >= WR) s0 -= WR;
@@ -457,11 +517,12 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     // blk - (kbs + i) SB .. + SB of block kbs + i of G, so L[(i SB + c) SB + c'] = l_{blk+c, (kbs+i) SB + c'}
     // (rows past the block's b + SB are out of the band: zero); at DOFF the block's own first SB
     // rows, L[DOFF + c SB + c'] = l_{blk+c, blk+c'}
-    auto bwd_slab = [&](int64_t kb, float2 *L) {
+    // 16-byte cp.async copies (many small pieces: one bulk copy each would queue on the copy engine)
+    auto bwd_slab = [&](int64_t kb, int buf) {
+        float4 *dst = reinterpret_cast<float4 *>(Lbuf + buf * LBS);
         const int64_t blk = kb * SB;
         const int64_t kbs = max((int64_t)0, blk - b) / SB;
         const int npc = (int)(kb - kbs);
-        float4 *dst = reinterpret_cast<float4 *>(L);
         constexpr int Q = SB / 2;                     // float4 per row of a piece
         for (int e = tid; e < npc * SB * Q; e += ST) {
             const int i = e / (SB * Q), r = e % (SB * Q);
@@ -485,18 +546,19 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         if (i >= 0 && i < n && qq < nrc) cp_async8(dst, Zs + i * ncol + qq);
         else *dst = zero;
     }
-    bwd_slab(nblk - 1, Lbuf);
+    bwd_slab(nblk - 1, (int)((nblk - 1) & 1));
     cp_async_commit();
     for (int64_t j = 0; j < nblk; ++j) {
         const int64_t blk = lastblk - j * SB;
         const int nb = (int)min((int64_t)SB, n - blk);
-        const float2 *Ls = Lbuf + (j & 1) * LBS;
+        const int buf = (int)((blk / SB) & 1);
+        const float2 *Ls = Lbuf + buf * LBS;
         const float2 *Ld = Ls + DOFF;
         const int64_t kbs = max((int64_t)0, blk - b) / SB;
         auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
         cp_async_wait_all();
         __syncthreads();
-        if (blk > 0) bwd_slab(blk / SB - 1, Lbuf + ((j + 1) & 1) * LBS);
+        if (blk > 0) bwd_slab(blk / SB - 1, buf ^ 1);
         {
             // rows [blk - b - SB, blk - b) go to the slots of rows [blk + SB, blk + 2 SB)
             int s0 = bs + SB;
@@ -670,7 +732,7 @@ static int launch_band_solve(Ctx *c, int64_t n, int b, int nshift, int ncol, con
     const size_t smem = band_smem_solve(b, SC);
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int ngrp = (ncol + SC - 1) / SC;
-    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
+    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z, c->dbg);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
