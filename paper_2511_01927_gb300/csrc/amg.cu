@@ -678,7 +678,7 @@ int AmgWork<T>::init(Ctx *c, const Amg *a, int nshift_, int ncol_, const double2
     size_t total = 0;
     for (int l = 1; l < nl; ++l) total += 4 * (size_t)nshift * a->lev[l].n * ncol * sizeof(C);
     total += (size_t)nshift * a->nc * a->nc * sizeof(C) + (size_t)nshift * a->nc * sizeof(int) + 256;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&base, total + 64 * 256, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&base, total + 64 * 256));
     char *q = base;
     auto take = [&](size_t b) { char *r = q; q += (b + 255) & ~(size_t)255; return r; };
     for (int l = 1; l < nl; ++l) {
@@ -703,7 +703,7 @@ int AmgWork<T>::init(Ctx *c, const Amg *a, int nshift_, int ncol_, const double2
 
 template <typename T> void AmgWork<T>::release()
 {
-    if (base) cudaFreeAsync(base, ctx->stream);
+    if (base) ctx_free(ctx, base);
     base = nullptr;
 }
 

@@ -81,6 +81,34 @@ LaunchScope::~LaunchScope()
     }
 }
 
+cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes)
+{
+    *p = nullptr;
+    cudaError_t e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), c->pool, c->stream);
+    if (e == cudaErrorMemoryAllocation) {
+        // give back what the pool holds idle and try once more
+        cudaGetLastError();
+        cudaStreamSynchronize(c->stream);
+        cudaMemPoolTrimTo(c->pool, 0);
+        e = cudaMallocFromPoolAsync(p, std::max<size_t>(bytes, 1), c->pool, c->stream);
+    }
+    if (e != cudaSuccess) { cudaGetLastError(); *p = nullptr; }
+    return e;
+}
+
+void ctx_free(Ctx *c, void *p)
+{
+    if (p) cudaFreeAsync(p, c->stream);
+}
+
+size_t ctx_pool_idle(Ctx *c)
+{
+    unsigned long long reserved = 0, used = 0;
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrReservedMemCurrent, &reserved);
+    cudaMemPoolGetAttribute(c->pool, cudaMemPoolAttrUsedMemCurrent, &used);
+    return reserved > used ? (size_t)(reserved - used) : 0;
+}
+
 int ctx_scratch(Ctx *c, size_t bytes, void **out)
 {
     if (bytes > c->scratch_bytes) {
@@ -233,6 +261,22 @@ int gcie_create(gcie_ctx **out, int device, void *stream)
         set_error("gcie_create: allocation failed");
         return GCIE_ECUDA;
     }
+    {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = device;
+        unsigned long long keep = ~(unsigned long long)0;
+        if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess ||
+            cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(c->dbg);
+            delete c;
+            set_error("gcie_create: memory pool creation failed");
+            return GCIE_ECUDA;
+        }
+    }
     if (stream) {
         c->stream = (cudaStream_t)stream;
     } else {
@@ -255,6 +299,10 @@ void gcie_destroy(gcie_ctx *c)
     flush_timing(c);
     if (c->scratch) cudaFree(c->scratch);
     if (c->dbg) cudaFree(c->dbg);
+    if (c->pool) {
+        cudaStreamSynchronize(c->stream);
+        cudaMemPoolDestroy(c->pool);
+    }
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -431,7 +479,7 @@ int gcie_trapezoid_nodes(double c, double r, int32_t N, double *h_z, double *h_w
 
 static int upload_shifts(gcie_ctx *c, int nshift, const double *h_z, double2 **d_z)
 {
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)d_z, sizeof(double2) * std::max(nshift, 1), c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)d_z, sizeof(double2) * std::max(nshift, 1)));
     GCIE_CUDA_TRY(cudaMemcpyAsync(*d_z, h_z, sizeof(double2) * nshift, cudaMemcpyHostToDevice, c->stream));
     return GCIE_OK;
 }
@@ -443,7 +491,7 @@ int gcie_shifted_spmm_f32(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const dou
     double2 *dz = nullptr;
     GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
     int rc = shifted_spmm_f32(c, p, nshift, dz, ncol, (const float2 *)d_P, (float2 *)d_Q);
-    cudaFreeAsync(dz, c->stream);
+    ctx_free(c, dz);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
     return rc;
@@ -456,7 +504,7 @@ int gcie_shifted_spmm_f64(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const dou
     double2 *dz = nullptr;
     GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
     int rc = shifted_spmm_f64(c, p, nshift, dz, ncol, (const double2 *)d_P, (double2 *)d_Q);
-    cudaFreeAsync(dz, c->stream);
+    ctx_free(c, dz);
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (rc == GCIE_OK && e != cudaSuccess) { set_error(cudaGetErrorString(e)); rc = GCIE_ECUDA; }
     return rc;
@@ -654,10 +702,10 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     }
     const int L = L0 + (L0 & 1);   // even width for the FP32 vector loads
     double *dV0 = nullptr, *dB0 = nullptr;
-    GCIE_CUDA_TRY(cudaMalloc(&dV0, sizeof(double) * (size_t)n * L));
-    if (cudaMalloc(&dB0, sizeof(double) * (size_t)n * L) != cudaSuccess) { cudaFree(dV0); set_error("out of memory"); return GCIE_ENOMEM; }
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dV0, sizeof(double) * (size_t)n * L));
+    if (ctx_malloc(c, (void **)&dB0, sizeof(double) * (size_t)n * L) != cudaSuccess) { ctx_free(c, dV0); set_error("out of memory"); return GCIE_ENOMEM; }
     int rc = GCIE_OK;
-    struct Guard { std::vector<void *> ptrs; ~Guard() { for (void *q : ptrs) cudaFree(q); } } guard;
+    struct Guard { Ctx *c; std::vector<void *> ptrs; ~Guard() { for (void *q : ptrs) ctx_free(c, q); } } guard{c, {}};
     guard.ptrs.push_back(dV0);
     guard.ptrs.push_back(dB0);
     GCIE_CUDA_TRY(cudaMemsetAsync(dV0, 0, sizeof(double) * (size_t)n * L, c->stream));
@@ -668,6 +716,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
 
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
+    free_b += ctx_pool_idle(c);   // reserved by this context's pool, reusable
     const size_t budget = o->hbm_budget_bytes ? o->hbm_budget_bytes : (size_t)(0.85 * free_b);
     const size_t esz = o->precision == GCIE_FP64 ? 16 : 8;
     int64_t cocg_iters = 0;
@@ -715,7 +764,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             int nrhs = 1;
             double *dBb = nullptr;
             double2 *dX = nullptr;
-            if (cudaMalloc(&dX, sizeof(double2) * (size_t)nshift * n * ncol) != cudaSuccess) {
+            if (ctx_malloc(c, (void **)&dX, sizeof(double2) * (size_t)nshift * n * ncol) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("solution block allocation failed");
                 return GCIE_ENOMEM;
@@ -724,10 +773,10 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             bool x0 = false;
             if (it > 0) {
                 nrhs = nb;
-                GCIE_CUDA_TRY(cudaMalloc(&dBb, sizeof(double) * (size_t)nb * n * ncol));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dBb, sizeof(double) * (size_t)nb * n * ncol));
                 guard.ptrs.push_back(dBb);
                 double *tmp = nullptr;
-                GCIE_CUDA_TRY(cudaMalloc(&tmp, sizeof(double) * (size_t)n * ncol));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&tmp, sizeof(double) * (size_t)n * ncol));
                 guard.ptrs.push_back(tmp);
                 for (int bi = 0; bi < nb; ++bi) {
                     ContourState &s = cs[act[b0 + bi]];
@@ -745,7 +794,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                             coef[(size_t)j * ncol + l] = cdiv(make_double2(1, 0), d);
                         }
                     double2 *dcoef = nullptr;
-                    GCIE_CUDA_TRY(cudaMalloc(&dcoef, sizeof(double2) * coef.size()));
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dcoef, sizeof(double2) * coef.size()));
                     guard.ptrs.push_back(dcoef);
                     GCIE_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, c->stream));
                     {
@@ -770,9 +819,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 const int pY = m * ncol;
                 if (pY > 256) { set_error("moments x columns > 256"); return GCIE_EINVAL; }
                 double *Y = nullptr, *Q = nullptr;
-                GCIE_CUDA_TRY(cudaMalloc(&Y, sizeof(double) * (size_t)n * pY));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Y, sizeof(double) * (size_t)n * pY));
                 guard.ptrs.push_back(Y);
-                GCIE_CUDA_TRY(cudaMalloc(&Q, sizeof(double) * (size_t)n * pY));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Q, sizeof(double) * (size_t)n * pY));
                 guard.ptrs.push_back(Q);
                 GCIE_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * pY, c->stream));
                 std::vector<double2> coef((size_t)half * m);
@@ -785,9 +834,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 int rank = 0;
                 GCIE_TRY(m_orthonormalize(c, p, n, pY, Y, 1e-14, Q, &rank));
                 double *Qc = nullptr, *Z = nullptr;
-                GCIE_CUDA_TRY(cudaMalloc(&Qc, sizeof(double) * (size_t)n * rank));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qc, sizeof(double) * (size_t)n * rank));
                 guard.ptrs.push_back(Qc);
-                GCIE_CUDA_TRY(cudaMalloc(&Z, sizeof(double) * (size_t)n * rank));
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Z, sizeof(double) * (size_t)n * rank));
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
                     k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pY, rank, rank, Q, Qc, c->dbg);
@@ -795,7 +844,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 std::vector<double> th(rank), rs(rank);
                 rc = rayleigh_ritz(c, p, rank, Qc, Z, th.data(), rs.data());
-                if (rc) { cudaFree(Z); return rc; }
+                if (rc) { ctx_free(c, Z); return rc; }
                 bool unconverged_inside = false;
                 double worst = 0.0;
                 std::vector<int> keep;
@@ -833,9 +882,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     if (!keep.empty()) {
                         int *didx = nullptr;
                         double *dout = nullptr;
-                        GCIE_CUDA_TRY(cudaMalloc(&didx, sizeof(int) * keep.size()));
+                        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&didx, sizeof(int) * keep.size()));
                         guard.ptrs.push_back(didx);
-                        GCIE_CUDA_TRY(cudaMalloc(&dout, sizeof(double) * (size_t)n * keep.size()));
+                        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dout, sizeof(double) * (size_t)n * keep.size()));
                         guard.ptrs.push_back(dout);
                         GCIE_CUDA_TRY(cudaMemcpyAsync(didx, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, c->stream));
                         {
@@ -852,11 +901,11 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     }
                     s.done = true;
                     s.status = (unconverged_inside && !(stalled && worst > 1e-6)) ? GCIE_ENOCONV : GCIE_OK;
-                    cudaFree(Z);
-                    if (s.Z) { cudaFree(s.Z); s.Z = nullptr; }
+                    ctx_free(c, Z);
+                    if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
                 } else {
                     // FEAST: next iteration filters all Ritz vectors, one moment
-                    if (s.Z) cudaFree(s.Z);
+                    if (s.Z) ctx_free(c, s.Z);
                     s.Z = Z;
                     s.q = rank;
                     s.theta = th;
@@ -867,13 +916,13 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             // release per-batch buffers now (the guard frees anything left on error paths)
             GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
             for (void *q : guard.ptrs)
-                if (q != dV0 && q != dB0) cudaFree(q);
+                if (q != dV0 && q != dB0) ctx_free(c, q);
             guard.ptrs.assign({dV0, dB0});
             b0 = b1;
         }
     }
     for (auto &s : cs)
-        if (s.Z) { cudaFree(s.Z); s.Z = nullptr; }
+        if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
 
     // merge and de-duplicate across contours (Algorithm 1, last step)
     struct Pair { double v, r; int k; const double *x; };

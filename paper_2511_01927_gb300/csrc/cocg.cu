@@ -531,7 +531,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     size_t bytes = 0;
     for (size_t b : sizes) bytes += (b + 255) & ~(size_t)255;
     char *base = nullptr;
-    cudaError_t ce = cudaMallocAsync((void **)&base, bytes, c->stream);
+    cudaError_t ce = ctx_malloc(c, (void **)&base, bytes);
     if (ce != cudaSuccess) {
         set_error(std::string("cocg: device allocation of ") + std::to_string(bytes) + " bytes failed");
         cudaGetLastError();
@@ -603,7 +603,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), nshift * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
     if (amg) {
         rc = aw.init(c, amg, nshift, ncol, d_z);
-        if (rc) { aw.release(); cudaFreeAsync(base, c->stream); return rc; }
+        if (rc) { aw.release(); ctx_free(c, base); return rc; }
     }
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_rhs, h_rhs_of, nshift * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     GCIE_CUDA_TRY(cudaMemsetAsync(D, 0, blk * sizeof(C), c->stream));
@@ -727,7 +727,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     }
 done:
     if (amg) aw.release();
-    cudaFreeAsync(base, c->stream);
+    ctx_free(c, base);
     return rc;
 }
 
@@ -741,7 +741,7 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
     // solve the diagonally scaled system D^-1/2 (z M - K) D^-1/2 y = D^-1/2 b, x = D^-1/2 y
     const int64_t n = p->n;
     double *Bs = nullptr;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&Bs, sizeof(double) * (size_t)nrhs * n * ncol, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Bs, sizeof(double) * (size_t)nrhs * n * ncol));
     auto grid = [&](int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 32)); };
     int rc = GCIE_OK;
     {
@@ -783,7 +783,7 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
                  : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
                                   bandAB, info);
     if (bandAB) {
-        cudaFreeAsync(bandAB, c->stream);
+        ctx_free(c, bandAB);
         // the band sweeps give up (and count it) when an asynchronous copy never completes
         unsigned int to = 0;
         if (cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -802,7 +802,7 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
                                                                                   (const double *)d_X, (double *)d_X);
         if (cudaGetLastError() != cudaSuccess) { set_error("cocg: unscale launch failed"); rc = GCIE_ECUDA; }
     }
-    cudaFreeAsync(Bs, c->stream);
+    ctx_free(c, Bs);
     return rc;
 }
 

@@ -88,7 +88,15 @@ struct Ctx {
     void *scratch = nullptr;
     size_t scratch_bytes = 0;
     DbgRec *dbg = nullptr;           // device record of the first index violation (checked builds)
+    cudaMemPool_t pool = nullptr;    // stream-ordered pool of the solve-time buffers
 };
+
+// Stream-ordered allocation from the context's pool.  The pool keeps what it has reserved between
+// calls (release threshold: unlimited), so the large per-solve buffers are reused instead of being
+// mapped and unmapped on every solve; gcie_destroy returns everything.
+cudaError_t ctx_malloc(Ctx *c, void **p, size_t bytes);
+void ctx_free(Ctx *c, void *p);
+size_t ctx_pool_idle(Ctx *c);        // bytes the pool holds reserved but not in use
 
 // Launch bookkeeping: every kernel launch goes through `launch_begin/launch_end` so the stats
 // count launches, algorithmic bytes and (when profiling) event-timed durations per class.

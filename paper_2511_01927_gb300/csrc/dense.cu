@@ -46,7 +46,7 @@ int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int nco
 {
     if (m > 8 || m < 1) { set_error("moments: 1 <= m <= 8"); return GCIE_EINVAL; }
     double2 *d_coef = nullptr;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_coef, sizeof(double2) * nshift * m, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_coef, sizeof(double2) * nshift * m));
     cudaError_t e = cudaMemcpyAsync(d_coef, h_coef, sizeof(double2) * nshift * m, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) {
         LaunchScope ls(c, GCIE_K_MOMENT, (double)n * ncol * (16.0 * nshift + 16.0 * m), 4.0 * n * ncol * nshift * m);
@@ -54,7 +54,7 @@ int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int nco
         k_moments<<<(int)std::max<int64_t>(1, blocks), 256, 0, c->stream>>>(n, nshift, d_coef, m, ncol, X, S, ldS, c->dbg);
         e = cudaGetLastError();
     }
-    cudaFreeAsync(d_coef, c->stream);
+    ctx_free(c, d_coef);
     if (e != cudaSuccess) { set_error(std::string("moments: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
     return GCIE_OK;
 }
@@ -544,11 +544,11 @@ int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
         return GCIE_OK;
     }
     double *wk = nullptr;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&wk, sizeof(double) * (size_t)nmat * p * p, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&wk, sizeof(double) * (size_t)nmat * p * p));
     LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
     k_jacobi<<<nmat, 1024, 0, c->stream>>>(p, A, w, V, wk, 1e-15, 60, c->dbg);
     cudaError_t e = cudaGetLastError();
-    cudaFreeAsync(wk, c->stream);
+    ctx_free(c, wk);
     if (e != cudaSuccess) { set_error(std::string("jacobi: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
     return GCIE_OK;
 }
@@ -717,15 +717,15 @@ int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double 
 {
     double *work = nullptr, *Q1 = nullptr;
     const size_t wbytes = sizeof(double) * ((size_t)n * ncol + 3 * (size_t)ncol * ncol + ncol);
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&work, wbytes, c->stream));
-    cudaError_t e = cudaMallocAsync((void **)&Q1, sizeof(double) * (size_t)n * ncol, c->stream);
-    if (e != cudaSuccess) { cudaFreeAsync(work, c->stream); set_error("m_orthonormalize: out of memory"); return GCIE_ENOMEM; }
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&work, wbytes));
+    cudaError_t e = ctx_malloc(c, (void **)&Q1, sizeof(double) * (size_t)n * ncol);
+    if (e != cudaSuccess) { ctx_free(c, work); set_error("m_orthonormalize: out of memory"); return GCIE_ENOMEM; }
     int r1 = 0, r2 = 0;
     int rc = orth_pass(c, p, n, ncol, Y, drop, Q1, &r1, work);
     // second pass on the r1 valid columns (zero columns beyond r1 are dropped by the rank test)
     if (rc == GCIE_OK) rc = orth_pass(c, p, n, ncol, Q1, drop, Q, &r2, work);
-    cudaFreeAsync(work, c->stream);
-    cudaFreeAsync(Q1, c->stream);
+    ctx_free(c, work);
+    ctx_free(c, Q1);
     *rank = r2;
     return rc;
 }
@@ -735,7 +735,7 @@ int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, do
     const int64_t n = p->n;
     double *work = nullptr;
     const size_t wbytes = sizeof(double) * (2 * (size_t)n * q + 2 * (size_t)q * q + 3 * (size_t)q);
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&work, wbytes, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&work, wbytes));
     double *KQ = work;                        // n x q, later K Z
     double *MZ = KQ + (size_t)n * q;          // n x q
     double *Kh = MZ + (size_t)n * q;          // q x q
@@ -760,7 +760,7 @@ int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, do
         for (int l = 0; l < q; ++l)
             h_res[l] = hz2[l] > 0 ? std::sqrt(hr2[l]) / (p->norm_k1 * std::sqrt(hz2[l])) : INFINITY;
     } while (0);
-    cudaFreeAsync(work, c->stream);
+    ctx_free(c, work);
     return rc;
 }
 

@@ -629,12 +629,13 @@ __global__ void k_rz_partials(int64_t n, int ncol, int64_t rows_per_chunk, int c
 // ------------------------------------------------------------------ host
 BandCache::~BandCache()
 {
-    for (auto &e : entries) cudaFree(e.AB);
+    for (auto &e : entries) ctx_free(ctx, e.AB);
 }
 
 // factors for the given shifts (reusing those already computed for identical shift values)
 int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float2 ***d_ptrs_out)
 {
+    ctx = c;
     std::vector<int> missing;
     std::vector<float2 *> ptr(nshift, nullptr);
     for (int s = 0; s < nshift; ++s) {
@@ -648,9 +649,9 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
         std::vector<double2> hz;
         for (int s : missing) {
             float2 *q = nullptr;
-            if (cudaMalloc(&q, per) != cudaSuccess) {
+            if (ctx_malloc(c, (void **)&q, per) != cudaSuccess) {
                 cudaGetLastError();
-                for (float2 *r : newp) cudaFree(r);
+                for (float2 *r : newp) ctx_free(c, r);
                 set_error("band LDL^T: factor storage allocation failed");
                 return GCIE_ENOMEM;
             }
@@ -659,21 +660,21 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
         }
         float2 **d_p = nullptr;
         double2 *d_z = nullptr;
-        GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_p, sizeof(float2 *) * newp.size(), c->stream));
-        GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_z, sizeof(double2) * hz.size(), c->stream));
+        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_p, sizeof(float2 *) * newp.size()));
+        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_z, sizeof(double2) * hz.size()));
         GCIE_CUDA_TRY(cudaMemcpyAsync(d_p, newp.data(), sizeof(float2 *) * newp.size(), cudaMemcpyHostToDevice, c->stream));
         GCIE_CUDA_TRY(cudaMemcpyAsync(d_z, hz.data(), sizeof(double2) * hz.size(), cudaMemcpyHostToDevice, c->stream));
         int rc = band_factor(c, p, (int)newp.size(), d_z, d_p, newp);
-        cudaFreeAsync(d_p, c->stream);
-        cudaFreeAsync(d_z, c->stream);
-        if (rc) { for (float2 *r : newp) cudaFree(r); return rc; }
+        ctx_free(c, d_p);
+        ctx_free(c, d_z);
+        if (rc) { for (float2 *r : newp) ctx_free(c, r); return rc; }
         for (size_t k = 0; k < missing.size(); ++k) {
             entries.push_back({hz[k], newp[k]});
             ptr[missing[k]] = newp[k];
         }
     }
     float2 **d_ptrs = nullptr;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_ptrs, sizeof(float2 *) * nshift, c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_ptrs, sizeof(float2 *) * nshift));
     GCIE_CUDA_TRY(cudaMemcpyAsync(d_ptrs, ptr.data(), sizeof(float2 *) * nshift, cudaMemcpyHostToDevice, c->stream));
     GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
     *d_ptrs_out = d_ptrs;
@@ -707,7 +708,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int *d_status = nullptr;
-    GCIE_CUDA_TRY(cudaMallocAsync((void **)&d_status, sizeof(int), c->stream));
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_status, sizeof(int)));
     GCIE_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), c->stream));
     const size_t smem = band_smem_factor(b);
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -719,7 +720,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     }
     int hs = 0;
     GCIE_CUDA_TRY(cudaMemcpyAsync(&hs, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    cudaFreeAsync(d_status, c->stream);
+    ctx_free(c, d_status);
     GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
     if (hs) { set_error("band LDL^T: zero or non-finite pivot"); return GCIE_EBREAKDOWN; }
     return GCIE_OK;

@@ -10,6 +10,7 @@ namespace gcie {
 struct BandCache {
     struct Entry { double2 z; float2 *AB; };
     std::vector<Entry> entries;
+    Ctx *ctx = nullptr;      // the context whose pool holds the factors
     // device array of per-shift factor pointers (caller frees it with cudaFreeAsync)
     int get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float2 ***d_ptrs_out);
     ~BandCache();
