@@ -654,6 +654,7 @@ struct ContourState {
     int status = GCIE_OK;
     int prev_conv = -1;        // converged pairs inside I_k after the previous FEAST iteration
     double prev_worst = 0.0;   // worst residual of the unconverged ones
+    std::vector<double> prev_open;   // Ritz values inside I_k still unconverged after it
     // kept pairs
     std::vector<double> kv, kr;
     std::vector<double> kvec;   // column-major n x kept
@@ -848,22 +849,35 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 bool unconverged_inside = false;
                 double worst = 0.0;
                 std::vector<int> keep;
+                std::vector<double> open;
+                // an unconverged value counts as a wanderer when its residual is at the solve-noise
+                // level (> 1e-6) and no unconverged value of the previous iteration lies next to it
+                bool all_wander = true;
                 for (int l = 0; l < rank; ++l) {
                     const bool inside = th[l] >= s.lo && th[l] <= s.hi;
                     if (!inside) continue;
-                    if (rs[l] <= o->tol) keep.push_back(l);
-                    else { unconverged_inside = true; worst = std::max(worst, rs[l]); }
+                    if (rs[l] <= o->tol) { keep.push_back(l); continue; }
+                    unconverged_inside = true;
+                    worst = std::max(worst, rs[l]);
+                    open.push_back(th[l]);
+                    bool near = false;
+                    for (double tp : s.prev_open) near = near || std::fabs(th[l] - tp) <= 1e-4 * std::max(1.0, std::fabs(th[l]));
+                    if (rs[l] <= 1e-6 || near) all_wander = false;
                 }
                 // An iteration that adds no converged pair and does not improve the worst remaining
                 // residual 10x leaves only Ritz values that do not converge: spurious ones, built from
                 // basis directions dominated by solve noise, which move from one iteration to the next.
                 // The contour stops; remaining residuals above 1e-6 are taken as spurious (status OK),
                 // lower ones as a stalled eigenpair (GCIE_ENOCONV).
+                // The same holds as soon as every unconverged value is a wanderer: a true eigenpair
+                // keeps its Ritz value in place from one iteration to the next.
                 bool stalled = false;
                 if (unconverged_inside && it > 0 && (int)keep.size() <= s.prev_conv && worst >= 0.1 * s.prev_worst)
                     stalled = true;
+                if (unconverged_inside && it > 0 && all_wander) stalled = true;
                 s.prev_conv = (int)keep.size();
                 s.prev_worst = worst;
+                s.prev_open = open;
                 s.iters = it + 1;
                 const bool last = (it + 1 == o->max_outer);
                 if (std::getenv("GCIE_VERBOSE")) {
