@@ -30,6 +30,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cooperative_groups.h>
+
 #include "ldlt.cuh"
 
 namespace gcie {
@@ -81,7 +83,10 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 }
 
 // ------------------------------------------------------------------ factorization
-// One CTA (KT threads) per shift walks the band by panels of NB columns.  Shared memory:
+// A cluster of KC CTAs (KT threads each) per shift walks the band by panels of NB columns: every
+// CTA factors the panel (steps 1-4, redundantly: they are short), the trailing update (step 5, the
+// bulk of the work) is split between them, and a cluster barrier closes each panel so that the
+// next panel sees every CTA's updates of the band.  Shared memory (per CTA):
 // PT[c][t] = A[p0 + t][p0 + c] (panel transposed: NB x R, R = NB + b, row stride RP),
 // WT[c][J] = l_{p0+NB+J, p0+c} d_c (NB x b, row stride WS), D[NB], DI[NB] = 1 / D.  Per panel:
 //   1. load the panel with cp.async (every element in flight at once);
@@ -98,6 +103,7 @@ __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const
 //      are broadcasts, and the read-modify-writes of the band are coalesced; the old band values
 //      are loaded before the products so that their latency overlaps them.
 constexpr int KT = 512;       // threads per CTA of the factorization
+constexpr int KC = 2;         // CTAs per shift (cluster)
 constexpr int TJ = 4;         // columns of a trailing-update item
 constexpr int TR = 4;         // rows per lane of a trailing-update item (128 rows per item)
 
@@ -110,13 +116,16 @@ __device__ __forceinline__ float2 cinvf(float2 d)
     return make_float2(d.x * r, -d.y * r);
 }
 
-__global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
-                                                  int *__restrict__ status)
+__global__ void __cluster_dims__(KC, 1, 1) __launch_bounds__(KT)
+k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off, int *__restrict__ status)
 {
+    namespace cgx = cooperative_groups;
+    cgx::cluster_group cl = cgx::this_cluster();
+    const int crank = (int)cl.block_rank();
     extern __shared__ float4 smf4[];
     float2 *sm2 = reinterpret_cast<float2 *>(smf4);
     const int64_t B1 = b + 1;
-    float2 *Gf = ABp[blockIdx.x];
+    float2 *Gf = ABp[blockIdx.x / KC];
     float2 *AB = Gf + ab_off;
     const int64_t nblk = (n + SB - 1) / SB;
     const int GB = (b + SB) * SB;
@@ -168,7 +177,8 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
                 if (r == 0 && c < nc) {
                     D[c] = d;
                     DI[c] = di;
-                    if (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)) atomicExch(status, 1);
+                    if (crank == 0 && (!(d.x * d.x + d.y * d.y > 0.f) || !isfinite(d.x) || !isfinite(d.y)))
+                        atomicExch(status, 1);
                 }
             }
 #pragma unroll
@@ -202,7 +212,7 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
 #pragma unroll
         for (int h = 0; h < NB / SB; ++h) {
             const int64_t kb = p0 / SB + h;
-            if (kb >= nblk) break;
+            if (kb >= nblk || crank != 0) break;
             float2 *g = Gf + kb * GB;
             for (int e = tid; e < GB; e += nth) {
                 const int il = e / SB, cp = e % SB;
@@ -221,7 +231,7 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
             const int tr = (int)min((int64_t)b, n - p0 - NB);
             const int njg = (tr + TJ - 1) / TJ;
             // items (column group g, row chunk k): rows J0 + 128 k .. + 128; enumerate group by group
-            int item = warp, g = 0, kbase = 0;
+            int item = crank * nwarp + warp, g = 0, kbase = 0;
             for (;;) {
                 while (g < njg) {
                     const int nk = (tr - g * TJ + 32 * TR - 1) / (32 * TR);
@@ -270,10 +280,10 @@ __global__ void __launch_bounds__(KT) k_band_ldlt(int64_t n, int b, float2 *cons
                                 make_float2(old[r][q].x - acc[r][q].x, old[r][q].y - acc[r][q].y);
                     }
                 }
-                item += nwarp;
+                item += KC * nwarp;
             }
         }
-        __syncthreads();
+        cl.sync();   // every CTA's band updates are visible before the next panel is loaded
     }
 }
 
@@ -715,7 +725,7 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     {
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
         LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
-        k_band_ldlt<<<nshift, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
+        k_band_ldlt<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int hs = 0;
