@@ -29,6 +29,7 @@
 //                    next block step copied in asynchronously.
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 
 #include <cooperative_groups.h>
 
@@ -765,6 +766,11 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
         if (!best || cost < best_cost) { best = sc; best_cost = cost; }
     }
     if (!best) { set_error("band sweep: bandwidth too large for shared memory"); return GCIE_EINVAL; }
+    // GCIE_BAND_SC = 8 | 16 | 32 forces the column count per CTA (tuning and tests of every variant)
+    if (const char *e = std::getenv("GCIE_BAND_SC")) {
+        const int v = std::atoi(e);
+        if ((v == 8 || v == 16 || v == 32) && band_smem_solve(b, v) <= c->smem_optin) best = v;
+    }
     const int ngrp = (ncol + best - 1) / best;
     const double macs = 2.0 * nact * n * b * ncol;
     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);

@@ -125,6 +125,28 @@ def test_shifted_solve_matches_lu(G, ctx, small2d, precision, precond):
         assert np.max(err) < 1e-7, (s, err)
 
 
+@pytest.mark.parametrize("sc", [8, 16, 32])
+def test_band_sweep_variants(G, ctx, small2d, sc, monkeypatch):
+    """Every column-per-CTA variant of the band sweeps gives the same converged solves (ragged
+    column groups: 38 columns do not fill the last group of 8, 16 or 32)."""
+    monkeypatch.setenv("GCIE_BAND_SC", str(sc))
+    K, M, spec, pen = small2d
+    lo, hi = spec["lo"], spec["hi"]
+    z, _ = O.trapezoid_nodes(0.5 * (lo + hi), 0.5 * (hi - lo), 16)
+    z = z[[1, 6]]
+    ncol = 38
+    V = P.gaussian_block(K.n, ncol, 11)
+    B = M.to_scipy() @ V
+    dX = torch.zeros((len(z), K.n, ncol), dtype=torch.complex128, device="cuda")
+    iters, rc = G.gcie_shifted_solve(ctx, pen, z, ncol, dev(B), dX, lin_tol=1e-11, precision=0, precond=3)
+    X = host(dX)
+    assert 0 < iters <= 12
+    for s, zs in enumerate(z):
+        Xr = O.ShiftedSolver(K, M, zs).solve(B)
+        err = np.linalg.norm(X[s] - Xr, axis=0) / np.linalg.norm(Xr, axis=0)
+        assert np.max(err) < 1e-7, (sc, s, err)
+
+
 def test_shifted_solve_initial_guess_and_zero_rhs(G, ctx, small2d):
     K, M, spec, pen = small2d
     z = np.array([200 + 20j])
