@@ -12,6 +12,7 @@ each rank solves its own replica of the workload (independent problems, no colle
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import subprocess
@@ -177,6 +178,23 @@ def run_ours(args, rank, world):
     return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e)
 
 
+def traffic_per_flop():
+    """DRAM bytes per algorithmic flop of the band sweeps from the committed ncu summary, or None when
+    the kernel source has changed since that capture."""
+    rec = {}
+    try:
+        with open(os.path.join(ROOT, "profiles", "band_solve_traffic.txt")) as fh:
+            for line in fh:
+                if "=" in line and not line.startswith("#"):
+                    k, v = line.strip().split("=", 1)
+                    rec[k] = v
+        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
+            sha = hashlib.sha256(fh.read()).hexdigest()
+    except (OSError, KeyError):
+        return None
+    return float(rec["dram_bytes_per_flop"]) if sha == rec.get("sha256") else None
+
+
 def pinned(a):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
@@ -305,8 +323,10 @@ def main():
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     if dom in ("prec", "factor"):
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
+        bpf = traffic_per_flop() if dom == "prec" else None
         roof = {"kernel_class": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                "frac": achieved / alu_peak, "traffic": None,
+                "frac": achieved / alu_peak,
+                "traffic": None if bpf is None else bpf * d["flops"] / launches,
                 "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
     else:
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
