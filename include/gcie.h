@@ -161,6 +161,10 @@ int gcie_solve(gcie_ctx *ctx, const gcie_csr *K, const gcie_csr *M, double lo, d
 int gcie_solve_pencil(gcie_ctx *ctx, gcie_pencil *p, double lo, double hi, const gcie_opts *opts,
                       gcie_result *out);
 void gcie_result_free(gcie_result *r);
+/* Frees one array of a gcie_result that the caller took out of the struct (and set to NULL there,
+ * so that gcie_result_free skips it), e.g. to hand the eigenvectors to another owner without a
+ * copy.  NULL is ignored. */
+void gcie_buffer_free(void *p);
 
 /* ------------------------------------------------------------------ steps of the path
  * Device-pointer entry points for the individual steps, used by the parity tests and by

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import ctypes as C
+import weakref
 import os
 
 import numpy as np
@@ -16,7 +17,7 @@ MIXED, FP64 = 0, 1
 EXPORTED_SYMBOLS = [
     "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
-    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
@@ -93,6 +94,7 @@ def lib():
         "gcie_solve": (C.c_int, [vp, C.POINTER(Csr), C.POINTER(Csr), d, d, C.POINTER(Opts), C.POINTER(Result)]),
         "gcie_solve_pencil": (C.c_int, [vp, vp, d, d, C.POINTER(Opts), C.POINTER(Result)]),
         "gcie_result_free": (None, [C.POINTER(Result)]),
+        "gcie_buffer_free": (None, [vp]),
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
         "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_spmm_f64": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
@@ -208,11 +210,24 @@ def gcie_pencil_destroy(p):
     lib().gcie_pencil_destroy(p)
 
 
+def _take_evecs(r: Result, n: int, k: int):
+    """The eigenvectors as an n x k view of the library's buffer, no copy: the pointer is taken out
+    of the result (gcie_result_free then skips it) and freed by gcie_buffer_free when the array is
+    garbage collected."""
+    if not k:
+        return np.zeros((n, 0))
+    ptr = C.cast(r.evecs, C.c_void_p).value
+    arr = np.ctypeslib.as_array(r.evecs, (k, n))
+    r.evecs = C.POINTER(C.c_double)()
+    weakref.finalize(arr, lib().gcie_buffer_free, C.c_void_p(ptr))
+    return arr.T
+
+
 def _take_result(r: Result) -> dict:
     n, k = int(r.n), int(r.count)
     out = dict(
         evals=np.ctypeslib.as_array(r.evals, (k,)).copy() if k else np.zeros(0),
-        evecs=(np.ctypeslib.as_array(r.evecs, (k, n)).copy().T if k else np.zeros((n, 0))),
+        evecs=_take_evecs(r, n, k),
         resid=np.ctypeslib.as_array(r.resid, (k,)).copy() if k else np.zeros(0),
         contour_of=np.ctypeslib.as_array(r.contour_of, (k,)).copy() if k else np.zeros(0, np.int32),
         status=[int(r.status_per_contour[i]) for i in range(r.ncontours)] if r.status_per_contour else [],

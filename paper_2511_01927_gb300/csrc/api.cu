@@ -613,6 +613,37 @@ __global__ void k_warm_start(int64_t n, int nshift, int ncol, int q, const doubl
 }
 
 // out[j*n + i] = Z[i*q + idx[j]]  (selected columns, column-major)
+// per column of X (n x ncol, column-major): the entry of largest magnitude (first such index) made
+// positive by flipping the column's sign
+__global__ void k_sign_fix(int64_t n, double *__restrict__ X)
+{
+    double *x = X + (int64_t)blockIdx.x * n;
+    __shared__ double sb[256];
+    __shared__ long long si[256];
+    double best = -1.0;
+    long long bi = 0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double a = fabs(x[i]);
+        if (a > best) { best = a; bi = i; }
+    }
+    sb[threadIdx.x] = best;
+    si[threadIdx.x] = bi;
+    __syncthreads();
+    for (int st = blockDim.x / 2; st > 0; st >>= 1) {
+        if ((int)threadIdx.x < st) {
+            const double o = sb[threadIdx.x + st];
+            const long long oi = si[threadIdx.x + st];
+            if (o > sb[threadIdx.x] || (o == sb[threadIdx.x] && oi < si[threadIdx.x])) {
+                sb[threadIdx.x] = o;
+                si[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    if (x[si[0]] < 0.0)
+        for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = -x[i];
+}
+
 __global__ void k_gather_cols(int64_t n, int q, int k, const int *__restrict__ idx, const double *__restrict__ Z,
                               double *__restrict__ out)
 {
@@ -657,7 +688,7 @@ struct ContourState {
     std::vector<double> prev_open;   // Ritz values inside I_k still unconverged after it
     // kept pairs
     std::vector<double> kv, kr;
-    std::vector<double> kvec;   // column-major n x kept
+    std::vector<const double *> kdev;   // device copies of the kept vectors (n each, sign fixed)
 };
 
 static double dot_m(const Pencil *p, const double *x, const double *y)
@@ -707,6 +738,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     if (ctx_malloc(c, (void **)&dB0, sizeof(double) * (size_t)n * L) != cudaSuccess) { ctx_free(c, dV0); set_error("out of memory"); return GCIE_ENOMEM; }
     int rc = GCIE_OK;
     struct Guard { Ctx *c; std::vector<void *> ptrs; ~Guard() { for (void *q : ptrs) ctx_free(c, q); } } guard{c, {}};
+    Guard kept_bufs{c, {}};   // device copies of the kept eigenvectors
     guard.ptrs.push_back(dV0);
     guard.ptrs.push_back(dB0);
     GCIE_CUDA_TRY(cudaMemsetAsync(dV0, 0, sizeof(double) * (size_t)n * L, c->stream));
@@ -899,18 +931,20 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                         GCIE_CUDA_TRY(ctx_malloc(c, (void **)&didx, sizeof(int) * keep.size()));
                         guard.ptrs.push_back(didx);
                         GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dout, sizeof(double) * (size_t)n * keep.size()));
-                        guard.ptrs.push_back(dout);
+                        kept_bufs.ptrs.push_back(dout);   // lives until the result is copied out
                         GCIE_CUDA_TRY(cudaMemcpyAsync(didx, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, c->stream));
                         {
                             LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
                             k_gather_cols<<<grid_for(c, n * (int64_t)keep.size()), 256, 0, c->stream>>>(n, rank, (int)keep.size(), didx, Z, dout);
                             GCIE_CUDA_TRY(cudaGetLastError());
                         }
-                        const size_t off = s.kvec.size();
-                        s.kvec.resize(off + (size_t)n * keep.size());
-                        GCIE_CUDA_TRY(cudaMemcpyAsync(s.kvec.data() + off, dout, sizeof(double) * (size_t)n * keep.size(),
-                                                      cudaMemcpyDeviceToHost, c->stream));
-                        GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+                        {
+                            // sign rule on the device: the entry of largest magnitude made positive
+                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
+                            k_sign_fix<<<(int)keep.size(), 256, 0, c->stream>>>(n, dout);
+                            GCIE_CUDA_TRY(cudaGetLastError());
+                        }
+                        for (size_t j = 0; j < keep.size(); ++j) s.kdev.push_back(dout + j * n);
                         for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
                     }
                     s.done = true;
@@ -939,17 +973,26 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
         if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
 
     // merge and de-duplicate across contours (Algorithm 1, last step)
-    struct Pair { double v, r; int k; const double *x; };
+    struct Pair { double v, r; int k; const double *x; };   // x: device vector
     std::vector<Pair> all;
     for (int k = 0; k < nc; ++k)
-        for (size_t j = 0; j < cs[k].kv.size(); ++j) all.push_back({cs[k].kv[j], cs[k].kr[j], k, cs[k].kvec.data() + j * n});
+        for (size_t j = 0; j < cs[k].kv.size(); ++j) all.push_back({cs[k].kv[j], cs[k].kr[j], k, cs[k].kdev[j]});
+    // M inner product of two kept vectors (only for pairs with nearly equal values: rare)
+    std::vector<double> ha(n), hb(n);
+    auto dot_dev = [&](const double *a, const double *b) -> double {
+        if (cudaMemcpyAsync(ha.data(), a, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaMemcpyAsync(hb.data(), b, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess)
+            return 0.0;
+        return dot_m(p, ha.data(), hb.data());
+    };
     std::stable_sort(all.begin(), all.end(), [](const Pair &a, const Pair &b) { return a.v < b.v; });
     std::vector<Pair> kept;
     for (const Pair &pr : all) {
         bool dup = false;
         for (int t = (int)kept.size() - 1; t >= 0; --t) {
             if (std::fabs(pr.v - kept[t].v) > 1e-8 * std::max(1.0, std::fabs(pr.v))) break;
-            if (std::fabs(dot_m(p, pr.x, kept[t].x)) > 0.5) {
+            if (std::fabs(dot_dev(pr.x, kept[t].x)) > 0.5) {
                 dup = true;
                 if (pr.r < kept[t].r) kept[t] = pr;
                 break;
@@ -971,20 +1014,23 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
         set_error("result allocation failed");
         return GCIE_ENOMEM;
     }
+    // Ritz vectors are M-orthonormal by construction (Q M-orthonormal, W orthogonal) and their sign
+    // was fixed on the device; they come back straight into the result
     for (size_t j = 0; j < kept.size(); ++j) {
         res->evals[j] = kept[j].v;
         res->resid[j] = kept[j].r;
         res->contour_of[j] = kept[j].k;
-        double *dst = res->evecs + j * n;
-        const double *x = kept[j].x;
-        // Ritz vectors are M-orthonormal by construction (Q M-orthonormal, W orthogonal); only the
-        // sign is fixed here: the entry of largest magnitude is made positive
-        const double nm = 1.0;
-        int64_t im = 0;
-        for (int64_t i = 1; i < n; ++i)
-            if (std::fabs(x[i]) > std::fabs(x[im])) im = i;
-        const double sg = x[im] < 0 ? -1.0 : 1.0;
-        for (int64_t i = 0; i < n; ++i) dst[i] = sg * x[i] / nm;
+        if (cudaMemcpyAsync(res->evecs + j * n, kept[j].x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess) {
+            gcie_result_free(res);
+            set_error("eigenvector copy failed");
+            return GCIE_ECUDA;
+        }
+    }
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        gcie_result_free(res);
+        set_error("eigenvector copy failed");
+        return GCIE_ECUDA;
     }
     int worst = GCIE_OK, outer = 0;
     for (int k = 0; k < nc; ++k) {
@@ -1044,6 +1090,8 @@ int gcie_solve(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, double lo, dou
     gcie_pencil_destroy(p);
     return rc;
 }
+
+void gcie_buffer_free(void *p) { std::free(p); }
 
 void gcie_result_free(gcie_result *r)
 {
