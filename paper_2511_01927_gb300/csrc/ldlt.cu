@@ -382,12 +382,42 @@ __device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 
     *pb = make_float4(v2.x, v2.y, v3.x, v3.y);
 }
 
+// Row stride of the window: SC columns padded so that the rows a quarter warp touches in one
+// 16-byte access fall on distinct banks (8 columns: 4 rows of 32 bytes -> stride 96 bytes; 16
+// columns: 2 rows of 64 bytes -> stride 192 bytes).
+__host__ __device__ constexpr int band_window_stride(int sc) { return sc == 8 ? 12 : sc == 16 ? 24 : sc; }
+
+// The block's SB rows, the thread's four columns, into registers (zero past the block's nb rows)
+template <int YS, int H>
+__device__ __forceinline__ void load_block(Quad (&yb)[SB], const float2 *Y, int bs, int WR, int nb, int q)
+{
+    if (nb == SB && bs + SB <= WR) {                  // whole block, no wrap: fixed offsets
+        const float2 *y0 = Y + bs * YS;
+#pragma unroll
+        for (int c = 0; c < SB; ++c) {
+            yb[c].a = *reinterpret_cast<const float4 *>(y0 + c * YS + 2 * q);
+            yb[c].b = *reinterpret_cast<const float4 *>(y0 + c * YS + 2 * q + H);
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < SB; ++c) {
+            const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+            int sl = bs + c;
+            sl -= sl >= WR ? WR : 0;
+            const float2 *yrow = Y + sl * YS;
+            yb[c].a = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q) : z4;
+            yb[c].b = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q + H) : z4;
+        }
+    }
+}
+
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall,
         DbgRec *__restrict__ dbg)
 {
     constexpr int H = SC / 2;
+    constexpr int YS = band_window_stride(SC);        // window row stride (padded: no bank conflicts)
     constexpr int QT = SC / 4;                        // threads per row in the updates (four columns each)
     constexpr int RG = ST / QT;                       // row groups of the updates
     static_assert(SB * SC <= ST, "in-block solve needs SB x SC threads");
@@ -406,7 +436,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
     float2 *Y = sm2;                                  // WR x SC
-    float2 *Lbuf = Y + (size_t)WR * SC;               // 2 x LBS
+    float2 *Lbuf = Y + (size_t)WR * YS;               // 2 x LBS
     const int tid = threadIdx.x;
     const int lg = tid % SB, cg = tid / SB;           // in-block solve: row lg of the block, column cg
     const unsigned gmask = 0xffffffffu;
@@ -444,7 +474,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             const int64_t i = r0 + c;
             int sl = slot0 + c;
             if (sl >= WR) sl -= WR;
-            float2 *dst = Y + sl * SC + qq;
+            float2 *dst = Y + sl * YS + qq;
             if (i >= 0 && i < n && qq < nrc) cp_async8(dst, src + i * ncol + qq);
             else *dst = zero;
         }
@@ -462,8 +492,8 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     };
     for (int e = tid; e < (b + SB) * SC; e += ST) {
         const int t = e / SC, qq = e % SC;
-        if (t < n && qq < nrc) cp_async8(Y + e, Rs + (int64_t)t * ncol + qq);
-        else Y[e] = zero;
+        if (t < n && qq < nrc) cp_async8(Y + t * YS + qq, Rs + (int64_t)t * ncol + qq);
+        else Y[t * YS + qq] = zero;
     }
     fwd_slab(0, 0);
     cp_async_commit();
@@ -484,7 +514,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         }
         cp_async_commit();
         if (cg < SC) {
-            float2 y = lg < nb ? Y[bslot(lg) * SC + cg] : zero;
+            float2 y = lg < nb ? Y[bslot(lg) * YS + cg] : zero;
 #pragma unroll
             for (int c = 0; c < SB - 1; ++c) {
                 const float yr = __shfl_sync(gmask, y.x, c, SB), yi = __shfl_sync(gmask, y.y, c, SB);
@@ -494,27 +524,19 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
                 }
             }
             if (lg < nb) {
-                Y[bslot(lg) * SC + cg] = y;
+                Y[bslot(lg) * YS + cg] = y;
                 if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmulf(y, Lb[lg * SB + lg]);   // y / d
             }
         }
         __syncthreads();
         {
             Quad yb[SB];
-#pragma unroll
-            for (int c = 0; c < SB; ++c) {
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float2 *yrow = Y + bslot(c) * SC;
-                yb[c].a = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4) : z4;
-                yb[c].b = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4 + H) : z4;
-            }
+            load_block<YS, H>(yb, Y, bs, WR, nb, q4);
             const int rhi = (int)min((int64_t)(nb + b), n - blk);   // rows relative to blk
-            int sl = bs + nb + rg;
-            while (sl >= WR) sl -= WR;
             for (int il = nb + rg; il < rhi; il += RG) {
-                row_update<H, 1>(Lb + il * SB, Y + sl * SC, q4, yb);
-                sl += RG;
-                while (sl >= WR) sl -= WR;
+                int sl = bs + il;                     // < 2 WR
+                sl -= sl >= WR ? WR : 0;
+                row_update<H, 1>(Lb + il * SB, Y + sl * YS, q4, yb);
             }
         }
         bs += SB;
@@ -553,7 +575,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         const int64_t i = lastblk - b + t;
         int sl = bs + WR - b + t;                     // slot of row i = lastblk + (t - b)
         while (sl >= WR) sl -= WR;
-        float2 *dst = Y + sl * SC + qq;
+        float2 *dst = Y + sl * YS + qq;
         if (i >= 0 && i < n && qq < nrc) cp_async8(dst, Zs + i * ncol + qq);
         else *dst = zero;
     }
@@ -578,7 +600,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         }
         cp_async_commit();
         if (cg < SC) {
-            float2 x = lg < nb ? Y[bslot(lg) * SC + cg] : zero;
+            float2 x = lg < nb ? Y[bslot(lg) * YS + cg] : zero;
 #pragma unroll
             for (int c = SB - 1; c > 0; --c) {
                 const float xr = __shfl_sync(gmask, x.x, c, SB), xi = __shfl_sync(gmask, x.y, c, SB);
@@ -588,29 +610,21 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
                 }
             }
             if (lg < nb) {
-                Y[bslot(lg) * SC + cg] = x;
+                Y[bslot(lg) * YS + cg] = x;
                 if (cg < nrc) Zs[(blk + lg) * ncol + cg] = x;
             }
         }
         __syncthreads();
         {
             Quad xb[SB];
-#pragma unroll
-            for (int c = 0; c < SB; ++c) {
-                const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-                const float2 *yrow = Y + bslot(c) * SC;
-                xb[c].a = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4) : z4;
-                xb[c].b = c < nb ? *reinterpret_cast<const float4 *>(yrow + 2 * q4 + H) : z4;
-            }
+            load_block<YS, H>(xb, Y, bs, WR, nb, q4);
             const int kklo = (int)(max((int64_t)0, blk - b) - (blk - b));
-            // row blk - b + kk sits in slot bs + 2 SB + kk (mod WR), since WR = b + 2 SB
-            int sl = bs + 2 * SB + kklo + rg;
-            while (sl >= WR) sl -= WR;
             for (int kk = kklo + rg; kk < b; kk += RG) {
+                // row blk - b + kk sits in slot bs + 2 SB + kk (mod WR), since WR = b + 2 SB
+                int sl = bs + 2 * SB + kk;            // < 2 WR
+                sl -= sl >= WR ? WR : 0;
                 const int64_t k = blk - b + kk;        // column k: piece k / SB - kbs, position k % SB
-                row_update<H, SB>(Ls + ((int)(k / SB - kbs) * SB) * SB + (int)(k % SB), Y + sl * SC, q4, xb);
-                sl += RG;
-                while (sl >= WR) sl -= WR;
+                row_update<H, SB>(Ls + ((int)(k / SB - kbs) * SB) * SB + (int)(k % SB), Y + sl * YS, q4, xb);
             }
         }
         bs -= SB;
@@ -695,8 +709,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)NB * factor_rp(b) + (size_t)NB * factor_ws(b) + 2 * NB); }
 size_t band_smem_solve(int b, int sc)
 {
-    // window (b + 2 SB) x sc + two slabs (b + 2 SB) x SB
-    return sizeof(float2) * ((size_t)(b + 2 * SB) * sc + 2 * (size_t)SB * (b + 2 * SB));
+    // window (b + 2 SB) x (sc padded) + two slabs (b + 2 SB) x SB
+    return sizeof(float2) * ((size_t)(b + 2 * SB) * band_window_stride(sc) + 2 * (size_t)SB * (b + 2 * SB));
 }
 
 bool band_feasible(const Ctx *c, int b)
