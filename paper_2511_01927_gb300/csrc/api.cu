@@ -845,39 +845,59 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                                  o->precision, o->precond, &bands, &info);
             cocg_iters += info.iters;
             if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
-            // per contour: moments, basis, Rayleigh-Ritz, keep
+            // per contour: moments; then the basis and Rayleigh-Ritz of all the batch's contours
+            // together (their small eigensolves share launches); then the keep decisions
+            std::vector<double *> Yb(nb), Qb(nb), Qcb(nb), Zb(nb, nullptr);
+            std::vector<int> pYb(nb), rankb(nb, 0);
             for (int bi = 0; bi < nb; ++bi) {
                 ContourState &s = cs[act[b0 + bi]];
                 const int m = s.m;
                 const int pY = m * ncol;
                 if (pY > 256) { set_error("moments x columns > 256"); return GCIE_EINVAL; }
-                double *Y = nullptr, *Q = nullptr;
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Y, sizeof(double) * (size_t)n * pY));
-                guard.ptrs.push_back(Y);
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Q, sizeof(double) * (size_t)n * pY));
-                guard.ptrs.push_back(Q);
-                GCIE_CUDA_TRY(cudaMemsetAsync(Y, 0, sizeof(double) * (size_t)n * pY, c->stream));
+                pYb[bi] = pY;
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Yb[bi], sizeof(double) * (size_t)n * pY));
+                guard.ptrs.push_back(Yb[bi]);
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qb[bi], sizeof(double) * (size_t)n * pY));
+                guard.ptrs.push_back(Qb[bi]);
+                GCIE_CUDA_TRY(cudaMemsetAsync(Yb[bi], 0, sizeof(double) * (size_t)n * pY, c->stream));
                 std::vector<double2> coef((size_t)half * m);
                 for (int j = 0; j < half; ++j) {
                     double2 sn = make_double2((zw[bi][j].x - s.c) / s.r, zw[bi][j].y / s.r);
                     double2 pw = make_double2(1, 0);
                     for (int k = 0; k < m; ++k) { coef[(size_t)j * m + k] = cmul(ww[bi][j], pw); pw = cmul(pw, sn); }
                 }
-                GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Y, pY));
-                int rank = 0;
-                GCIE_TRY(m_orthonormalize(c, p, n, pY, Y, 1e-14, Q, &rank));
-                double *Qc = nullptr, *Z = nullptr;
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qc, sizeof(double) * (size_t)n * rank));
-                guard.ptrs.push_back(Qc);
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Z, sizeof(double) * (size_t)n * rank));
+                GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Yb[bi], pY));
+            }
+            GCIE_TRY(m_orthonormalize_batch(c, p, n, nb, pYb.data(), Yb.data(), 1e-14, Qb.data(), rankb.data()));
+            std::vector<std::vector<double>> thb(nb), rsb(nb);
+            std::vector<double *> thp(nb), rsp(nb);
+            for (int bi = 0; bi < nb; ++bi) {
+                const int rank = rankb[bi];
+                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qcb[bi], sizeof(double) * (size_t)n * rank));
+                guard.ptrs.push_back(Qcb[bi]);
+                if (ctx_malloc(c, (void **)&Zb[bi], sizeof(double) * (size_t)n * rank) != cudaSuccess) {
+                    for (double *z : Zb) ctx_free(c, z);
+                    set_error("out of memory");
+                    return GCIE_ENOMEM;
+                }
                 {
                     LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
-                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pY, rank, rank, Q, Qc, c->dbg);
+                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pYb[bi], rank, rank, Qb[bi], Qcb[bi], c->dbg);
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
-                std::vector<double> th(rank), rs(rank);
-                rc = rayleigh_ritz(c, p, rank, Qc, Z, th.data(), rs.data());
-                if (rc) { ctx_free(c, Z); return rc; }
+                thb[bi].resize(rank);
+                rsb[bi].resize(rank);
+                thp[bi] = thb[bi].data();
+                rsp[bi] = rsb[bi].data();
+            }
+            rc = rayleigh_ritz_batch(c, p, nb, rankb.data(), Qcb.data(), Zb.data(), thp.data(), rsp.data());
+            if (rc) { for (double *z : Zb) ctx_free(c, z); return rc; }
+            for (int bi = 0; bi < nb; ++bi) {
+                ContourState &s = cs[act[b0 + bi]];
+                const int rank = rankb[bi];
+                double *Z = Zb[bi];
+                Zb[bi] = nullptr;    // owned below (kept as the next iteration's block or freed)
+                std::vector<double> &th = thb[bi], &rs = rsb[bi];
                 bool unconverged_inside = false;
                 double worst = 0.0;
                 std::vector<int> keep;

@@ -349,17 +349,25 @@ static size_t jacobi_cl_smem(int p)
     return nd * sizeof(double) + ni * sizeof(int);
 }
 
+// up to JB matrices of different sizes per launch, one cluster each
+constexpr int JB = 16;
+struct JacobiBatch {
+    int p[JB];
+    const double *A[JB];
+    double *w[JB], *V[JB];
+};
+
 __global__ void __cluster_dims__(JCL, 1, 1) __launch_bounds__(JT)
-k_jacobi_cl(int p, const double *__restrict__ Aall, double *__restrict__ wall, double *__restrict__ Vall, double tol,
-            int maxsweep)
+k_jacobi_cl(const __grid_constant__ JacobiBatch jb, double tol, int maxsweep)
 {
     namespace cgx = cooperative_groups;
     cgx::cluster_group cl = cgx::this_cluster();
     const int rank = (int)cl.block_rank();
     const int mat = blockIdx.x / JCL;
-    const double *A = Aall + (int64_t)mat * p * p;
-    double *Vo = Vall + (int64_t)mat * p * p;
-    double *w = wall + (int64_t)mat * p;
+    const int p = jb.p[mat];
+    const double *A = jb.A[mat];
+    double *Vo = jb.V[mat];
+    double *w = jb.w[mat];
     const int pe = p + (p & 1), h = pe / 2;
     const int npl = (h + JCL - 1) / JCL, nvl = (p + JCL - 1) / JCL;
     extern __shared__ double jsm[];
@@ -531,17 +539,48 @@ k_jacobi_cl(int p, const double *__restrict__ Aall, double *__restrict__ wall, d
     cl.sync();   // no CTA leaves while others may still write into its shared memory
 }
 
+int jacobi_batch(Ctx *c, int nmat, const int *h_p, double *const *h_A, double *const *h_w, double *const *h_V)
+{
+    int pmax = 0;
+    double work = 0.0;
+    for (int i = 0; i < nmat; ++i) {
+        if (h_p[i] <= 0 || h_p[i] > JCL_MAXP) { set_error("jacobi_batch: p outside 1..256"); return GCIE_EINVAL; }
+        pmax = std::max(pmax, h_p[i]);
+        work += 24.0 * h_p[i] * h_p[i];
+    }
+    if (nmat <= 0) return GCIE_OK;
+    const size_t smem = jacobi_cl_smem(pmax);
+    if (smem > c->smem_optin) { set_error("jacobi_batch: shared memory"); return GCIE_EINVAL; }
+    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    LaunchScope ls(c, GCIE_K_DENSE, work, 0);
+    for (int i0 = 0; i0 < nmat; i0 += JB) {
+        const int cnt = std::min(JB, nmat - i0);
+        JacobiBatch jb{};
+        for (int i = 0; i < cnt; ++i) {
+            jb.p[i] = h_p[i0 + i];
+            jb.A[i] = h_A[i0 + i];
+            jb.w[i] = h_w[i0 + i];
+            jb.V[i] = h_V[i0 + i];
+        }
+        k_jacobi_cl<<<cnt * JCL, JT, smem, c->stream>>>(jb, 1e-15, 60);
+        GCIE_CUDA_TRY(cudaGetLastError());
+    }
+    return GCIE_OK;
+}
+
 int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V)
 {
     if (nmat <= 0 || p <= 0) return GCIE_OK;
     if (p > 1024) { set_error("jacobi: p > 1024"); return GCIE_EINVAL; }
     if (p <= JCL_MAXP && jacobi_cl_smem(p) <= c->smem_optin) {
-        const size_t smem = jacobi_cl_smem(p);
-        GCIE_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LaunchScope ls(c, GCIE_K_DENSE, 24.0 * nmat * p * p, 0);
-        k_jacobi_cl<<<nmat * JCL, JT, smem, c->stream>>>(p, A, w, V, 1e-15, 60);
-        GCIE_CUDA_TRY(cudaGetLastError());
-        return GCIE_OK;
+        std::vector<int> ps(nmat, p);
+        std::vector<double *> As(nmat), ws(nmat), Vs(nmat);
+        for (int i = 0; i < nmat; ++i) {
+            As[i] = A + (size_t)i * p * p;
+            ws[i] = w + (size_t)i * p;
+            Vs[i] = V + (size_t)i * p * p;
+        }
+        return jacobi_batch(c, nmat, ps.data(), As.data(), ws.data(), Vs.data());
     }
     double *wk = nullptr;
     GCIE_CUDA_TRY(ctx_malloc(c, (void **)&wk, sizeof(double) * (size_t)nmat * p * p));
@@ -683,85 +722,133 @@ __global__ void k_scale_cols(int p, int k, const double *__restrict__ U, const d
 }
 
 // One pass: Q = Y U_k diag(s_k)^-1/2 where G = Y^T M Y = U diag(s) U^T and s_i > drop * max s.
-static int orth_pass(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q, int *rank,
-                     double *work)
+// One orthonormalisation pass over a batch of bases (Y_b: n x ncol_b row-major): G_b = Y_bᵀ M Y_b,
+// all eigensolves in one launch, then Q_b = Y_b U_k diag(s_k)^-1/2 with the s_i > drop max s kept.
+// work_b: n ncol_b + 3 ncol_b² + ncol_b doubles.
+static int orth_pass_batch(Ctx *c, const Pencil *p, int64_t n, int nb, const int *ncol, const double *const *Y,
+                           double drop, double *const *Q, int *rank, double *const *work)
 {
-    double *W = work;                            // n x ncol (M Y)
-    double *G = W + (size_t)n * ncol;            // ncol^2
-    double *U = G + (size_t)ncol * ncol;         // ncol^2
-    double *s = U + (size_t)ncol * ncol;         // ncol
-    double *T = s + ncol;                        // ncol^2
-    GCIE_TRY(spmm_real(c, p, 1, ncol, Y, W));
-    GCIE_TRY(gram(c, n, ncol, Y, W, G));
-    GCIE_TRY(jacobi(c, 1, ncol, G, s, U));
-    std::vector<double> hs(ncol);
-    GCIE_CUDA_TRY(cudaMemcpyAsync(hs.data(), s, sizeof(double) * ncol, cudaMemcpyDeviceToHost, c->stream));
-    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-    const double smax = hs[ncol - 1];
-    int k = 0;
-    if (smax > 0 && std::isfinite(smax))
-        for (int i = ncol - 1; i >= 0; --i)
-            if (hs[i] > drop * smax) ++k;
-    *rank = k;
-    if (k == 0) { set_error("m_orthonormalize: basis has rank 0"); return GCIE_ENOTSPD; }
-    {
-        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * ncol * k, 0);
-        k_scale_cols<<<std::max(1, (ncol * k + 255) / 256), 256, 0, c->stream>>>(ncol, k, U, s, T, c->dbg);
-        GCIE_CUDA_TRY(cudaGetLastError());
+    std::vector<double *> G(nb), U(nb), s(nb), T(nb);
+    for (int b = 0; b < nb; ++b) {
+        const int nc = ncol[b];
+        double *W = work[b];                              // n x nc (M Y)
+        G[b] = W + (size_t)n * nc;                        // nc^2
+        U[b] = G[b] + (size_t)nc * nc;                    // nc^2
+        s[b] = U[b] + (size_t)nc * nc;                    // nc
+        T[b] = s[b] + nc;                                 // nc^2
+        GCIE_TRY(spmm_real(c, p, 1, nc, Y[b], W));
+        GCIE_TRY(gram(c, n, nc, Y[b], W, G[b]));
     }
-    GCIE_CUDA_TRY(cudaMemsetAsync(Q, 0, sizeof(double) * (size_t)n * ncol, c->stream));
-    return gemm_tall(c, n, ncol, k, Y, ncol, T, Q, ncol);
+    GCIE_TRY(jacobi_batch(c, nb, ncol, G.data(), s.data(), U.data()));
+    std::vector<std::vector<double>> hs(nb);
+    for (int b = 0; b < nb; ++b) {
+        hs[b].resize(ncol[b]);
+        GCIE_CUDA_TRY(cudaMemcpyAsync(hs[b].data(), s[b], sizeof(double) * ncol[b], cudaMemcpyDeviceToHost, c->stream));
+    }
+    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    for (int b = 0; b < nb; ++b) {
+        const int nc = ncol[b];
+        const double smax = hs[b][nc - 1];
+        int k = 0;
+        if (smax > 0 && std::isfinite(smax))
+            for (int i = nc - 1; i >= 0; --i)
+                if (hs[b][i] > drop * smax) ++k;
+        rank[b] = k;
+        if (k == 0) { set_error("m_orthonormalize: basis has rank 0"); return GCIE_ENOTSPD; }
+        {
+            LaunchScope ls(c, GCIE_K_DENSE, 16.0 * nc * k, 0);
+            k_scale_cols<<<std::max(1, (nc * k + 255) / 256), 256, 0, c->stream>>>(nc, k, U[b], s[b], T[b], c->dbg);
+            GCIE_CUDA_TRY(cudaGetLastError());
+        }
+        GCIE_CUDA_TRY(cudaMemsetAsync(Q[b], 0, sizeof(double) * (size_t)n * nc, c->stream));
+        GCIE_TRY(gemm_tall(c, n, nc, k, Y[b], nc, T[b], Q[b], nc));
+    }
+    return GCIE_OK;
+}
+
+int m_orthonormalize_batch(Ctx *c, const Pencil *p, int64_t n, int nb, const int *ncol, const double *const *Y,
+                           double drop, double *const *Q, int *rank)
+{
+    std::vector<double *> work(nb, nullptr), Q1(nb, nullptr);
+    int rc = GCIE_OK;
+    for (int b = 0; b < nb && rc == GCIE_OK; ++b) {
+        const size_t wbytes = sizeof(double) * ((size_t)n * ncol[b] + 3 * (size_t)ncol[b] * ncol[b] + ncol[b]);
+        if (ctx_malloc(c, (void **)&work[b], wbytes) != cudaSuccess ||
+            ctx_malloc(c, (void **)&Q1[b], sizeof(double) * (size_t)n * ncol[b]) != cudaSuccess) {
+            set_error("m_orthonormalize: out of memory");
+            rc = GCIE_ENOMEM;
+        }
+    }
+    std::vector<int> r1(nb, 0);
+    if (rc == GCIE_OK) rc = orth_pass_batch(c, p, n, nb, ncol, Y, drop, Q1.data(), r1.data(), work.data());
+    // second pass on the r1 valid columns (zero columns beyond r1 are dropped by the rank test)
+    if (rc == GCIE_OK) rc = orth_pass_batch(c, p, n, nb, ncol, Q1.data(), drop, Q, rank, work.data());
+    for (int b = 0; b < nb; ++b) {
+        ctx_free(c, work[b]);
+        ctx_free(c, Q1[b]);
+    }
+    return rc;
 }
 
 int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q, int *rank)
 {
-    double *work = nullptr, *Q1 = nullptr;
-    const size_t wbytes = sizeof(double) * ((size_t)n * ncol + 3 * (size_t)ncol * ncol + ncol);
-    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&work, wbytes));
-    cudaError_t e = ctx_malloc(c, (void **)&Q1, sizeof(double) * (size_t)n * ncol);
-    if (e != cudaSuccess) { ctx_free(c, work); set_error("m_orthonormalize: out of memory"); return GCIE_ENOMEM; }
-    int r1 = 0, r2 = 0;
-    int rc = orth_pass(c, p, n, ncol, Y, drop, Q1, &r1, work);
-    // second pass on the r1 valid columns (zero columns beyond r1 are dropped by the rank test)
-    if (rc == GCIE_OK) rc = orth_pass(c, p, n, ncol, Q1, drop, Q, &r2, work);
-    ctx_free(c, work);
-    ctx_free(c, Q1);
-    *rank = r2;
+    return m_orthonormalize_batch(c, p, n, 1, &ncol, &Y, drop, &Q, rank);
+}
+
+int rayleigh_ritz_batch(Ctx *c, const Pencil *p, int nb, const int *q, const double *const *Q, double *const *Z,
+                        double *const *h_theta, double *const *h_res)
+{
+    const int64_t n = p->n;
+    std::vector<double *> work(nb, nullptr), KQ(nb), MZ(nb), Kh(nb), U(nb), th(nb), r2(nb), z2(nb);
+    int rc = GCIE_OK;
+    for (int b = 0; b < nb && rc == GCIE_OK; ++b) {
+        const size_t wbytes = sizeof(double) * (2 * (size_t)n * q[b] + 2 * (size_t)q[b] * q[b] + 3 * (size_t)q[b]);
+        if (ctx_malloc(c, (void **)&work[b], wbytes) != cudaSuccess) {
+            set_error("rayleigh_ritz: out of memory");
+            rc = GCIE_ENOMEM;
+            break;
+        }
+        KQ[b] = work[b];                        // n x q, later K Z
+        MZ[b] = KQ[b] + (size_t)n * q[b];       // n x q
+        Kh[b] = MZ[b] + (size_t)n * q[b];       // q x q
+        U[b] = Kh[b] + (size_t)q[b] * q[b];     // q x q
+        th[b] = U[b] + (size_t)q[b] * q[b];     // q
+        r2[b] = th[b] + q[b];
+        z2[b] = r2[b] + q[b];
+    }
+    std::vector<std::vector<double>> hr2(nb), hz2(nb);
+    do {
+        if (rc) break;
+        for (int b = 0; b < nb && !rc; ++b) {
+            if ((rc = spmm_real(c, p, 0, q[b], Q[b], KQ[b]))) break;
+            rc = gram(c, n, q[b], Q[b], KQ[b], Kh[b]);
+        }
+        if (rc || (rc = jacobi_batch(c, nb, q, Kh.data(), th.data(), U.data()))) break;
+        for (int b = 0; b < nb && !rc; ++b) {
+            if ((rc = gemm_tall(c, n, q[b], q[b], Q[b], q[b], U[b], Z[b], q[b]))) break;
+            if ((rc = spmm_real(c, p, 0, q[b], Z[b], KQ[b]))) break;
+            if ((rc = spmm_real(c, p, 1, q[b], Z[b], MZ[b]))) break;
+            if ((rc = resid_norms(c, n, q[b], KQ[b], MZ[b], Z[b], th[b], r2[b], z2[b]))) break;
+            hr2[b].resize(q[b]);
+            hz2[b].resize(q[b]);
+            cudaMemcpyAsync(h_theta[b], th[b], sizeof(double) * q[b], cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(hr2[b].data(), r2[b], sizeof(double) * q[b], cudaMemcpyDeviceToHost, c->stream);
+            cudaMemcpyAsync(hz2[b].data(), z2[b], sizeof(double) * q[b], cudaMemcpyDeviceToHost, c->stream);
+        }
+        if (rc) break;
+        cudaError_t e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { set_error(std::string("rayleigh_ritz: ") + cudaGetErrorString(e)); rc = GCIE_ECUDA; break; }
+        for (int b = 0; b < nb; ++b)
+            for (int l = 0; l < q[b]; ++l)
+                h_res[b][l] = hz2[b][l] > 0 ? std::sqrt(hr2[b][l]) / (p->norm_k1 * std::sqrt(hz2[b][l])) : INFINITY;
+    } while (0);
+    for (int b = 0; b < nb; ++b) ctx_free(c, work[b]);
     return rc;
 }
 
 int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, double *h_theta, double *h_res)
 {
-    const int64_t n = p->n;
-    double *work = nullptr;
-    const size_t wbytes = sizeof(double) * (2 * (size_t)n * q + 2 * (size_t)q * q + 3 * (size_t)q);
-    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&work, wbytes));
-    double *KQ = work;                        // n x q, later K Z
-    double *MZ = KQ + (size_t)n * q;          // n x q
-    double *Kh = MZ + (size_t)n * q;          // q x q
-    double *U = Kh + (size_t)q * q;           // q x q
-    double *th = U + (size_t)q * q;           // q
-    double *r2 = th + q, *z2 = r2 + q;
-    int rc = GCIE_OK;
-    std::vector<double> hr2(q), hz2(q);
-    do {
-        if ((rc = spmm_real(c, p, 0, q, Q, KQ))) break;
-        if ((rc = gram(c, n, q, Q, KQ, Kh))) break;
-        if ((rc = jacobi(c, 1, q, Kh, th, U))) break;
-        if ((rc = gemm_tall(c, n, q, q, Q, q, U, Z, q))) break;
-        if ((rc = spmm_real(c, p, 0, q, Z, KQ))) break;
-        if ((rc = spmm_real(c, p, 1, q, Z, MZ))) break;
-        if ((rc = resid_norms(c, n, q, KQ, MZ, Z, th, r2, z2))) break;
-        cudaMemcpyAsync(h_theta, th, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(hr2.data(), r2, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
-        cudaMemcpyAsync(hz2.data(), z2, sizeof(double) * q, cudaMemcpyDeviceToHost, c->stream);
-        cudaError_t e = cudaStreamSynchronize(c->stream);
-        if (e != cudaSuccess) { set_error(std::string("rayleigh_ritz: ") + cudaGetErrorString(e)); rc = GCIE_ECUDA; break; }
-        for (int l = 0; l < q; ++l)
-            h_res[l] = hz2[l] > 0 ? std::sqrt(hr2[l]) / (p->norm_k1 * std::sqrt(hz2[l])) : INFINITY;
-    } while (0);
-    ctx_free(c, work);
-    return rc;
+    return rayleigh_ritz_batch(c, p, 1, &q, &Q, &Z, &h_theta, &h_res);
 }
 
 }  // namespace gcie

@@ -45,6 +45,8 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G);
 int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const double *T, double *Z, int ldZ);
 // Batched cyclic Jacobi: nmat symmetric p x p matrices (A destroyed), ascending w, V columns.
 int jacobi(Ctx *c, int nmat, int p, double *A, double *w, double *V);
+// matrices of different sizes (1..256), all solved in one launch (one thread-block cluster each)
+int jacobi_batch(Ctx *c, int nmat, const int *h_p, double *const *h_A, double *const *h_w, double *const *h_V);
 // The same for one matrix, with the workspace in a fixed device array (no allocation, p <= 256).
 int jacobi_noalloc(cudaStream_t stream, int p, double *A, double *w, double *V);
 // Column sums over rows: out[l] = sum_i (KZ_il - theta_l MZ_il)^2 and out2[l] = sum_i Z_il^2.
@@ -56,5 +58,10 @@ int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double 
                      int *rank);
 // a9-a11 for one basis: theta (host, ascending), residuals (host), Z = Q W on device (n x q).
 int rayleigh_ritz(Ctx *c, const Pencil *p, int q, const double *Q, double *Z, double *h_theta, double *h_res);
+// the same two steps over a batch of contours: their small eigensolves share one launch
+int m_orthonormalize_batch(Ctx *c, const Pencil *p, int64_t n, int nb, const int *ncol, const double *const *Y,
+                           double drop, double *const *Q, int *rank);
+int rayleigh_ritz_batch(Ctx *c, const Pencil *p, int nb, const int *q, const double *const *Q, double *const *Z,
+                        double *const *h_theta, double *const *h_res);
 
 }  // namespace gcie
