@@ -240,13 +240,15 @@ __global__ void k_refine_x(int64_t n, int ncol, int64_t rows_per_chunk, int chun
 }
 
 // r64 = b - (z M - K) x64 in FP64; r = (T)(r64 / scale_next) unless norm_only; partials of r^T r
-// (from the rounded, scaled r) and |r64|^2 (absolute).
+// (from the rounded, scaled r) and |r64|^2 (absolute).  x_zero: x64 is known to be zero (the first
+// residual of a solve without initial guess), so r64 = b without the FP64 products.
 template <typename T, int CPT>
 __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
         const double *__restrict__ kv, const double *__restrict__ mv, const double2 *__restrict__ z, int ncol,
         int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine, const int *__restrict__ rhs_of,
         const double *__restrict__ B, const double2 *__restrict__ X, const double *__restrict__ scale_next,
-        int norm_only, typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA, double *__restrict__ partB)
+        int norm_only, int x_zero, typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA,
+        double *__restrict__ partB)
 {
     using C = typename cplx<T>::t;
     const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
@@ -265,7 +267,7 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
     double pa[CPT][2] = {}, pb[CPT] = {};
     for (int64_t i = r0 + rsub; i < r1; i += rpb) {
         double am[CPT][2] = {}, ak[CPT][2] = {};
-        const int e1 = rowptr[i + 1];
+        const int e1 = x_zero ? rowptr[i] : rowptr[i + 1];
         for (int k = rowptr[i]; k < e1; ++k) {
             const int j = __ldg(col + k);
             const double a = __ldg(kv + k), b = __ldg(mv + k);
@@ -619,22 +621,22 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         k_bnorm_init<<<nshift, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, bch, d_rhs, S.partB, S);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
-    auto refine_r = [&](int nact, int norm_only) -> int {
+    auto refine_r = [&](int nact, int norm_only, int x_zero) -> int {
         LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
-                       (double)nact * p->nnz * ncol * 8.0);
+                       x_zero ? 0.0 : (double)nact * p->nnz * ncol * 8.0);
         k_refine_r<T, CPT><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
-            ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, R,
+            ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, x_zero, R,
             S.partA, S.partB);
         GCIE_CUDA_TRY(cudaGetLastError());
         return GCIE_OK;
     };
-    auto refine = [&](int nact) -> int {
+    auto refine = [&](int nact, int x_zero = 0) -> int {
         {
             LaunchScope ls(c, GCIE_K_REFINE, (double)nact * n * ncol * (2 * esz + 32), 0);
             k_refine_x<T><<<ntiles, 256, 0, c->stream>>>(n, ncol, g.rows_per_chunk, g.chunks, S.shift_refine, S.scale, D, d_X);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
-        GCIE_TRY(refine_r(nact, 0));
+        GCIE_TRY(refine_r(nact, 0, x_zero));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
             k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2);
@@ -651,14 +653,15 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         return GCIE_OK;
     };
     // first update: exact scale from a norm-only residual pass, then the scaled residual
-    rc = refine_r(nshift, 1);
+    // without an initial guess x64 = 0 (and D = 0), so the first two residuals are b itself
+    rc = refine_r(nshift, 1, !x0);
     if (rc) goto done;
     {
         LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
         k_scale_from_norm<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
-    rc = refine(nshift);
+    rc = refine(nshift, !x0);
     if (rc) goto done;
     rc = precond_beta(nshift, 1);
     if (rc) goto done;
