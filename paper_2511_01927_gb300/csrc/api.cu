@@ -2,11 +2,13 @@
 // (Algorithm 1 with the moment method and subspace iteration of Appendix A.3.3), and the
 // per-step device-pointer entry points.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "amg.cuh"
@@ -303,6 +305,7 @@ void gcie_destroy(gcie_ctx *c)
         cudaStreamSynchronize(c->stream);
         cudaMemPoolDestroy(c->pool);
     }
+    if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
 }
@@ -705,6 +708,17 @@ static double dot_m(const Pencil *p, const double *x, const double *y)
 static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts *o, gcie_result *res)
 {
     const int64_t n = p->n;
+    // GCIE_VERBOSE: wall time of each phase (the stream is drained at each mark, so it includes the
+    // phase's GPU work)
+    const bool verbose = std::getenv("GCIE_VERBOSE") != nullptr;
+    auto t_last = std::chrono::steady_clock::now();
+    auto mark = [&](const char *what) {
+        if (!verbose) return;
+        cudaStreamSynchronize(c->stream);
+        const auto t = std::chrono::steady_clock::now();
+        fprintf(stderr, "[gcie] %-28s %9.1f ms\n", what, std::chrono::duration<double, std::milli>(t - t_last).count());
+        t_last = t;
+    };
     const int N = o->nodes, L0 = o->L, half = N / 2;
     std::vector<ContourState> cs;
     if (o->ncontours > 0) {
@@ -746,6 +760,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                                     cudaMemcpyHostToDevice, c->stream));
     GCIE_TRY(spmm_real(c, p, 1, L, dV0, dB0));
     for (auto &s : cs) { s.ncol = L; s.m = o->moments; }
+    mark("setup (V0, B0)");
 
     size_t free_b = 0, total_b = 0;
     cudaMemGetInfo(&free_b, &total_b);
@@ -841,8 +856,10 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 x0 = true;
             }
             SolveInfo info;
+            mark("right-hand sides");
             int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
                                  o->precision, o->precond, &bands, &info);
+            mark("shifted solves");
             cocg_iters += info.iters;
             if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
             // per contour: moments; then the basis and Rayleigh-Ritz of all the batch's contours
@@ -868,7 +885,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Yb[bi], pY));
             }
+            mark("moments");
             GCIE_TRY(m_orthonormalize_batch(c, p, n, nb, pYb.data(), Yb.data(), 1e-14, Qb.data(), rankb.data()));
+            mark("M-orthonormal basis");
             std::vector<std::vector<double>> thb(nb), rsb(nb);
             std::vector<double *> thp(nb), rsp(nb);
             for (int bi = 0; bi < nb; ++bi) {
@@ -892,6 +911,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
             }
             rc = rayleigh_ritz_batch(c, p, nb, rankb.data(), Qcb.data(), Zb.data(), thp.data(), rsp.data());
             if (rc) { for (double *z : Zb) ctx_free(c, z); return rc; }
+            mark("Rayleigh-Ritz");
             for (int bi = 0; bi < nb; ++bi) {
                 ContourState &s = cs[act[b0 + bi]];
                 const int rank = rankb[bi];
@@ -992,6 +1012,7 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     for (auto &s : cs)
         if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
 
+    mark("keep decisions, buffers");
     // merge and de-duplicate across contours (Algorithm 1, last step)
     struct Pair { double v, r; int k; const double *x; };   // x: device vector
     std::vector<Pair> all;
@@ -1035,12 +1056,27 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
         return GCIE_ENOMEM;
     }
     // Ritz vectors are M-orthonormal by construction (Q M-orthonormal, W orthogonal) and their sign
-    // was fixed on the device; they come back straight into the result
+    // was fixed on the device.  They come back through the context's pinned staging buffer (a copy
+    // into freshly allocated pageable memory runs at a few GB/s), which host threads then copy into
+    // the result.
+    const size_t vbytes = sizeof(double) * (size_t)n * kept.size();
+    if (vbytes > c->h_stage_bytes) {
+        if (c->h_stage) cudaFreeHost(c->h_stage);
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        if (cudaMallocHost(&c->h_stage, vbytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->h_stage = nullptr;
+        } else {
+            c->h_stage_bytes = vbytes;
+        }
+    }
+    double *dst0 = c->h_stage ? (double *)c->h_stage : res->evecs;
     for (size_t j = 0; j < kept.size(); ++j) {
         res->evals[j] = kept[j].v;
         res->resid[j] = kept[j].r;
         res->contour_of[j] = kept[j].k;
-        if (cudaMemcpyAsync(res->evecs + j * n, kept[j].x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) !=
+        if (cudaMemcpyAsync(dst0 + j * n, kept[j].x, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream) !=
             cudaSuccess) {
             gcie_result_free(res);
             set_error("eigenvector copy failed");
@@ -1052,6 +1088,18 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
         set_error("eigenvector copy failed");
         return GCIE_ECUDA;
     }
+    if (c->h_stage && vbytes) {
+        const unsigned nt = std::max(1u, std::min(8u, std::thread::hardware_concurrency()));
+        const size_t chunk = (vbytes / nt + 4095) & ~(size_t)4095;
+        std::vector<std::thread> th;
+        for (unsigned t = 0; t < nt; ++t) {
+            const size_t b0 = std::min(vbytes, t * chunk), b1 = std::min(vbytes, b0 + chunk);
+            if (b1 > b0)
+                th.emplace_back([=] { std::memcpy((char *)res->evecs + b0, (const char *)c->h_stage + b0, b1 - b0); });
+        }
+        for (auto &x : th) x.join();
+    }
+    mark("merge, eigenvectors out");
     int worst = GCIE_OK, outer = 0;
     for (int k = 0; k < nc; ++k) {
         res->status_per_contour[k] = cs[k].status;

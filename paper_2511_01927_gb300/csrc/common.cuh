@@ -89,6 +89,8 @@ struct Ctx {
     size_t scratch_bytes = 0;
     DbgRec *dbg = nullptr;           // device record of the first index violation (checked builds)
     cudaMemPool_t pool = nullptr;    // stream-ordered pool of the solve-time buffers
+    void *h_stage = nullptr;         // pinned host staging for results copied out (grown on demand)
+    size_t h_stage_bytes = 0;
 };
 
 // Stream-ordered allocation from the context's pool.  The pool keeps what it has reserved between
