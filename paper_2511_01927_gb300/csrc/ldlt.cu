@@ -633,7 +633,22 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     cp_async_wait_all();
 }
 
-// partial sums of r^T z (unconjugated) per (shift, chunk, column), geometry of the COCG sweeps
+// partial sums of r^T z (unconjugated) per (shift, chunk, column), geometry of the COCG sweeps.
+// FP32 products are exact as a float pair (p = a b rounded, e = fma(a, b, -p)); the sums are kept as
+// float pairs (Knuth's two-sum), about 48 bits, so the kernel is bound by reading r and z rather
+// than by FP64 arithmetic.
+struct FF { float hi, lo; };
+__device__ __forceinline__ void ff_add_prod(FF &s, float a, float b)
+{
+    // _rn intrinsics: never contracted into FMAs, which would break the error-free steps
+    const float p = __fmul_rn(a, b);
+    const float e = fmaf(a, b, -p);
+    const float t = __fadd_rn(s.hi, p);
+    const float bb = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, __fadd_rn(err, e));
+}
 __global__ void k_rz_partials(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const int *__restrict__ mask,
                               const float2 *__restrict__ R, const float2 *__restrict__ Z, double2 *__restrict__ part)
 {
@@ -641,13 +656,18 @@ __global__ void k_rz_partials(int64_t n, int ncol, int64_t rows_per_chunk, int c
     if (!mask[s]) return;
     const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
     for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        double re = 0.0, im = 0.0;
+        FF re{0.f, 0.f}, im{0.f, 0.f};
+        const float2 *Rs = R + ((int64_t)s * n) * ncol + c, *Zs = Z + ((int64_t)s * n) * ncol + c;
+#pragma unroll 4
         for (int64_t i = r0; i < r1; ++i) {
-            const float2 r = R[((int64_t)s * n + i) * ncol + c], z = Z[((int64_t)s * n + i) * ncol + c];
-            re += (double)r.x * z.x - (double)r.y * z.y;
-            im += (double)r.x * z.y + (double)r.y * z.x;
+            const float2 r = Rs[i * ncol], z = Zs[i * ncol];
+            ff_add_prod(re, r.x, z.x);
+            ff_add_prod(re, -r.y, z.y);
+            ff_add_prod(im, r.x, z.y);
+            ff_add_prod(im, r.y, z.x);
         }
-        part[((int64_t)s * chunks + ch) * ncol + c] = make_double2(re, im);
+        part[((int64_t)s * chunks + ch) * ncol + c] =
+            make_double2((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
     }
 }
 
