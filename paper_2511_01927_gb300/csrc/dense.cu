@@ -1,6 +1,7 @@
 // Everything after the shifted solves, in FP64 on the device (steps a7-a11):
 //   moments      S_k = 2 Re sum_s w_s ((z_s - c)/r)^k X_s           (Appendix A.3.3, moment method)
-//   gram         G = Y^T W, tall-skinny (row chunks -> per-CTA partial p x p -> ordered sum)
+//   gram         G = Y^T W for a symmetric result (W = M Y or K Y): tall-skinny, row chunks -> per-CTA
+//                partial upper 8 x 8 tiles -> ordered sum, lower tiles mirrored
 //   gemm_tall    Z = Y T with a small T held in shared memory
 //   jacobi       cyclic Jacobi, round-robin (tournament) pair ordering so each round applies
 //                p/2 disjoint rotations in parallel; one 8-CTA cluster per matrix (rows spread
@@ -69,9 +70,16 @@ __global__ void k_gram_part(int64_t n, int p, int pp, int64_t rows_per_chunk, co
     extern __shared__ double sm[];
     double *sY = sm;                   // [RB][pp]
     double *sW = sm + GRAM_RB * pp;    // [RB][pp]
+    // G is symmetric (Y^T M Y, Q^T K Q): only the 8 x 8 tiles (ta, tb) with ta <= tb are formed,
+    // thread t taking the t-th of them in row order
     const int nt = pp / 8;
-    const bool valid = threadIdx.x < nt * nt;   // the block may be padded to a full warp
-    const int ta = valid ? threadIdx.x / nt : 0, tb = threadIdx.x % nt;
+    const bool valid = threadIdx.x < nt * (nt + 1) / 2;   // the block may be padded to a full warp
+    int ta = 0, tb = 0;
+    if (valid) {
+        int t = threadIdx.x;
+        while (t >= nt - ta) { t -= nt - ta; ++ta; }
+        tb = ta + t;
+    }
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
     double acc[8][8];
 #pragma unroll
@@ -115,7 +123,8 @@ __global__ void k_gram_sum(int nchunk, int p, int pp, const double *__restrict__
                            DbgRec *dbg)
 {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < p * p; e += gridDim.x * blockDim.x) {
-        const int a = e / p, b = e % p;
+        int a = e / p, b = e % p;
+        if (a / 8 > b / 8) { const int t = a; a = b; b = t; }   // lower tiles mirror the upper ones
         double s = 0.0;
         for (int cidx = 0; cidx < nchunk; ++cidx)
             if (GCHK(dbg, (int64_t)cidx * pp * pp + a * pp + b, (int64_t)nchunk * pp * pp, 311))
@@ -129,7 +138,7 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G)
     if (p <= 0) return GCIE_OK;
     if (p > 256) { set_error("gram: p > 256"); return GCIE_EINVAL; }
     const int pp = ((p + 7) / 8) * 8;
-    const int threads = (pp / 8) * (pp / 8);
+    const int threads = (pp / 8) * (pp / 8 + 1) / 2;      // upper 8 x 8 tiles of the symmetric result
     int nchunk = (int)std::min<int64_t>((int64_t)c->num_sms * (threads <= 256 ? 4 : 1), (n + 63) / 64);
     nchunk = std::max(nchunk, 1);
     const int64_t rpc = (n + nchunk - 1) / nchunk;
@@ -138,7 +147,7 @@ int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G)
     GCIE_TRY(ctx_scratch(c, sizeof(double) * (size_t)nchunk * pp * pp, (void **)&part));
     const size_t smem = sizeof(double) * 2 * GRAM_RB * pp;
     {
-        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * n * p, 2.0 * n * p * p);
+        LaunchScope ls(c, GCIE_K_DENSE, 16.0 * n * p, 1.0 * n * p * (p + 8));
         k_gram_part<<<nchunk, std::max(threads, 32), smem, c->stream>>>(n, p, pp, rpc, Y, W, part, nchunk, c->dbg);
         GCIE_CUDA_TRY(cudaGetLastError());
     }

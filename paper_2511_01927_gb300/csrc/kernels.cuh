@@ -39,7 +39,8 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
 int moments(Ctx *c, int64_t n, int nshift, const double2 *h_coef, int m, int ncol, const double2 *X, double *S,
             int ldS);
 
-// G = Y^T W (p x p), Y and W n x p row-major FP64 (p <= 256).
+// G = Y^T W (p x p), Y and W n x p row-major FP64 (p <= 256), for W = M Y or K Y (G symmetric:
+// only the upper 8 x 8 tiles are formed, the lower ones mirrored).
 int gram(Ctx *c, int64_t n, int p, const double *Y, const double *W, double *G);
 // Z = Y T, Y n x p (leading dim ldY), T p x q row-major, Z n x q (leading dim ldZ).
 int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const double *T, double *Z, int ldZ);
