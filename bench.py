@@ -178,6 +178,17 @@ def run_ours(args, rank, world):
     return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e)
 
 
+def source_digest(text):
+    """sha256 of a CUDA source with its // comments and blank lines removed, so that edits to
+    comments alone do not mark a capture as stale."""
+    lines = []
+    for line in text.splitlines():
+        code = line.split("//", 1)[0].rstrip()
+        if code.strip():
+            lines.append(code)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def traffic_per_flop():
     """DRAM bytes per algorithmic flop of the band sweeps from the committed ncu summary, or None when
     the kernel source has changed since that capture."""
@@ -188,8 +199,8 @@ def traffic_per_flop():
                 if "=" in line and not line.startswith("#"):
                     k, v = line.strip().split("=", 1)
                     rec[k] = v
-        with open(os.path.join(ROOT, rec["source"]), "rb") as fh:
-            sha = hashlib.sha256(fh.read()).hexdigest()
+        with open(os.path.join(ROOT, rec["source"])) as fh:
+            sha = source_digest(fh.read())
     except (OSError, KeyError):
         return None
     return float(rec["dram_bytes_per_flop"]) if sha == rec.get("sha256") else None

@@ -14,19 +14,19 @@
 //      t = 0..b, so column j is contiguous; assembled and updated in place by the factorization;
 //   G  (the factor, from the start of the buffer): block-column layout, block kb (columns
 //      kb SB .. kb SB + SB - 1) is a dense (b + SB) x SB array G_kb[il][c] = l_{kb SB + il, kb SB + c}
-//      (1 / d_j on the diagonal, so the sweeps never divide; zero outside the band).  The factorization writes each finished panel
-//      there; G's block kb ends before the AB columns still being factored begin, so the two share
-//      one buffer.  In this layout the forward sweep reads one contiguous block per step and the
-//      backward sweep contiguous SB x SB pieces.
+//      (1 / d_j on the diagonal, so the sweeps never divide; zero outside the band).  The
+//      factorization writes each finished panel there; G's block kb ends before the AB columns
+//      still being factored begin, so the two share one buffer.  In this layout the forward sweep
+//      reads one contiguous block per step and the backward sweep contiguous SB x SB pieces.
 //
-// Kernels (one CTA per shift for the factorization, nshift x column groups for the sweeps):
+// Kernels (a 2-CTA cluster per shift for the factorization, nshift x column groups for the sweeps):
 //   k_band_assemble  A_s from the union CSR pattern;
 //   k_band_ldlt      right-looking factorization by panels of NB columns: the panel (NB + b rows)
 //                    is factored in shared memory, then the trailing b x b triangle receives the
-//                    rank-NB update L_p D_p L_p^T (tiles of 4 x 4 per thread);
+//                    rank-NB update L_p D_p L_p^T (4-column x 128-row items shared by the cluster);
 //   k_band_solve     z = L^-T D^-1 L^-1 r for a group of right-hand sides, with a sliding window of
-//                    b + 2 SB rows in shared memory for each sweep and the factor columns of the
-//                    next block step copied in asynchronously.
+//                    b + 2 SB rows in shared memory for each sweep and the factor block of the
+//                    next block step copied in asynchronously (bulk copy forward, cp.async back).
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
