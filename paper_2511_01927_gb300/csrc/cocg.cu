@@ -796,7 +796,7 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
         } else if (to) {
             cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(to), c->stream);
             set_error("band sweep: an asynchronous copy did not complete in time");
-            rc = GCIE_ECUDA;
+            rc = GCIE_ETIMEOUT;
         }
     }
     if (rc == GCIE_OK || rc == GCIE_ENOCONV) {

@@ -29,6 +29,7 @@
 //                    next block step copied in asynchronously (bulk copy forward, cp.async back).
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 
 #include <cooperative_groups.h>
@@ -414,7 +415,7 @@ __device__ __forceinline__ void load_block(Quad (&yb)[SB], const float2 *Y, int 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
         const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall,
-        DbgRec *__restrict__ dbg)
+        DbgRec *__restrict__ dbg, int64_t stop_issue)
 {
     constexpr int H = SC / 2;
     constexpr int YS = band_window_stride(SC);        // window row stride (padded: no bank conflicts)
@@ -445,6 +446,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int64_t nblk = (n + SB - 1) / SB;
     __shared__ unsigned long long bars[2];            // completion of the bulk copies into slab buffer 0 / 1
     int uses0 = 0, uses1 = 0;                         // completed phases of each barrier
+    bool pend0 = false, pend1 = false;                // a bulk copy into the buffer is in flight
     if (tid == 0) {
         mbar_init(&bars[0]);
         mbar_init(&bars[1]);
@@ -454,15 +456,17 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     // wait for slab buffer `buf`; false (in every thread) if some thread's wait gave up
     auto slab_wait = [&](int buf) -> bool {
         const int par = (buf ? uses1 : uses0) & 1;
-        const bool ok = mbar_wait(&bars[buf], par);
-        if (buf) ++uses1; else ++uses0;
-        return !__syncthreads_or(!ok);
+        const bool ok = __syncthreads_and(mbar_wait(&bars[buf], par));
+        if (ok) {
+            if (buf) { ++uses1; pend1 = false; } else { ++uses0; pend0 = false; }
+        }
+        return ok;
     };
-    // after a failed wait: record it, let the copies still in flight land (bounded), leave
+    // after a failed wait: record it, let the bulk copies still in flight land (bounded), leave
     auto give_up = [&]() {
         if (tid == 0) atomicAdd(&dbg->wait_timeouts, 1u);
-        mbar_wait(&bars[0], uses0 & 1);
-        mbar_wait(&bars[1], uses1 & 1);
+        if (pend0) mbar_wait(&bars[0], uses0 & 1);
+        if (pend1) mbar_wait(&bars[1], uses1 & 1);
         cp_async_wait_all();
     };
 
@@ -496,6 +500,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         else Y[t * YS + qq] = zero;
     }
     fwd_slab(0, 0);
+    pend0 = true;
     cp_async_commit();
     int bs = 0;                                       // slot of row blk
     for (int64_t kb = 0; kb < nblk; ++kb) {
@@ -506,7 +511,12 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         cp_async_wait_all();
         if (!slab_wait((int)(kb & 1))) { give_up(); return; }
         // next step's slab and the rows entering the window then (slots of the previous block)
-        if (kb + 1 < nblk) fwd_slab(kb + 1, (int)((kb + 1) & 1));
+        // (stop_issue < nblk only in the test of the timeout path: the copy of block stop_issue is
+        //  never issued, so its wait runs out)
+        if (kb + 1 < nblk && kb + 1 < stop_issue) {
+            fwd_slab(kb + 1, (int)((kb + 1) & 1));
+            if ((kb + 1) & 1) pend1 = true; else pend0 = true;
+        }
         {
             int s0 = bs + b + SB;
             while (s0 >= WR) s0 -= WR;
@@ -773,12 +783,12 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
 
 template <int SC>
 static int launch_band_solve(Ctx *c, int64_t n, int b, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
-                             const float2 *R, float2 *Z)
+                             const float2 *R, float2 *Z, int64_t stop_issue)
 {
     const size_t smem = band_smem_solve(b, SC);
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     const int ngrp = (ncol + SC - 1) / SC;
-    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z, c->dbg);
+    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z, c->dbg, stop_issue);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
@@ -808,9 +818,24 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     const int ngrp = (ncol + best - 1) / best;
     const double macs = 2.0 * nact * n * b * ncol;
     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
-    if (best == 32) return launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
-    if (best == 16) return launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
-    return launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
+    // GCIE_TEST_STOP_COPY = k: test of the bounded wait: the forward sweep never issues the copy of
+    // factor block k, its wait gives up after about a second, and the call reports GCIE_ETIMEOUT
+    // (checked here, right after the launch, only in this test mode)
+    int64_t stop_issue = INT64_MAX;
+    if (const char *e = std::getenv("GCIE_TEST_STOP_COPY")) stop_issue = std::max<int64_t>(1, std::atoll(e));
+    int rc = best == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue)
+             : best == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue)
+                          : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue);
+    if (rc == GCIE_OK && stop_issue != INT64_MAX) {
+        unsigned int to = 0;
+        GCIE_CUDA_TRY(cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream));
+        GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+        if (to) {
+            set_error("band sweep: an asynchronous copy did not complete in time");
+            return GCIE_ETIMEOUT;
+        }
+    }
+    return rc;
 }
 
 int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,

@@ -147,6 +147,30 @@ def test_band_sweep_variants(G, ctx, small2d, sc, monkeypatch):
         assert np.max(err) < 1e-7, (sc, s, err)
 
 
+def test_band_sweep_wait_timeout_reports_and_recovers(G, small2d, monkeypatch):
+    """The bounded wait of the band sweeps: with the copy of one factor block never issued (test
+    switch), the waiting CTAs give up after about a second, the call returns GCIE_ETIMEOUT, and the
+    context stays usable for the next solve."""
+    K, M, spec, _ = small2d
+    ctx2 = G.gcie_create(0)
+    try:
+        pen = G.gcie_pencil_create(ctx2, K, M)
+        z = np.array([0.5 * (spec["lo"] + spec["hi"]) + 20j])
+        B = M.to_scipy() @ P.gaussian_block(K.n, 8, 3)
+        dX = torch.zeros((1, K.n, 8), dtype=torch.complex128, device="cuda")
+        monkeypatch.setenv("GCIE_TEST_STOP_COPY", "3")
+        with pytest.raises(G.GcieError) as e:
+            G.gcie_shifted_solve(ctx2, pen, z, 8, dev(B), dX, lin_tol=1e-11, precision=0, precond=3)
+        assert e.value.code == 7
+        monkeypatch.delenv("GCIE_TEST_STOP_COPY")
+        iters, rc = G.gcie_shifted_solve(ctx2, pen, z, 8, dev(B), dX, lin_tol=1e-11, precision=0, precond=3)
+        Xr = O.ShiftedSolver(K, M, z[0]).solve(B)
+        assert rc == 0 and np.max(np.abs(host(dX)[0] - Xr)) <= 1e-7 * np.max(np.abs(Xr))
+        G.gcie_pencil_destroy(pen)
+    finally:
+        G.gcie_destroy(ctx2)
+
+
 def test_shifted_solve_initial_guess_and_zero_rhs(G, ctx, small2d):
     K, M, spec, pen = small2d
     z = np.array([200 + 20j])
@@ -270,6 +294,19 @@ def test_solve_fem1d_closed_form(G, ctx, precision):
     X /= np.sqrt(np.einsum("ij,ij->j", X, M.to_scipy() @ X))
     assert len(r["evals"]) == spec["count"] == O.count_in(K, M, spec["lo"], spec["hi"])
     _check_against(r, lam, K, M, X)
+
+
+def test_solve_fem3d_q1_octants_matches_definition(G, ctx):
+    """Reduced member of the 3D Q1 octant-coefficient family (27-point stencil, n = 9^3 = 729,
+    bandwidth 91): the returned set is the definition's, eigenvalues 12..51 of the dense solve."""
+    K, M = P.fem_q1(10, 3, P.octant_coefficients(3, 4), P.octant_coefficients(3, 5))
+    lam, X = O.eigpairs_dense(K, M)
+    i0, i1 = 12, 51
+    lo, hi = 0.5 * (lam[i0 - 1] + lam[i0]), 0.5 * (lam[i1] + lam[i1 + 1])
+    V = P.gaussian_block(K.n, 32, 4)
+    r = G.gcie_solve(ctx, K, M, lo, hi, nodes=16, moments=2, nuniform=2, V0=V, tol=1e-10)
+    assert len(r["evals"]) == i1 - i0 + 1 == O.count_in(K, M, lo, hi)
+    _check_against(r, lam[i0:i1 + 1], K, M, X[:, i0:i1 + 1])
 
 
 def test_solve_fem2d_matches_oracle_ci(G, ctx, small2d):
