@@ -162,12 +162,7 @@ def run_ours(args, rank, world):
     clk = clocks.stop()
     stats = G.gcie_get_stats(ctx)
     if world > 1:
-        t = torch.tensor([ms, count], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-        tsum = t.clone()
-        torch.distributed.all_reduce(tsum, op=torch.distributed.ReduceOp.SUM)
-        ms, count = float(tmax[0]), int(tsum[1])
+        ms, count = reduce_over_ranks(ms, count, "cuda")
     resid_max = float(np.max(last["resid"])) if len(last["resid"]) else None
 
     # end to end through the public host-buffer call: CSR and V0 from pinned host memory in, the
@@ -204,6 +199,19 @@ def traffic_per_flop():
     except (OSError, KeyError):
         return None
     return float(rec["dram_bytes_per_flop"]) if sha == rec.get("sha256") else None
+
+
+def reduce_over_ranks(ms, count, device):
+    """Whole-job figures of a replicas run: the slowest rank's time and the eigenpairs of all ranks
+    (value = total count / max time)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, count], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), int(tsum[1])
 
 
 def pinned(a):
