@@ -166,6 +166,22 @@ void gcie_result_free(gcie_result *r);
  * copy.  NULL is ignored. */
 void gcie_buffer_free(void *p);
 
+/* ------------------------------------------------------------------ contours from a predicted spectrum
+ * Algorithm 2 (adaptive contour construction via KDE; Section 4.2): the range of the predictions,
+ * widened by eps = beta (max - min) on both sides, is split recursively at the minimiser of the
+ * interval sparsity function G_k(t) = sum_j exp(-w (t - lam_j)^2 / (b - a)^2) until no interval
+ * holds more than nmax predictions; intervals with fewer than nmin are then joined to their
+ * nearer neighbour (a joined interval above nmax is split between its two middle predictions).
+ * Contour k: c = (lo + hi)/2, r = (1 + alpha)(hi - lo)/2, lo/hi the interval (a prediction belongs
+ * to [lo, hi); the last interval also takes hi).  Host only, no device work.
+ *   pred: host, npred >= 1 finite predicted eigenvalues, any order (the paper's Lambda-hat).
+ *   nmin, nmax: per-contour count range (paper: 10, 50); w: gap sensitivity (paper: 10).
+ *   out, counts: host arrays of cap entries: the contours in ascending order and the number of
+ *   predictions each holds.  *nout: number of contours (also set when cap is too small).
+ * Errors: GCIE_EINVAL for bad arguments or cap < *nout (nothing written then). */
+int gcie_kde_contours(const double *pred, int32_t npred, int32_t nmin, int32_t nmax, double w, double alpha,
+                      double beta, gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout);
+
 /* ------------------------------------------------------------------ steps of the path
  * Device-pointer entry points for the individual steps, used by the parity tests and by
  * callers that drive the pipeline themselves.  Each runs the same kernels as gcie_solve. */

@@ -18,8 +18,13 @@ for Fast Large-Scale Generalized Eigensolvers"):
   subspace iteration of FEAST (Appendix A.3.3, U_{i+1} = orth(P_k U_i)) until the residual
   tolerance is met (Section 5.1 / Appendix B.2), and the merge/de-duplication across contours.
 
+* the KDE contour construction of Algorithm 2 (`kde_contours`): recursive splits of the predicted
+  spectrum's range at the minimiser of the interval sparsity function G_k (Section 4.2), then
+  the merge of intervals holding too few predicted eigenvalues.
+
 Readings of points the paper leaves open (node placement, moment scaling, residual norm, basis
-orthonormalisation, dedup rule, eigenvector sign) are stated at each function.
+orthonormalisation, dedup rule, eigenvector sign, the argmin domain and merge rule of Algorithm 2)
+are stated at each function.
 
 Notation: the paper's A, B are K (stiffness, symmetric) and M (mass, SPD) here.
 """
@@ -355,3 +360,118 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
     Zn = Z / np.sqrt(np.einsum("ij,ij->j", Z, Ms @ Z))
     return dict(evals=theta, evecs=fix_sign(Zn), resid=res, contour_of=cid,
                 outer_iters=max(iters) if iters else 0, status=status)
+
+
+# --------------------------------------------------------------------------- Algorithm 2 (KDE)
+
+KDE_GRID = 1024        # grid points of the first search for the minimiser of G_k
+KDE_GOLDEN_STEPS = 100  # golden-section steps of its refinement
+
+
+def kde_sparsity(t, pts, a: float, b: float, w: float):
+    """G_k(t) = sum_j exp(-w (t - lam_j)^2 / (b - a)^2) over the predictions lam_j in I_k = [a, b]
+    (Section 4.2, interval sparsity function)."""
+    t = np.atleast_1d(np.asarray(t, dtype=np.float64))
+    s = w / (b - a) ** 2
+    return np.exp(-s * (t[:, None] - pts[None, :]) ** 2).sum(axis=1)
+
+
+def kde_cut(pts, a: float, b: float, w: float) -> float:
+    """The split point of Algorithm 2: argmin of G_k.  Reading: the minimum is taken over the open
+    range between the interval's smallest and largest predictions (over all of I_k it would always
+    be an end point, where the kernels thin out), located by a uniform grid of KDE_GRID cell centres
+    (first minimum on ties) and refined by golden-section search between the neighbouring cell
+    centres, so the cut lies strictly between the smallest and largest prediction and both halves
+    keep at least one."""
+    lo, hi = float(pts.min()), float(pts.max())
+    h = (hi - lo) / KDE_GRID
+    grid = lo + (np.arange(KDE_GRID) + 0.5) * h
+    i = int(np.argmin(kde_sparsity(grid, pts, a, b, w)))
+    ga, gb = grid[max(i - 1, 0)], grid[min(i + 1, KDE_GRID - 1)]
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    x1, x2 = gb - g * (gb - ga), ga + g * (gb - ga)
+    f1, f2 = kde_sparsity(x1, pts, a, b, w)[0], kde_sparsity(x2, pts, a, b, w)[0]
+    for _ in range(KDE_GOLDEN_STEPS):
+        if f1 <= f2:
+            gb, x2, f2 = x2, x1, f1
+            x1 = gb - g * (gb - ga)
+            f1 = kde_sparsity(x1, pts, a, b, w)[0]
+        else:
+            ga, x1, f1 = x1, x2, f2
+            x2 = ga + g * (gb - ga)
+            f2 = kde_sparsity(x2, pts, a, b, w)[0]
+    return 0.5 * (ga + gb)
+
+
+def kde_contours(pred, nmin: int = 10, nmax: int = 50, w: float = 10.0, alpha: float = 0.0,
+                 beta: float = 0.0):
+    """Algorithm 2 (adaptive contour construction via KDE), in its order:
+
+    1. the initial range I_0 = [min - eps, max + eps], eps = beta (max - min) (Section 4.2);
+    2. pop an interval; if it holds at most nmax predictions it is final, else it is split at the
+       minimiser of G_k (`kde_cut`) and both halves are pushed;
+    3. intervals with fewer than nmin predictions are merged with their nearest neighbour, and a
+       merged interval above nmax is split again (Section 4.2, refinement loop).
+
+    Readings: a prediction belongs to [lo, hi) (the last interval also takes hi); an interval whose
+    predictions are all equal is not split.  The refinement repeatedly takes the interval with the
+    fewest predictions (leftmost on ties) while it holds fewer than nmin, and joins it to the
+    neighbour with the nearer centre (left on ties); a joined interval above nmax is split again
+    between its two middle predictions (the KDE cut would peel off the edge of a locally uniform
+    stretch and recreate the small interval).  The loop ends when no interval is below nmin, one
+    interval is left, or after 4 x (number of intervals) joins.  Contours: c = (lo + hi)/2,
+    r = (1 + alpha)(hi - lo)/2 (Section 4.2).  Returns a list of (lo, hi, c, r, count), ascending."""
+    p = np.sort(np.asarray(pred, dtype=np.float64))
+    if p.size == 0:
+        raise ValueError("no predicted eigenvalues")
+    eps = beta * (p[-1] - p[0])
+    A, B = p[0] - eps, p[-1] + eps
+
+    def members(a, b):
+        m = (p >= a) & (p < b)
+        if b == B:
+            m |= p == b
+        return p[m]
+
+    def split_all(intervals):
+        work, done = list(intervals), []
+        while work:
+            a, b = work.pop()
+            pts = members(a, b)
+            if pts.size <= nmax or pts.min() == pts.max():
+                done.append((a, b))
+                continue
+            t = kde_cut(pts, a, b, w)
+            work.append((a, t))
+            work.append((t, b))
+        return sorted(done)
+
+    final = split_all([(A, B)])
+    for _ in range(4 * len(final)):
+        if len(final) == 1:
+            break
+        counts = [members(a, b).size for a, b in final]
+        k = int(np.argmin(counts))
+        if counts[k] >= nmin:
+            break
+        if k == 0:
+            j = 1
+        elif k == len(final) - 1:
+            j = k - 1
+        else:
+            ck = 0.5 * (final[k][0] + final[k][1])
+            dl = ck - 0.5 * (final[k - 1][0] + final[k - 1][1])
+            dr = 0.5 * (final[k + 1][0] + final[k + 1][1]) - ck
+            j = k - 1 if dl <= dr else k + 1
+        lo_i, hi_i = min(k, j), max(k, j)
+        a, b = final[lo_i][0], final[hi_i][1]
+        q = members(a, b)
+        if q.size > nmax:
+            m = q.size // 2
+            t = 0.5 * (q[m - 1] + q[m])
+            new = [(a, t), (t, b)]
+        else:
+            new = [(a, b)]
+        final = final[:lo_i] + new + final[hi_i + 1:]
+    out = final
+    return [(a, b, 0.5 * (a + b), (1.0 + alpha) * 0.5 * (b - a), int(members(a, b).size)) for a, b in out]

@@ -17,7 +17,7 @@ MIXED, FP64 = 0, 1
 EXPORTED_SYMBOLS = [
     "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
-    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
@@ -96,6 +96,7 @@ def lib():
         "gcie_result_free": (None, [C.POINTER(Result)]),
         "gcie_buffer_free": (None, [vp]),
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
+        "gcie_kde_contours": (C.c_int, [vp, i32, i32, i32, d, d, d, vp, vp, i32, C.POINTER(i32)]),
         "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_spmm_f64": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_solve": (C.c_int, [vp, vp, i32, vp, i32, vp, vp, i32, d, i32, i32, i32, C.POINTER(i64)]),
@@ -261,6 +262,20 @@ def gcie_solve_pencil(ctx, pencil, lo: float, hi: float, allow_noconv: bool = Fa
 
 
 # ------------------------------------------------------------------ steps (device buffers)
+
+def gcie_kde_contours(pred, nmin: int = 10, nmax: int = 50, w: float = 10.0, alpha: float = 0.0,
+                      beta: float = 0.0) -> list:
+    """Contours from predicted eigenvalues (Algorithm 2); a list of (lo, hi, c, r, count)."""
+    p = np.ascontiguousarray(np.asarray(pred, dtype=np.float64).ravel())
+    n = C.c_int32(0)
+    cap = max(1, p.size)
+    out = (Contour * cap)()
+    counts = np.zeros(cap, dtype=np.int32)
+    _check(lib().gcie_kde_contours(p.ctypes.data, int(p.size), int(nmin), int(nmax), float(w), float(alpha),
+                                   float(beta), C.cast(out, C.c_void_p), counts.ctypes.data, cap, C.byref(n)),
+           "gcie_kde_contours")
+    return [(out[i].lo, out[i].hi, out[i].c, out[i].r, int(counts[i])) for i in range(n.value)]
+
 
 def gcie_trapezoid_nodes(c: float, r: float, N: int):
     z = np.zeros(N // 2, dtype=np.complex128)

@@ -1,0 +1,185 @@
+// Contour construction from a predicted spectrum (Algorithm 2, Section 4.2), on the host.
+//
+// The predicted eigenvalues are sorted once; an interval [a, b) of the real axis (the last one
+// also takes b) is then a contiguous range of them.  Steps, in the algorithm's order:
+//   1. the initial range I_0 = [min - eps, max + eps], eps = beta (max - min);
+//   2. an interval holding more than nmax predictions is split at the minimiser of the interval
+//      sparsity function G_k(t) = sum_j exp(-w (t - lam_j)^2 / (b - a)^2) over its predictions; the
+//      minimiser is searched strictly between its smallest and largest prediction (over all of
+//      [a, b] it would sit at an end, where the kernels thin out): the first minimum of G_k on
+//      KDE_GRID cell centres, refined by golden-section search between the neighbouring centres;
+//      an interval whose predictions are all equal is not split;
+//   3. refinement: while the interval with the fewest predictions (leftmost on ties) holds fewer
+//      than nmin and more than one interval is left, it is joined to the neighbour whose centre is
+//      nearer (left on ties); a joined interval above nmax is split between its two middle
+//      predictions; at most 4 x (number of intervals) joins;
+//   4. contour k: c = (lo + hi) / 2, r = (1 + alpha) (hi - lo) / 2.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "common.cuh"
+
+namespace gcie {
+namespace {
+
+constexpr int KDE_GRID = 1024;
+constexpr int KDE_GOLDEN_STEPS = 100;
+
+struct Spectrum {
+    std::vector<double> p;   // sorted predictions
+    double A = 0, B = 0;     // the initial range
+    // predictions of [a, b) (and b itself for the last interval) as the index range [i0, i1)
+    std::pair<size_t, size_t> range(double a, double b) const
+    {
+        const size_t i0 = std::lower_bound(p.begin(), p.end(), a) - p.begin();
+        const size_t i1 = (b == B ? std::upper_bound(p.begin(), p.end(), b) : std::lower_bound(p.begin(), p.end(), b)) -
+                          p.begin();
+        return {i0, std::max(i0, i1)};
+    }
+    size_t count(double a, double b) const
+    {
+        const auto r = range(a, b);
+        return r.second - r.first;
+    }
+};
+
+double sparsity(const Spectrum &S, size_t i0, size_t i1, double s, double t)
+{
+    double g = 0.0;
+    for (size_t j = i0; j < i1; ++j) {
+        const double d = t - S.p[j];
+        g += std::exp(-s * d * d);
+    }
+    return g;
+}
+
+double kde_cut(const Spectrum &S, size_t i0, size_t i1, double a, double b, double w)
+{
+    const double lo = S.p[i0], hi = S.p[i1 - 1];
+    const double s = w / ((b - a) * (b - a));
+    const double h = (hi - lo) / KDE_GRID;
+    int best = 0;
+    double gbest = 0.0;
+    for (int i = 0; i < KDE_GRID; ++i) {
+        const double g = sparsity(S, i0, i1, s, lo + (i + 0.5) * h);
+        if (i == 0 || g < gbest) { gbest = g; best = i; }
+    }
+    double ga = lo + (std::max(best - 1, 0) + 0.5) * h;
+    double gb = lo + (std::min(best + 1, KDE_GRID - 1) + 0.5) * h;
+    const double gr = (std::sqrt(5.0) - 1.0) / 2.0;
+    double x1 = gb - gr * (gb - ga), x2 = ga + gr * (gb - ga);
+    double f1 = sparsity(S, i0, i1, s, x1), f2 = sparsity(S, i0, i1, s, x2);
+    for (int it = 0; it < KDE_GOLDEN_STEPS; ++it) {
+        if (f1 <= f2) {
+            gb = x2; x2 = x1; f2 = f1;
+            x1 = gb - gr * (gb - ga);
+            f1 = sparsity(S, i0, i1, s, x1);
+        } else {
+            ga = x1; x1 = x2; f1 = f2;
+            x2 = ga + gr * (gb - ga);
+            f2 = sparsity(S, i0, i1, s, x2);
+        }
+    }
+    return 0.5 * (ga + gb);
+}
+
+// step 2 on a list of intervals; returns the final intervals in ascending order
+std::vector<std::pair<double, double>> split_all(const Spectrum &S, std::vector<std::pair<double, double>> work,
+                                                 int nmax, double w)
+{
+    std::vector<std::pair<double, double>> done;
+    while (!work.empty()) {
+        const auto iv = work.back();
+        work.pop_back();
+        const auto r = S.range(iv.first, iv.second);
+        const size_t nk = r.second - r.first;
+        if (nk <= (size_t)nmax || S.p[r.first] == S.p[r.second - 1]) {
+            done.push_back(iv);
+            continue;
+        }
+        const double t = kde_cut(S, r.first, r.second, iv.first, iv.second, w);
+        work.push_back({iv.first, t});
+        work.push_back({t, iv.second});
+    }
+    std::sort(done.begin(), done.end());
+    return done;
+}
+
+}  // namespace
+}  // namespace gcie
+
+extern "C" int gcie_kde_contours(const double *pred, int32_t npred, int32_t nmin, int32_t nmax, double w, double alpha,
+                                 double beta, gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout)
+{
+    using namespace gcie;
+    if (!pred || npred < 1 || !out || !counts || !nout || cap < 0) {
+        set_error("kde_contours: null pointer or no predictions");
+        return GCIE_EINVAL;
+    }
+    if (nmax < 1 || nmin < 0 || nmin > nmax || !(w > 0) || !(alpha >= 0) || !(beta >= 0) || !std::isfinite(w) ||
+        !std::isfinite(alpha) || !std::isfinite(beta)) {
+        set_error("kde_contours: need 0 <= nmin <= nmax, nmax >= 1, w > 0, alpha >= 0, beta >= 0");
+        return GCIE_EINVAL;
+    }
+    Spectrum S;
+    S.p.assign(pred, pred + npred);
+    for (double v : S.p)
+        if (!std::isfinite(v)) { set_error("kde_contours: non-finite prediction"); return GCIE_EINVAL; }
+    std::sort(S.p.begin(), S.p.end());
+    const double eps = beta * (S.p.back() - S.p.front());
+    S.A = S.p.front() - eps;
+    S.B = S.p.back() + eps;
+
+    std::vector<std::pair<double, double>> fin = split_all(S, {{S.A, S.B}}, nmax, w);
+    const size_t joins = 4 * fin.size();
+    for (size_t it = 0; it < joins && fin.size() > 1; ++it) {
+        size_t k = 0, ck = S.count(fin[0].first, fin[0].second);
+        for (size_t i = 1; i < fin.size(); ++i) {
+            const size_t c = S.count(fin[i].first, fin[i].second);
+            if (c < ck) { ck = c; k = i; }
+        }
+        if (ck >= (size_t)nmin) break;
+        size_t j;
+        if (k == 0) {
+            j = 1;
+        } else if (k == fin.size() - 1) {
+            j = k - 1;
+        } else {
+            const double cc = 0.5 * (fin[k].first + fin[k].second);
+            const double dl = cc - 0.5 * (fin[k - 1].first + fin[k - 1].second);
+            const double dr = 0.5 * (fin[k + 1].first + fin[k + 1].second) - cc;
+            j = dl <= dr ? k - 1 : k + 1;
+        }
+        const size_t lo_i = std::min(k, j), hi_i = std::max(k, j);
+        const double a = fin[lo_i].first, b = fin[hi_i].second;
+        const auto r = S.range(a, b);
+        std::vector<std::pair<double, double>> repl;
+        if (r.second - r.first > (size_t)nmax) {
+            const size_t m = (r.second - r.first) / 2;
+            const double t = 0.5 * (S.p[r.first + m - 1] + S.p[r.first + m]);
+            repl = {{a, t}, {t, b}};
+        } else {
+            repl = {{a, b}};
+        }
+        fin.erase(fin.begin() + lo_i, fin.begin() + hi_i + 1);
+        fin.insert(fin.begin() + lo_i, repl.begin(), repl.end());
+    }
+    *nout = (int32_t)fin.size();
+    if ((int32_t)fin.size() > cap) {
+        set_error("kde_contours: output capacity " + std::to_string(cap) + " < " + std::to_string(fin.size()) +
+                  " contours");
+        return GCIE_EINVAL;
+    }
+    for (size_t i = 0; i < fin.size(); ++i) {
+        const double a = fin[i].first, b = fin[i].second;
+        out[i].lo = a;
+        out[i].hi = b;
+        out[i].c = 0.5 * (a + b);
+        out[i].r = (1.0 + alpha) * 0.5 * (b - a);
+        counts[i] = (int32_t)S.count(a, b);
+    }
+    return GCIE_OK;
+}
