@@ -16,7 +16,10 @@ for Fast Large-Scale Generalized Eigensolvers"):
   node (Algorithm 1), the moment sums S_k (Appendix A.3.3, moment-based methods), orthonormal
   basis, projection, reduced GEP, Ritz recovery and "keep lambda in I_k" (Algorithm 1), the
   subspace iteration of FEAST (Appendix A.3.3, U_{i+1} = orth(P_k U_i)) until the residual
-  tolerance is met (Section 5.1 / Appendix B.2), and the merge/de-duplication across contours.
+  tolerance is met (Section 5.1 / Appendix B.2), and the merge/de-duplication across contours;
+* the count check of a contour (`trace_estimate`, `count_miss`, `resplit`): the stochastic trace
+  estimate of the enclosed eigenvalue count (Section 2, CI eigensolvers) against the Ritz count,
+  and the re-split of a contour that misses eigenvalues at a KDE cut (Algorithm 2).
 
 * the KDE contour construction of Algorithm 2 (`kde_contours`): recursive splits of the predicted
   spectrum's range at the minimiser of the interval sparsity function G_k (Section 4.2), then
@@ -303,9 +306,59 @@ def merge_dedup(theta, Z, res, cid, M, rtol: float = 1e-8):
     return theta[keep], Z[:, keep], res[keep], cid[keep]
 
 
+def trace_estimate(V: np.ndarray, S0: np.ndarray):
+    """Stochastic estimate of how many eigenvalues the contour encloses: the eigenvalue-count
+    estimate by stochastic trace estimation that the paper names among the ways CI methods place
+    contours (Section 2, CI eigensolvers).  S_0 = P V, P the quadrature's spectral filter (Eq.
+    quadrature_appendix); for V with independent N(0, 1) entries E[v^T P v] = tr P, the sum of the
+    filter over the spectrum: the enclosed count, up to the filter's leakage next to the circle.
+    Reading: one sample per column, est = mean_l v_l^T (S_0)_l, and its standard error
+    std_l / sqrt(L) from the same samples.  Returns (est, se)."""
+    per = np.einsum("il,il->l", V, S0)
+    L = per.size
+    se = float(per.std(ddof=1) / np.sqrt(L)) if L > 1 else float("inf")
+    return float(per.mean()), se
+
+
+def count_miss(est: float, se: float, theta, res, c: float, R: float, rank: int, tol: float) -> bool:
+    """Count check of a finished contour (the stochastic trace of S_0 and the Ritz count).
+    Reading: on the circle's diameter [c - R, c + R] a contour misses eigenvalues when (a) every
+    Ritz value of its basis lies there (no spare direction: the basis may be smaller than the
+    number of enclosed eigenvalues, which the subspace iteration of Appendix A.3.3 needs it to
+    exceed), or (b) the trace estimate exceeds the converged Ritz pairs there by more than
+    max(1.5, 3 se)."""
+    on = np.abs(np.asarray(theta) - c) <= R
+    found = int(np.sum(on & (np.asarray(res) <= tol)))
+    return bool(int(np.sum(on)) >= rank or est - found > max(1.5, 3.0 * se))
+
+
+def resplit(theta, c: float, R: float, s: float, e: float, w: float = 10.0):
+    """The two contours that replace one that failed the count check.  I_k = [s, e] is split at
+    the minimiser of the KDE sparsity function of its Ritz values in [s, e] (G_k and `kde_cut` of
+    Algorithm 2) searched between their lower and upper quartiles: the cut lies in a gap, and each
+    half keeps at least a quarter of them (a plain argmin peels the edge of a spectrum whose gaps
+    widen, one level per few eigenvalues).  Reading: with k sorted Ritz values the quartiles are
+    the (k // 4)-th and (k - 1 - k // 4)-th; with fewer than two distinct values between them, or a
+    cut not strictly inside (s, e), the midpoint.  Both halves keep the parent's radius-to-half-width
+    ratio (1 + alpha, Section 4.2 circle rule).  Returns two (c, R, s, e)."""
+    th = np.asarray(theta, dtype=np.float64)
+    pts = np.sort(th[(th >= s) & (th <= e)])
+    t = 0.5 * (s + e)
+    k = pts.size
+    if k >= 2:
+        q1, q3 = pts[k // 4], pts[k - 1 - k // 4]
+        if q1 < q3:
+            tc = kde_cut(pts, s, e, w, within=(q1, q3))
+            if s < tc < e:
+                t = tc
+    infl = R / (0.5 * (e - s))
+    return [(0.5 * (s + t), infl * 0.5 * (t - s), s, t), (0.5 * (t + e), infl * 0.5 * (e - t), t, e)]
+
+
 def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, nodes: int = 16,
              moments_m: int = 2, tol: float = 1e-10, max_outer: int = 10, alpha: float = 0.0,
-             contours=None, trace: dict | None = None):
+             contours=None, trace: dict | None = None, judge: bool = False, max_resplit: int = 3,
+             kde_w: float = 10.0):
     """The CI eigensolver of Algorithm 1 with the moment method and FEAST outer iterations.
 
     For each contour (c, R) enclosing I_k = [s, e]:
@@ -316,16 +369,23 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
          is <= tol;
       5. if some theta in I_k still has residual > tol: next iteration with V <- Z (all Ritz
          vectors), one moment (plain FEAST filter P_k Z), same factorizations; back to 3.
+    With `judge`, a finished contour that fails the count check (`count_miss`, on the trace
+    estimate of iteration 0's S_0) is replaced, in place, by the two halves of `resplit` (up to
+    `max_resplit` levels; at the last level it keeps its pairs and reports non-convergence).
     Then merge/dedup across contours.  V is the random block (n x L) drawn by the caller.
     `trace`, if given, receives per-contour intermediates of iteration 0 (nodes, S, Q, theta).
-    Returns dict(evals, evecs, resid, contour_of, outer_iters, status)."""
+    Returns dict(evals, evecs, resid, contour_of, outer_iters, status, contours, estimates,
+    resplits); contour_of indexes the final contours."""
     Ks, Ms = as_scipy(K), as_scipy(M)
     nK = norm1(Ks)
     if contours is None:
         contours = uniform_contours(lo, hi, ncontours, alpha)
     bw = bandwidth(Ks, Ms)
-    all_t, all_z, all_r, all_c, iters, status = [], [], [], [], [], []
-    for k, (c, R, s, e) in enumerate(contours):
+    work = [(tuple(ct), 0) for ct in contours]
+    leaves, all_t, all_z, all_r, iters, status, ests = [], [], [], [], [], [], []
+    resplits = 0
+    while work:
+        (c, R, s, e), depth = work.pop(0)
         z, w = trapezoid_nodes(c, R, nodes)
         solvers = [ShiftedSolver(Ks, Ms, zj, bw) for zj in z]
         Vk = np.asarray(V, dtype=np.float64)
@@ -335,6 +395,8 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
             B = Ms @ Vk
             X = [sv.solve(B) for sv in solvers]
             S = moments(X, z, w, c, R, m)
+            if it == 0:
+                est, se = trace_estimate(Vk, S[0])
             Y = np.concatenate(S, axis=1)
             Q = m_orthonormalize(Y, Ms)
             theta, Z = rayleigh_ritz(Ks, Ms, Q)
@@ -346,20 +408,29 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
                 ok = True
                 break
             Vk, m = Z, 1
+        if judge and count_miss(est, se, theta, res, c, R, Q.shape[1], tol):
+            if depth < max_resplit and e > s:
+                work[0:0] = [(ch, depth + 1) for ch in resplit(theta, c, R, s, e, kde_w)]
+                resplits += 1
+                continue
+            ok = False
+        leaves.append((c, R, s, e))
+        ests.append(est)
         iters.append(it + 1)
         status.append(0 if ok else 1)
         sel = inside & (res <= tol)
         all_t.append(theta[sel]); all_z.append(Z[:, sel]); all_r.append(res[sel])
-        all_c.append(np.full(int(sel.sum()), k, dtype=np.int32))
+    cid = [np.full(t.size, k, dtype=np.int32) for k, t in enumerate(all_t)]
     theta = np.concatenate(all_t)
     Z = np.concatenate(all_z, axis=1) if all_z else np.zeros((Ks.shape[0], 0))
     res = np.concatenate(all_r)
-    cid = np.concatenate(all_c)
+    cid = np.concatenate(cid)
     theta, Z, res, cid = merge_dedup(theta, Z, res, cid, Ms)
     # M-normalise and fix the sign of each returned vector
     Zn = Z / np.sqrt(np.einsum("ij,ij->j", Z, Ms @ Z))
     return dict(evals=theta, evecs=fix_sign(Zn), resid=res, contour_of=cid,
-                outer_iters=max(iters) if iters else 0, status=status)
+                outer_iters=max(iters) if iters else 0, status=status, contours=leaves,
+                estimates=np.array(ests), resplits=resplits)
 
 
 # --------------------------------------------------------------------------- Algorithm 2 (KDE)
@@ -376,14 +447,14 @@ def kde_sparsity(t, pts, a: float, b: float, w: float):
     return np.exp(-s * (t[:, None] - pts[None, :]) ** 2).sum(axis=1)
 
 
-def kde_cut(pts, a: float, b: float, w: float) -> float:
+def kde_cut(pts, a: float, b: float, w: float, within=None) -> float:
     """The split point of Algorithm 2: argmin of G_k.  Reading: the minimum is taken over the open
     range between the interval's smallest and largest predictions (over all of I_k it would always
     be an end point, where the kernels thin out), located by a uniform grid of KDE_GRID cell centres
     (first minimum on ties) and refined by golden-section search between the neighbouring cell
     centres, so the cut lies strictly between the smallest and largest prediction and both halves
-    keep at least one."""
-    lo, hi = float(pts.min()), float(pts.max())
+    keep at least one.  `within` = (lo, hi) narrows the search range (the re-split of `resplit`)."""
+    lo, hi = (float(pts.min()), float(pts.max())) if within is None else (float(within[0]), float(within[1]))
     h = (hi - lo) / KDE_GRID
     grid = lo + (np.arange(KDE_GRID) + 0.5) * h
     i = int(np.argmin(kde_sparsity(grid, pts, a, b, w)))
