@@ -89,6 +89,12 @@ typedef struct {
     int32_t profile;        /* 1: time every kernel launch with CUDA events (see gcie_stats) */
     int32_t precond;        /* GCIE_PREC_AUTO (default): banded LDL^T factors when the bandwidth
                                allows (mixed precision), else the multigrid cycle; or a GCIE_PREC_* */
+    int32_t judge;          /* 1: count check of every finished contour (see gcie_count_miss): a
+                               contour that misses eigenvalues is replaced by the two halves of
+                               gcie_resplit (w = 10) and they are solved; 0 (default): off */
+    int32_t max_resplit;    /* levels of re-splitting below an input contour, 0..16 (default 4); a
+                               contour that still fails at the last level keeps its pairs and
+                               reports GCIE_ENOCONV */
 } gcie_opts;
 
 /* Results: library-allocated host arrays, released by gcie_result_free. */
@@ -106,6 +112,11 @@ typedef struct {
     int32_t outer_iters;        /* max over contours */
     int64_t cocg_iters;         /* COCG iterations summed over solve batches */
     double norm_k1;             /* ||K||_1 used in the residual */
+    gcie_contour *contours;     /* ncontours: the final contours, each re-split one replaced in place
+                                   by its two halves (ascending when the input was) */
+    double *count_estimate;     /* ncontours: stochastic trace estimate of the enclosed eigenvalue
+                                   count (with judge = 1; NaN otherwise) */
+    int32_t resplits;           /* contours replaced by their halves */
 } gcie_result;
 
 /* Per-kernel-class accounting since the last gcie_reset_stats (profile = 1 fills times). */
@@ -181,6 +192,26 @@ void gcie_buffer_free(void *p);
  * Errors: GCIE_EINVAL for bad arguments or cap < *nout (nothing written then). */
 int gcie_kde_contours(const double *pred, int32_t npred, int32_t nmin, int32_t nmax, double w, double alpha,
                       double beta, gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout);
+
+/* Count check of a finished contour (the judge of gcie_opts).  est is the stochastic trace estimate
+ * of the number of eigenvalues the contour encloses, mean_l v_l^T (S_0)_l over the L columns of the
+ * Gaussian starting block V (Section 2, CI eigensolvers: eigenvalue counts by stochastic trace
+ * estimation; E[v^T S_0] = trace of the quadrature filter), se its standard error std_l / sqrt(L).
+ * theta, res: host, the q Ritz values and residuals of the contour's last iteration; rank: the
+ * dimension of its basis.  *miss = 1 when every Ritz value lies on the diameter [c - r, c + r]
+ * (on >= rank: the basis has no spare direction) or est exceeds the converged ones there
+ * (res <= tol) by more than max(1.5, 3 se); else 0.  Host only.  Errors: GCIE_EINVAL. */
+int gcie_count_miss(double est, double se, const double *theta, const double *res, int32_t q, double c,
+                    double r, int32_t rank, double tol, int32_t *miss);
+
+/* The two contours that replace one that failed the count check: [lo, t] and [t, hi], t the
+ * minimiser of the KDE sparsity function G_k (Algorithm 2) of the Ritz values in [lo, hi], searched
+ * between their quartiles (the (k/4)-th and (k-1-k/4)-th of k sorted) so that the cut lies in a gap
+ * and each half keeps a quarter of them; the midpoint when fewer than two distinct values lie
+ * between the quartiles or the cut is not strictly inside.  Both halves keep the parent's ratio
+ * r / ((hi - lo)/2).  theta: host, q values; out: host, 2 contours.  Host only.
+ * Errors: GCIE_EINVAL unless lo < hi, r > 0, w > 0. */
+int gcie_resplit(const double *theta, int32_t q, const gcie_contour *parent, double w, gcie_contour *out);
 
 /* ------------------------------------------------------------------ steps of the path
  * Device-pointer entry points for the individual steps, used by the parity tests and by

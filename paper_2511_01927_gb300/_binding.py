@@ -17,7 +17,7 @@ MIXED, FP64 = 0, 1
 EXPORTED_SYMBOLS = [
     "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
-    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
@@ -42,7 +42,8 @@ class Opts(C.Structure):
                 ("max_iters", C.c_int32), ("precision", C.c_int32), ("tol", C.c_double), ("lin_tol", C.c_double),
                 ("ncontours", C.c_int32), ("nuniform", C.c_int32), ("contours", C.c_void_p), ("alpha", C.c_double),
                 ("h_V0", C.c_void_p), ("seed", C.c_uint64), ("hbm_budget_bytes", C.c_size_t),
-                ("expected_count", C.c_int32), ("profile", C.c_int32), ("precond", C.c_int32)]
+                ("expected_count", C.c_int32), ("profile", C.c_int32), ("precond", C.c_int32),
+                ("judge", C.c_int32), ("max_resplit", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -50,7 +51,9 @@ class Result(C.Structure):
                 ("evecs", C.POINTER(C.c_double)), ("resid", C.POINTER(C.c_double)),
                 ("contour_of", C.POINTER(C.c_int32)), ("ncontours", C.c_int32),
                 ("status_per_contour", C.POINTER(C.c_int32)), ("iters_per_contour", C.POINTER(C.c_int32)),
-                ("outer_iters", C.c_int32), ("cocg_iters", C.c_int64), ("norm_k1", C.c_double)]
+                ("outer_iters", C.c_int32), ("cocg_iters", C.c_int64), ("norm_k1", C.c_double),
+                ("contours", C.POINTER(Contour)), ("count_estimate", C.POINTER(C.c_double)),
+                ("resplits", C.c_int32)]
 
 
 NCLASS = 8
@@ -97,6 +100,8 @@ def lib():
         "gcie_buffer_free": (None, [vp]),
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
         "gcie_kde_contours": (C.c_int, [vp, i32, i32, i32, d, d, d, vp, vp, i32, C.POINTER(i32)]),
+        "gcie_count_miss": (C.c_int, [d, d, vp, vp, i32, d, d, i32, d, C.POINTER(i32)]),
+        "gcie_resplit": (C.c_int, [vp, i32, C.POINTER(Contour), d, vp]),
         "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_spmm_f64": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
         "gcie_shifted_solve": (C.c_int, [vp, vp, i32, vp, i32, vp, vp, i32, d, i32, i32, i32, C.POINTER(i64)]),
@@ -233,7 +238,11 @@ def _take_result(r: Result) -> dict:
         contour_of=np.ctypeslib.as_array(r.contour_of, (k,)).copy() if k else np.zeros(0, np.int32),
         status=[int(r.status_per_contour[i]) for i in range(r.ncontours)] if r.status_per_contour else [],
         iters=[int(r.iters_per_contour[i]) for i in range(r.ncontours)] if r.iters_per_contour else [],
-        outer_iters=int(r.outer_iters), cocg_iters=int(r.cocg_iters), norm_k1=float(r.norm_k1))
+        outer_iters=int(r.outer_iters), cocg_iters=int(r.cocg_iters), norm_k1=float(r.norm_k1),
+        contours=[(r.contours[i].c, r.contours[i].r, r.contours[i].lo, r.contours[i].hi) for i in range(r.ncontours)]
+        if r.contours else [],
+        count_estimate=np.array([r.count_estimate[i] for i in range(r.ncontours)]) if r.count_estimate else np.zeros(0),
+        resplits=int(r.resplits))
     lib().gcie_result_free(C.byref(r))
     return out
 
@@ -275,6 +284,28 @@ def gcie_kde_contours(pred, nmin: int = 10, nmax: int = 50, w: float = 10.0, alp
                                    float(beta), C.cast(out, C.c_void_p), counts.ctypes.data, cap, C.byref(n)),
            "gcie_kde_contours")
     return [(out[i].lo, out[i].hi, out[i].c, out[i].r, int(counts[i])) for i in range(n.value)]
+
+
+def gcie_count_miss(est: float, se: float, theta, res, c: float, r: float, rank: int, tol: float) -> bool:
+    """Count check of a finished contour (trace estimate against the Ritz count)."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).ravel())
+    rs = np.ascontiguousarray(np.asarray(res, dtype=np.float64).ravel())
+    if th.size != rs.size:
+        raise ValueError("theta and res differ in length")
+    miss = C.c_int32(0)
+    _check(lib().gcie_count_miss(float(est), float(se), th.ctypes.data, rs.ctypes.data, int(th.size), float(c),
+                                 float(r), int(rank), float(tol), C.byref(miss)), "gcie_count_miss")
+    return bool(miss.value)
+
+
+def gcie_resplit(theta, c: float, r: float, lo: float, hi: float, w: float = 10.0) -> list:
+    """The two halves (c, r, lo, hi) of a contour that failed the count check."""
+    th = np.ascontiguousarray(np.asarray(theta, dtype=np.float64).ravel())
+    parent = Contour(float(c), float(r), float(lo), float(hi))
+    out = (Contour * 2)()
+    _check(lib().gcie_resplit(th.ctypes.data, int(th.size), C.byref(parent), float(w), C.cast(out, C.c_void_p)),
+           "gcie_resplit")
+    return [(o.c, o.r, o.lo, o.hi) for o in out]
 
 
 def gcie_trapezoid_nodes(c: float, r: float, N: int):

@@ -239,6 +239,8 @@ void gcie_default_opts(gcie_opts *o)
     o->seed = 1;
     o->expected_count = -1;
     o->precond = 1;
+    o->judge = 0;
+    o->max_resplit = 4;
 }
 
 int gcie_create(gcie_ctx **out, int device, void *stream)
@@ -673,6 +675,63 @@ __global__ void k_copy_cols(int64_t n, int ld, int k, int kpad, const double *__
     }
 }
 
+// Per-column sums of V .* S over the rows, one partial per block: part[b * L + l] sums
+// V[i][l] S[i][l] over the rows i this block visits (rows b*R + r, stepping by gridDim.x * R, with
+// R = blockDim.x / L rows per step, L <= blockDim.x <= 256).
+__global__ void k_trace_cols(int64_t n, int L, const double *__restrict__ V, int ldv, const double *__restrict__ S,
+                             int lds, double *__restrict__ part)
+{
+    __shared__ double sh[256];
+    const int R = (int)blockDim.x / L;
+    const int l = (int)threadIdx.x % L, r = (int)threadIdx.x / L;
+    double acc = 0.0;
+    if (r < R)
+        for (int64_t i = (int64_t)blockIdx.x * R + r; i < n; i += (int64_t)gridDim.x * R)
+            acc += V[i * ldv + l] * S[i * lds + l];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    if ((int)threadIdx.x < L) {
+        double t = 0.0;
+        for (int q = 0; q < R; ++q) t += sh[q * L + threadIdx.x];
+        part[(int64_t)blockIdx.x * L + threadIdx.x] = t;
+    }
+}
+
+// Stochastic trace estimate of the enclosed eigenvalue count from the starting block V (n x ldv,
+// Gaussian columns 0..L0-1) and S_0 (the first columns of S, row stride lds): the mean over the
+// columns of v_l^T (S_0)_l and its standard error std_l / sqrt(L0)
+static int trace_estimate(Ctx *c, int64_t n, int L0, const double *V, int ldv, const double *S, int lds, double *est,
+                          double *se)
+{
+    if (L0 < 1 || L0 > 256 || L0 > ldv || L0 > lds) { set_error("trace estimate: bad column count"); return GCIE_EINVAL; }
+    const int R = 256 / L0;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + R - 1) / R, (int64_t)c->num_sms * 2));
+    double *part = nullptr;
+    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&part, sizeof(double) * (size_t)blocks * L0));
+    std::vector<double> h((size_t)blocks * L0);
+    cudaError_t e;
+    {
+        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * L0, 2.0 * n * L0);
+        k_trace_cols<<<blocks, 256, 0, c->stream>>>(n, L0, V, ldv, S, lds, part);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), part, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    ctx_free(c, part);
+    if (e != cudaSuccess) { set_error(std::string("trace estimate: ") + cudaGetErrorString(e)); return GCIE_ECUDA; }
+    std::vector<double> per(L0, 0.0);
+    for (int b = 0; b < blocks; ++b)
+        for (int l = 0; l < L0; ++l) per[l] += h[(size_t)b * L0 + l];
+    double mean = 0.0;
+    for (double v : per) mean += v;
+    mean /= L0;
+    double var = 0.0;
+    for (double v : per) var += (v - mean) * (v - mean);
+    *est = mean;
+    *se = L0 > 1 ? std::sqrt(var / (L0 - 1) / L0) : INFINITY;
+    return GCIE_OK;
+}
+
 static int grid_for(const Ctx *c, int64_t total) { return (int)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)c->num_sms * 32)); }
 
 struct ContourState {
@@ -692,6 +751,13 @@ struct ContourState {
     // kept pairs
     std::vector<double> kv, kr;
     std::vector<const double *> kdev;   // device copies of the kept vectors (n each, sign fixed)
+    // count check
+    double est = NAN, se = NAN;       // trace estimate of the enclosed count (iteration 0)
+    std::vector<double> th_last, rs_last;   // Ritz values and residuals of the last iteration
+    int rank_last = 0;
+    int depth = 0;                    // re-split level below the input contour
+    bool judged = false, split = false;
+    int child[2] = {-1, -1};
 };
 
 static double dot_m(const Pencil *p, const double *x, const double *y)
@@ -770,254 +836,312 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     int64_t cocg_iters = 0;
     BandCache bands;   // band factors of the nodes, reused by the later FEAST iterations
 
-    for (int it = 0; it < o->max_outer; ++it) {
-        std::vector<int> act;
-        for (int k = 0; k < nc; ++k)
-            if (!cs[k].done) act.push_back(k);
-        if (act.empty()) break;
-        // batches of contours that fit the memory budget
-        size_t b0 = 0;
-        while (b0 < act.size()) {
-            int ncol = 0;
-            size_t b1 = b0;
-            while (b1 < act.size()) {
-                int nn = std::max(ncol, cs[act[b1]].ncol);
-                nn += nn & 1;
-                // per contour: COCG blocks (7 with a preconditioner), the FP64 iterate, moments and
-                // basis blocks, and FP32 band factors of its nodes
-                const bool band = o->precision == GCIE_MIXED && o->precond != GCIE_PREC_NONE &&
-                                  o->precond != GCIE_PREC_AMG && band_feasible(c, p->bw);
-                const size_t per = (size_t)half * n * nn * (7 * esz + 16) + (size_t)n * nn * 8 * 4 +
-                                   (band ? (size_t)half * band_elems(n, p->bw) * 8 : 0);
-                if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
-                ncol = nn;
-                ++b1;
-            }
-            const int nb = (int)(b1 - b0);
-            const int nshift = nb * half;
-            std::vector<double> hz(2 * (size_t)nshift);
-            std::vector<int> rhs_of(nshift);
-            std::vector<std::vector<double2>> zw(nb), ww(nb);
-            for (int bi = 0; bi < nb; ++bi) {
-                ContourState &s = cs[act[b0 + bi]];
-                trapezoid(s.c, s.r, N, zw[bi], ww[bi]);
-                for (int j = 0; j < half; ++j) {
-                    hz[2 * (bi * half + j)] = zw[bi][j].x;
-                    hz[2 * (bi * half + j) + 1] = zw[bi][j].y;
-                    rhs_of[bi * half + j] = it == 0 ? 0 : bi;
+    int resplits = 0;
+    for (;;) {   // passes: the contours of the input, then the halves of those that fail the count check
+        for (int it = 0; it < o->max_outer; ++it) {
+            std::vector<int> act;
+            for (int k = 0; k < (int)cs.size(); ++k)
+                if (!cs[k].done) act.push_back(k);
+            if (act.empty()) break;
+            // batches of contours that fit the memory budget
+            size_t b0 = 0;
+            while (b0 < act.size()) {
+                int ncol = 0;
+                size_t b1 = b0;
+                while (b1 < act.size()) {
+                    int nn = std::max(ncol, cs[act[b1]].ncol);
+                    nn += nn & 1;
+                    // per contour: COCG blocks (7 with a preconditioner), the FP64 iterate, moments and
+                    // basis blocks, and FP32 band factors of its nodes
+                    const bool band = o->precision == GCIE_MIXED && o->precond != GCIE_PREC_NONE &&
+                                      o->precond != GCIE_PREC_AMG && band_feasible(c, p->bw);
+                    const size_t per = (size_t)half * n * nn * (7 * esz + 16) + (size_t)n * nn * 8 * 4 +
+                                       (band ? (size_t)half * band_elems(n, p->bw) * 8 : 0);
+                    if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
+                    ncol = nn;
+                    ++b1;
                 }
-            }
-            // right-hand sides
-            double *dB = dB0;
-            int nrhs = 1;
-            double *dBb = nullptr;
-            double2 *dX = nullptr;
-            if (ctx_malloc(c, (void **)&dX, sizeof(double2) * (size_t)nshift * n * ncol) != cudaSuccess) {
-                cudaGetLastError();
-                set_error("solution block allocation failed");
-                return GCIE_ENOMEM;
-            }
-            guard.ptrs.push_back(dX);
-            bool x0 = false;
-            if (it > 0) {
-                nrhs = nb;
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dBb, sizeof(double) * (size_t)nb * n * ncol));
-                guard.ptrs.push_back(dBb);
-                double *tmp = nullptr;
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&tmp, sizeof(double) * (size_t)n * ncol));
-                guard.ptrs.push_back(tmp);
+                const int nb = (int)(b1 - b0);
+                const int nshift = nb * half;
+                std::vector<double> hz(2 * (size_t)nshift);
+                std::vector<int> rhs_of(nshift);
+                std::vector<std::vector<double2>> zw(nb), ww(nb);
                 for (int bi = 0; bi < nb; ++bi) {
                     ContourState &s = cs[act[b0 + bi]];
-                    {
-                        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * ncol, 0);
-                        k_copy_cols<<<grid_for(c, n * ncol), 256, 0, c->stream>>>(n, s.q, s.q, ncol, s.Z, tmp, c->dbg);
-                        GCIE_CUDA_TRY(cudaGetLastError());
-                    }
-                    GCIE_TRY(spmm_real(c, p, 1, ncol, tmp, dBb + (size_t)bi * n * ncol));
-                    // warm start from the Ritz pairs
-                    std::vector<double2> coef((size_t)half * ncol, make_double2(0, 0));
-                    for (int j = 0; j < half; ++j)
-                        for (int l = 0; l < s.q; ++l) {
-                            double2 d = make_double2(zw[bi][j].x - s.theta[l], zw[bi][j].y);
-                            coef[(size_t)j * ncol + l] = cdiv(make_double2(1, 0), d);
-                        }
-                    double2 *dcoef = nullptr;
-                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dcoef, sizeof(double2) * coef.size()));
-                    guard.ptrs.push_back(dcoef);
-                    GCIE_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, c->stream));
-                    {
-                        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * half * n * ncol, 0);
-                        k_warm_start<<<grid_for(c, (int64_t)half * n * ncol), 256, 0, c->stream>>>(
-                            n, half, ncol, s.q, s.Z, dcoef, dX + (size_t)bi * half * n * ncol);
-                        GCIE_CUDA_TRY(cudaGetLastError());
+                    trapezoid(s.c, s.r, N, zw[bi], ww[bi]);
+                    for (int j = 0; j < half; ++j) {
+                        hz[2 * (bi * half + j)] = zw[bi][j].x;
+                        hz[2 * (bi * half + j) + 1] = zw[bi][j].y;
+                        rhs_of[bi * half + j] = it == 0 ? 0 : bi;
                     }
                 }
-                dB = dBb;
-                x0 = true;
-            }
-            SolveInfo info;
-            mark("right-hand sides");
-            int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
-                                 o->precision, o->precond, &bands, &info);
-            mark("shifted solves");
-            cocg_iters += info.iters;
-            if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
-            // per contour: moments; then the basis and Rayleigh-Ritz of all the batch's contours
-            // together (their small eigensolves share launches); then the keep decisions
-            std::vector<double *> Yb(nb), Qb(nb), Qcb(nb), Zb(nb, nullptr);
-            std::vector<int> pYb(nb), rankb(nb, 0);
-            for (int bi = 0; bi < nb; ++bi) {
-                ContourState &s = cs[act[b0 + bi]];
-                const int m = s.m;
-                const int pY = m * ncol;
-                if (pY > 256) { set_error("moments x columns > 256"); return GCIE_EINVAL; }
-                pYb[bi] = pY;
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Yb[bi], sizeof(double) * (size_t)n * pY));
-                guard.ptrs.push_back(Yb[bi]);
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qb[bi], sizeof(double) * (size_t)n * pY));
-                guard.ptrs.push_back(Qb[bi]);
-                GCIE_CUDA_TRY(cudaMemsetAsync(Yb[bi], 0, sizeof(double) * (size_t)n * pY, c->stream));
-                std::vector<double2> coef((size_t)half * m);
-                for (int j = 0; j < half; ++j) {
-                    double2 sn = make_double2((zw[bi][j].x - s.c) / s.r, zw[bi][j].y / s.r);
-                    double2 pw = make_double2(1, 0);
-                    for (int k = 0; k < m; ++k) { coef[(size_t)j * m + k] = cmul(ww[bi][j], pw); pw = cmul(pw, sn); }
-                }
-                GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Yb[bi], pY));
-            }
-            mark("moments");
-            GCIE_TRY(m_orthonormalize_batch(c, p, n, nb, pYb.data(), Yb.data(), 1e-14, Qb.data(), rankb.data()));
-            mark("M-orthonormal basis");
-            std::vector<std::vector<double>> thb(nb), rsb(nb);
-            std::vector<double *> thp(nb), rsp(nb);
-            for (int bi = 0; bi < nb; ++bi) {
-                const int rank = rankb[bi];
-                GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qcb[bi], sizeof(double) * (size_t)n * rank));
-                guard.ptrs.push_back(Qcb[bi]);
-                if (ctx_malloc(c, (void **)&Zb[bi], sizeof(double) * (size_t)n * rank) != cudaSuccess) {
-                    for (double *z : Zb) ctx_free(c, z);
-                    set_error("out of memory");
+                // right-hand sides
+                double *dB = dB0;
+                int nrhs = 1;
+                double *dBb = nullptr;
+                double2 *dX = nullptr;
+                if (ctx_malloc(c, (void **)&dX, sizeof(double2) * (size_t)nshift * n * ncol) != cudaSuccess) {
+                    cudaGetLastError();
+                    set_error("solution block allocation failed");
                     return GCIE_ENOMEM;
                 }
-                {
-                    LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
-                    k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pYb[bi], rank, rank, Qb[bi], Qcb[bi], c->dbg);
-                    GCIE_CUDA_TRY(cudaGetLastError());
-                }
-                thb[bi].resize(rank);
-                rsb[bi].resize(rank);
-                thp[bi] = thb[bi].data();
-                rsp[bi] = rsb[bi].data();
-            }
-            rc = rayleigh_ritz_batch(c, p, nb, rankb.data(), Qcb.data(), Zb.data(), thp.data(), rsp.data());
-            if (rc) { for (double *z : Zb) ctx_free(c, z); return rc; }
-            mark("Rayleigh-Ritz");
-            for (int bi = 0; bi < nb; ++bi) {
-                ContourState &s = cs[act[b0 + bi]];
-                const int rank = rankb[bi];
-                double *Z = Zb[bi];
-                Zb[bi] = nullptr;    // owned below (kept as the next iteration's block or freed)
-                std::vector<double> &th = thb[bi], &rs = rsb[bi];
-                bool unconverged_inside = false;
-                double worst = 0.0;
-                std::vector<int> keep;
-                std::vector<double> open;
-                // an unconverged value counts as a wanderer when its residual is at the solve-noise
-                // level (> 1e-6) and no unconverged value of the previous iteration lies next to it
-                bool all_wander = true;
-                for (int l = 0; l < rank; ++l) {
-                    const bool inside = th[l] >= s.lo && th[l] <= s.hi;
-                    if (!inside) continue;
-                    if (rs[l] <= o->tol) { keep.push_back(l); continue; }
-                    unconverged_inside = true;
-                    worst = std::max(worst, rs[l]);
-                    open.push_back(th[l]);
-                    bool near = false;
-                    for (double tp : s.prev_open) near = near || std::fabs(th[l] - tp) <= 1e-4 * std::max(1.0, std::fabs(th[l]));
-                    if (rs[l] <= 1e-6 || near) all_wander = false;
-                }
-                // An iteration that adds no converged pair and does not improve the worst remaining
-                // residual 10x leaves only Ritz values that do not converge: spurious ones, built from
-                // basis directions dominated by solve noise, which move from one iteration to the next.
-                // The contour stops; remaining residuals above 1e-6 are taken as spurious (status OK),
-                // lower ones as a stalled eigenpair (GCIE_ENOCONV).
-                // The same holds as soon as every unconverged value is a wanderer: a true eigenpair
-                // keeps its Ritz value in place from one iteration to the next.
-                bool stalled = false;
-                if (unconverged_inside && it > 0 && (int)keep.size() <= s.prev_conv && worst >= 0.1 * s.prev_worst)
-                    stalled = true;
-                if (unconverged_inside && it > 0 && all_wander) stalled = true;
-                s.prev_conv = (int)keep.size();
-                s.prev_worst = worst;
-                s.prev_open = open;
-                s.iters = it + 1;
-                const bool last = (it + 1 == o->max_outer);
-                if (std::getenv("GCIE_VERBOSE")) {
-                    int nin = 0;
-                    double worst = 0.0, wth = 0.0;
-                    for (int l = 0; l < rank; ++l)
-                        if (th[l] >= s.lo && th[l] <= s.hi) {
-                            ++nin;
-                            if (rs[l] > worst) { worst = rs[l]; wth = th[l]; }
-                        }
-                    fprintf(stderr, "[gcie] contour %d it %d: rank %d, %d Ritz values inside [%.6g, %.6g], %zu converged, "
-                            "worst residual %.3e at %.10g\n", act[b0 + bi], it, rank, nin, s.lo, s.hi, keep.size(), worst, wth);
-                }
-                if (!unconverged_inside || last || stalled) {
-                    // final: keep converged pairs
-                    if (!keep.empty()) {
-                        int *didx = nullptr;
-                        double *dout = nullptr;
-                        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&didx, sizeof(int) * keep.size()));
-                        guard.ptrs.push_back(didx);
-                        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dout, sizeof(double) * (size_t)n * keep.size()));
-                        kept_bufs.ptrs.push_back(dout);   // lives until the result is copied out
-                        GCIE_CUDA_TRY(cudaMemcpyAsync(didx, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, c->stream));
+                guard.ptrs.push_back(dX);
+                bool x0 = false;
+                if (it > 0) {
+                    nrhs = nb;
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dBb, sizeof(double) * (size_t)nb * n * ncol));
+                    guard.ptrs.push_back(dBb);
+                    double *tmp = nullptr;
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&tmp, sizeof(double) * (size_t)n * ncol));
+                    guard.ptrs.push_back(tmp);
+                    for (int bi = 0; bi < nb; ++bi) {
+                        ContourState &s = cs[act[b0 + bi]];
                         {
-                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
-                            k_gather_cols<<<grid_for(c, n * (int64_t)keep.size()), 256, 0, c->stream>>>(n, rank, (int)keep.size(), didx, Z, dout);
+                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * ncol, 0);
+                            k_copy_cols<<<grid_for(c, n * ncol), 256, 0, c->stream>>>(n, s.q, s.q, ncol, s.Z, tmp, c->dbg);
                             GCIE_CUDA_TRY(cudaGetLastError());
                         }
+                        GCIE_TRY(spmm_real(c, p, 1, ncol, tmp, dBb + (size_t)bi * n * ncol));
+                        // warm start from the Ritz pairs
+                        std::vector<double2> coef((size_t)half * ncol, make_double2(0, 0));
+                        for (int j = 0; j < half; ++j)
+                            for (int l = 0; l < s.q; ++l) {
+                                double2 d = make_double2(zw[bi][j].x - s.theta[l], zw[bi][j].y);
+                                coef[(size_t)j * ncol + l] = cdiv(make_double2(1, 0), d);
+                            }
+                        double2 *dcoef = nullptr;
+                        GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dcoef, sizeof(double2) * coef.size()));
+                        guard.ptrs.push_back(dcoef);
+                        GCIE_CUDA_TRY(cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, c->stream));
                         {
-                            // sign rule on the device: the entry of largest magnitude made positive
-                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
-                            k_sign_fix<<<(int)keep.size(), 256, 0, c->stream>>>(n, dout);
+                            LaunchScope ls(c, GCIE_K_OTHER, 16.0 * half * n * ncol, 0);
+                            k_warm_start<<<grid_for(c, (int64_t)half * n * ncol), 256, 0, c->stream>>>(
+                                n, half, ncol, s.q, s.Z, dcoef, dX + (size_t)bi * half * n * ncol);
                             GCIE_CUDA_TRY(cudaGetLastError());
                         }
-                        for (size_t j = 0; j < keep.size(); ++j) s.kdev.push_back(dout + j * n);
-                        for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
                     }
-                    s.done = true;
-                    s.status = (unconverged_inside && !(stalled && worst > 1e-6)) ? GCIE_ENOCONV : GCIE_OK;
-                    ctx_free(c, Z);
-                    if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
-                } else {
-                    // FEAST: next iteration filters all Ritz vectors, one moment
-                    if (s.Z) ctx_free(c, s.Z);
-                    s.Z = Z;
-                    s.q = rank;
-                    s.theta = th;
-                    s.ncol = rank;
-                    s.m = 1;
+                    dB = dBb;
+                    x0 = true;
                 }
+                SolveInfo info;
+                mark("right-hand sides");
+                int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
+                                     o->precision, o->precond, &bands, &info);
+                mark("shifted solves");
+                cocg_iters += info.iters;
+                if (src != GCIE_OK && src != GCIE_ENOCONV) return src;
+                // per contour: moments; then the basis and Rayleigh-Ritz of all the batch's contours
+                // together (their small eigensolves share launches); then the keep decisions
+                std::vector<double *> Yb(nb), Qb(nb), Qcb(nb), Zb(nb, nullptr);
+                std::vector<int> pYb(nb), rankb(nb, 0);
+                for (int bi = 0; bi < nb; ++bi) {
+                    ContourState &s = cs[act[b0 + bi]];
+                    const int m = s.m;
+                    const int pY = m * ncol;
+                    if (pY > 256) { set_error("moments x columns > 256"); return GCIE_EINVAL; }
+                    pYb[bi] = pY;
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Yb[bi], sizeof(double) * (size_t)n * pY));
+                    guard.ptrs.push_back(Yb[bi]);
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qb[bi], sizeof(double) * (size_t)n * pY));
+                    guard.ptrs.push_back(Qb[bi]);
+                    GCIE_CUDA_TRY(cudaMemsetAsync(Yb[bi], 0, sizeof(double) * (size_t)n * pY, c->stream));
+                    std::vector<double2> coef((size_t)half * m);
+                    for (int j = 0; j < half; ++j) {
+                        double2 sn = make_double2((zw[bi][j].x - s.c) / s.r, zw[bi][j].y / s.r);
+                        double2 pw = make_double2(1, 0);
+                        for (int k = 0; k < m; ++k) { coef[(size_t)j * m + k] = cmul(ww[bi][j], pw); pw = cmul(pw, sn); }
+                    }
+                    GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Yb[bi], pY));
+                    if (o->judge && it == 0) GCIE_TRY(trace_estimate(c, n, L0, dV0, L, Yb[bi], pY, &s.est, &s.se));
+                }
+                mark("moments");
+                GCIE_TRY(m_orthonormalize_batch(c, p, n, nb, pYb.data(), Yb.data(), 1e-14, Qb.data(), rankb.data()));
+                mark("M-orthonormal basis");
+                std::vector<std::vector<double>> thb(nb), rsb(nb);
+                std::vector<double *> thp(nb), rsp(nb);
+                for (int bi = 0; bi < nb; ++bi) {
+                    const int rank = rankb[bi];
+                    GCIE_CUDA_TRY(ctx_malloc(c, (void **)&Qcb[bi], sizeof(double) * (size_t)n * rank));
+                    guard.ptrs.push_back(Qcb[bi]);
+                    if (ctx_malloc(c, (void **)&Zb[bi], sizeof(double) * (size_t)n * rank) != cudaSuccess) {
+                        for (double *z : Zb) ctx_free(c, z);
+                        set_error("out of memory");
+                        return GCIE_ENOMEM;
+                    }
+                    {
+                        LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * rank, 0);
+                        k_copy_cols<<<grid_for(c, n * rank), 256, 0, c->stream>>>(n, pYb[bi], rank, rank, Qb[bi], Qcb[bi], c->dbg);
+                        GCIE_CUDA_TRY(cudaGetLastError());
+                    }
+                    thb[bi].resize(rank);
+                    rsb[bi].resize(rank);
+                    thp[bi] = thb[bi].data();
+                    rsp[bi] = rsb[bi].data();
+                }
+                rc = rayleigh_ritz_batch(c, p, nb, rankb.data(), Qcb.data(), Zb.data(), thp.data(), rsp.data());
+                if (rc) { for (double *z : Zb) ctx_free(c, z); return rc; }
+                mark("Rayleigh-Ritz");
+                for (int bi = 0; bi < nb; ++bi) {
+                    ContourState &s = cs[act[b0 + bi]];
+                    const int rank = rankb[bi];
+                    double *Z = Zb[bi];
+                    Zb[bi] = nullptr;    // owned below (kept as the next iteration's block or freed)
+                    std::vector<double> &th = thb[bi], &rs = rsb[bi];
+                    bool unconverged_inside = false;
+                    double worst = 0.0;
+                    std::vector<int> keep;
+                    std::vector<double> open;
+                    // an unconverged value counts as a wanderer when its residual is at the solve-noise
+                    // level (> 1e-6) and no unconverged value of the previous iteration lies next to it
+                    bool all_wander = true;
+                    for (int l = 0; l < rank; ++l) {
+                        const bool inside = th[l] >= s.lo && th[l] <= s.hi;
+                        if (!inside) continue;
+                        if (rs[l] <= o->tol) { keep.push_back(l); continue; }
+                        unconverged_inside = true;
+                        worst = std::max(worst, rs[l]);
+                        open.push_back(th[l]);
+                        bool near = false;
+                        for (double tp : s.prev_open) near = near || std::fabs(th[l] - tp) <= 1e-4 * std::max(1.0, std::fabs(th[l]));
+                        if (rs[l] <= 1e-6 || near) all_wander = false;
+                    }
+                    // An iteration that adds no converged pair and does not improve the worst remaining
+                    // residual 10x leaves only Ritz values that do not converge: spurious ones, built from
+                    // basis directions dominated by solve noise, which move from one iteration to the next.
+                    // The contour stops; remaining residuals above 1e-6 are taken as spurious (status OK),
+                    // lower ones as a stalled eigenpair (GCIE_ENOCONV).
+                    // The same holds as soon as every unconverged value is a wanderer: a true eigenpair
+                    // keeps its Ritz value in place from one iteration to the next.
+                    bool stalled = false;
+                    if (unconverged_inside && it > 0 && (int)keep.size() <= s.prev_conv && worst >= 0.1 * s.prev_worst)
+                        stalled = true;
+                    if (unconverged_inside && it > 0 && all_wander) stalled = true;
+                    s.prev_conv = (int)keep.size();
+                    s.prev_worst = worst;
+                    s.prev_open = open;
+                    s.iters = it + 1;
+                    const bool last = (it + 1 == o->max_outer);
+                    if (std::getenv("GCIE_VERBOSE")) {
+                        int nin = 0;
+                        double worst = 0.0, wth = 0.0;
+                        for (int l = 0; l < rank; ++l)
+                            if (th[l] >= s.lo && th[l] <= s.hi) {
+                                ++nin;
+                                if (rs[l] > worst) { worst = rs[l]; wth = th[l]; }
+                            }
+                        fprintf(stderr, "[gcie] contour %d it %d: rank %d, %d Ritz values inside [%.6g, %.6g], %zu converged, "
+                                "worst residual %.3e at %.10g\n", act[b0 + bi], it, rank, nin, s.lo, s.hi, keep.size(), worst, wth);
+                    }
+                    if (!unconverged_inside || last || stalled) {
+                        s.th_last = th;
+                        s.rs_last = rs;
+                        s.rank_last = rank;
+                        // final: keep converged pairs
+                        if (!keep.empty()) {
+                            int *didx = nullptr;
+                            double *dout = nullptr;
+                            GCIE_CUDA_TRY(ctx_malloc(c, (void **)&didx, sizeof(int) * keep.size()));
+                            guard.ptrs.push_back(didx);
+                            GCIE_CUDA_TRY(ctx_malloc(c, (void **)&dout, sizeof(double) * (size_t)n * keep.size()));
+                            kept_bufs.ptrs.push_back(dout);   // lives until the result is copied out
+                            GCIE_CUDA_TRY(cudaMemcpyAsync(didx, keep.data(), sizeof(int) * keep.size(), cudaMemcpyHostToDevice, c->stream));
+                            {
+                                LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
+                                k_gather_cols<<<grid_for(c, n * (int64_t)keep.size()), 256, 0, c->stream>>>(n, rank, (int)keep.size(), didx, Z, dout);
+                                GCIE_CUDA_TRY(cudaGetLastError());
+                            }
+                            {
+                                // sign rule on the device: the entry of largest magnitude made positive
+                                LaunchScope ls(c, GCIE_K_OTHER, 16.0 * n * keep.size(), 0);
+                                k_sign_fix<<<(int)keep.size(), 256, 0, c->stream>>>(n, dout);
+                                GCIE_CUDA_TRY(cudaGetLastError());
+                            }
+                            for (size_t j = 0; j < keep.size(); ++j) s.kdev.push_back(dout + j * n);
+                            for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
+                        }
+                        s.done = true;
+                        s.status = (unconverged_inside && !(stalled && worst > 1e-6)) ? GCIE_ENOCONV : GCIE_OK;
+                        ctx_free(c, Z);
+                        if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
+                    } else {
+                        // FEAST: next iteration filters all Ritz vectors, one moment
+                        if (s.Z) ctx_free(c, s.Z);
+                        s.Z = Z;
+                        s.q = rank;
+                        s.theta = th;
+                        s.ncol = rank;
+                        s.m = 1;
+                    }
+                }
+                // release per-batch buffers now (the guard frees anything left on error paths)
+                GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+                for (void *q : guard.ptrs)
+                    if (q != dV0 && q != dB0) ctx_free(c, q);
+                guard.ptrs.assign({dV0, dB0});
+                b0 = b1;
             }
-            // release per-batch buffers now (the guard frees anything left on error paths)
-            GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
-            for (void *q : guard.ptrs)
-                if (q != dV0 && q != dB0) ctx_free(c, q);
-            guard.ptrs.assign({dV0, dB0});
-            b0 = b1;
+        }
+        for (auto &s : cs)
+            if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
+        if (!o->judge) break;
+        // count check of the contours finished in this pass; one that misses eigenvalues is replaced
+        // by its two halves (its pairs are dropped), which the next pass solves from the same V
+        bool added = false;
+        const size_t ncs = cs.size();
+        for (size_t k = 0; k < ncs; ++k) {
+            if (cs[k].judged) continue;
+            cs[k].judged = true;
+            if (!count_miss(cs[k].est, cs[k].se, cs[k].th_last.data(), cs[k].rs_last.data(), (int)cs[k].th_last.size(),
+                            cs[k].c, cs[k].r, cs[k].rank_last, o->tol))
+                continue;
+            if (cs[k].depth >= o->max_resplit || !(cs[k].hi > cs[k].lo)) {
+                cs[k].status = GCIE_ENOCONV;
+                continue;
+            }
+            gcie_contour parent{cs[k].c, cs[k].r, cs[k].lo, cs[k].hi}, half2[2];
+            resplit(cs[k].th_last.data(), (int)cs[k].th_last.size(), parent, 10.0, half2);
+            cs[k].split = true;
+            cs[k].kv.clear(); cs[k].kr.clear(); cs[k].kdev.clear();
+            const int depth = cs[k].depth + 1;
+            for (int h = 0; h < 2; ++h) {
+                ContourState ch;
+                ch.c = half2[h].c; ch.r = half2[h].r; ch.lo = half2[h].lo; ch.hi = half2[h].hi;
+                ch.ncol = L;
+                ch.m = o->moments;
+                ch.depth = depth;
+                cs[k].child[h] = (int)cs.size();
+                cs.push_back(ch);
+            }
+            ++resplits;
+            added = true;
+        }
+        if (!added) break;
+        bands.clear();   // the factors belong to the finished contours' nodes
+        mark("count check, re-split");
+    }
+
+    // the final contours: every re-split one replaced in place by its halves
+    std::vector<int> leaves;
+    {
+        std::vector<int> stack;
+        for (int k = nc - 1; k >= 0; --k) stack.push_back(k);
+        while (!stack.empty()) {
+            const int k = stack.back();
+            stack.pop_back();
+            if (cs[k].split) { stack.push_back(cs[k].child[1]); stack.push_back(cs[k].child[0]); }
+            else leaves.push_back(k);
         }
     }
-    for (auto &s : cs)
-        if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
+    const int nl = (int)leaves.size();
 
     mark("keep decisions, buffers");
     // merge and de-duplicate across contours (Algorithm 1, last step)
     struct Pair { double v, r; int k; const double *x; };   // x: device vector
     std::vector<Pair> all;
-    for (int k = 0; k < nc; ++k)
-        for (size_t j = 0; j < cs[k].kv.size(); ++j) all.push_back({cs[k].kv[j], cs[k].kr[j], k, cs[k].kdev[j]});
+    for (int li = 0; li < nl; ++li) {
+        const ContourState &s = cs[leaves[li]];
+        for (size_t j = 0; j < s.kv.size(); ++j) all.push_back({s.kv[j], s.kr[j], li, s.kdev[j]});
+    }
     // M inner product of two kept vectors (only for pairs with nearly equal values: rare)
     std::vector<double> ha(n), hb(n);
     auto dot_dev = [&](const double *a, const double *b) -> double {
@@ -1043,14 +1167,18 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     }
     res->n = n;
     res->count = (int32_t)kept.size();
-    res->ncontours = nc;
+    res->ncontours = nl;
+    res->resplits = resplits;
     res->evals = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, kept.size()));
     res->resid = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, kept.size()));
     res->contour_of = (int32_t *)std::malloc(sizeof(int32_t) * std::max<size_t>(1, kept.size()));
     res->evecs = (double *)std::malloc(sizeof(double) * std::max<size_t>(1, (size_t)n * kept.size()));
-    res->status_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nc));
-    res->iters_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nc));
-    if (!res->evals || !res->resid || !res->contour_of || !res->evecs || !res->status_per_contour || !res->iters_per_contour) {
+    res->status_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nl));
+    res->iters_per_contour = (int32_t *)std::malloc(sizeof(int32_t) * std::max(1, nl));
+    res->contours = (gcie_contour *)std::malloc(sizeof(gcie_contour) * std::max(1, nl));
+    res->count_estimate = (double *)std::malloc(sizeof(double) * std::max(1, nl));
+    if (!res->evals || !res->resid || !res->contour_of || !res->evecs || !res->status_per_contour || !res->iters_per_contour ||
+        !res->contours || !res->count_estimate) {
         gcie_result_free(res);
         set_error("result allocation failed");
         return GCIE_ENOMEM;
@@ -1101,11 +1229,14 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
     }
     mark("merge, eigenvectors out");
     int worst = GCIE_OK, outer = 0;
-    for (int k = 0; k < nc; ++k) {
-        res->status_per_contour[k] = cs[k].status;
-        res->iters_per_contour[k] = cs[k].iters;
-        outer = std::max(outer, cs[k].iters);
-        if (cs[k].status != GCIE_OK) worst = cs[k].status;
+    for (int li = 0; li < nl; ++li) {
+        const ContourState &s = cs[leaves[li]];
+        res->status_per_contour[li] = s.status;
+        res->iters_per_contour[li] = s.iters;
+        res->contours[li] = gcie_contour{s.c, s.r, s.lo, s.hi};
+        res->count_estimate[li] = s.est;
+        outer = std::max(outer, s.iters);
+        if (s.status != GCIE_OK) worst = s.status;
     }
     res->outer_iters = outer;
     res->cocg_iters = cocg_iters;
@@ -1132,7 +1263,8 @@ int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const g
     if (o.nodes < 2 || o.nodes > 64 || o.nodes % 2 || o.L < 1 || o.moments < 1 || o.moments > 8 || o.max_outer < 1 ||
         o.max_iters < 1 || !(o.tol > 0) || !(o.lin_tol > 0) || (o.precision != GCIE_MIXED && o.precision != GCIE_FP64) ||
         o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0 ||
-        o.precond < GCIE_PREC_NONE || o.precond > GCIE_PREC_BAND) {
+        o.precond < GCIE_PREC_NONE || o.precond > GCIE_PREC_BAND || o.judge < 0 || o.judge > 1 || o.max_resplit < 0 ||
+        o.max_resplit > 16) {
         set_error("solve: option out of range");
         return GCIE_EINVAL;
     }
@@ -1166,6 +1298,7 @@ void gcie_result_free(gcie_result *r)
     if (!r) return;
     std::free(r->evals); std::free(r->evecs); std::free(r->resid); std::free(r->contour_of);
     std::free(r->status_per_contour); std::free(r->iters_per_contour);
+    std::free(r->contours); std::free(r->count_estimate);
     std::memset(r, 0, sizeof(*r));
 }
 

@@ -113,6 +113,14 @@ struct LaunchScope {
 // device scratch of at least `bytes` (reused; contents undefined)
 int ctx_scratch(Ctx *c, size_t bytes, void **out);
 
+// contours.cu (host): the KDE cut of Algorithm 2, the minimiser of G_k over [lo, hi] for the k
+// sorted values p of the interval [a, b]; the count check of a finished contour; the two contours
+// that replace one that fails it
+double kde_cut(const double *p, size_t k, double a, double b, double w, double lo, double hi);
+bool count_miss(double est, double se, const double *theta, const double *res, int q, double c, double r, int rank,
+                double tol);
+void resplit(const double *theta, int q, const gcie_contour &parent, double w, gcie_contour out[2]);
+
 // ------------------------------------------------------------------ complex helpers
 template <typename T> struct cplx;
 template <> struct cplx<float> { using t = float2; };

@@ -46,45 +46,88 @@ struct Spectrum {
     }
 };
 
-double sparsity(const Spectrum &S, size_t i0, size_t i1, double s, double t)
-{
-    double g = 0.0;
-    for (size_t j = i0; j < i1; ++j) {
-        const double d = t - S.p[j];
-        g += std::exp(-s * d * d);
-    }
-    return g;
-}
+}  // namespace
 
-double kde_cut(const Spectrum &S, size_t i0, size_t i1, double a, double b, double w)
+// minimiser of G_k over [lo, hi]: the first minimum on KDE_GRID cell centres, refined by
+// golden-section search between the neighbouring centres; G_k sums over the k sorted values p
+double kde_cut(const double *p, size_t k, double a, double b, double w, double lo, double hi)
 {
-    const double lo = S.p[i0], hi = S.p[i1 - 1];
     const double s = w / ((b - a) * (b - a));
+    auto G = [&](double t) {
+        double g = 0.0;
+        for (size_t j = 0; j < k; ++j) {
+            const double d = t - p[j];
+            g += std::exp(-s * d * d);
+        }
+        return g;
+    };
     const double h = (hi - lo) / KDE_GRID;
     int best = 0;
     double gbest = 0.0;
     for (int i = 0; i < KDE_GRID; ++i) {
-        const double g = sparsity(S, i0, i1, s, lo + (i + 0.5) * h);
+        const double g = G(lo + (i + 0.5) * h);
         if (i == 0 || g < gbest) { gbest = g; best = i; }
     }
     double ga = lo + (std::max(best - 1, 0) + 0.5) * h;
     double gb = lo + (std::min(best + 1, KDE_GRID - 1) + 0.5) * h;
     const double gr = (std::sqrt(5.0) - 1.0) / 2.0;
     double x1 = gb - gr * (gb - ga), x2 = ga + gr * (gb - ga);
-    double f1 = sparsity(S, i0, i1, s, x1), f2 = sparsity(S, i0, i1, s, x2);
+    double f1 = G(x1), f2 = G(x2);
     for (int it = 0; it < KDE_GOLDEN_STEPS; ++it) {
         if (f1 <= f2) {
             gb = x2; x2 = x1; f2 = f1;
             x1 = gb - gr * (gb - ga);
-            f1 = sparsity(S, i0, i1, s, x1);
+            f1 = G(x1);
         } else {
             ga = x1; x1 = x2; f1 = f2;
             x2 = ga + gr * (gb - ga);
-            f2 = sparsity(S, i0, i1, s, x2);
+            f2 = G(x2);
         }
     }
     return 0.5 * (ga + gb);
 }
+
+// Count check of a finished contour: the stochastic trace estimate est (standard error se) of the
+// enclosed eigenvalue count against its Ritz values on the diameter [c - r, c + r].  A miss when
+// every Ritz value of the rank-dimensional basis lies there (no spare direction), or when est
+// exceeds the converged ones there by more than max(1.5, 3 se).
+bool count_miss(double est, double se, const double *theta, const double *res, int q, double c, double r, int rank,
+                double tol)
+{
+    int on = 0, found = 0;
+    for (int l = 0; l < q; ++l)
+        if (std::fabs(theta[l] - c) <= r) {
+            ++on;
+            if (res[l] <= tol) ++found;
+        }
+    return on >= rank || est - found > std::max(1.5, 3.0 * se);
+}
+
+// The halves [lo, t], [t, hi] of a contour that failed the count check: t minimises G_k of its
+// Ritz values in [lo, hi] between their quartiles (the (k/4)-th and (k-1-k/4)-th of k sorted),
+// else the midpoint; both keep the parent's radius-to-half-width ratio.
+void resplit(const double *theta, int q, const gcie_contour &parent, double w, gcie_contour out[2])
+{
+    const double lo = parent.lo, hi = parent.hi;
+    std::vector<double> pts;
+    for (int l = 0; l < q; ++l)
+        if (theta[l] >= lo && theta[l] <= hi) pts.push_back(theta[l]);
+    std::sort(pts.begin(), pts.end());
+    double t = 0.5 * (lo + hi);
+    const size_t k = pts.size();
+    if (k >= 2) {
+        const double q1 = pts[k / 4], q3 = pts[k - 1 - k / 4];
+        if (q1 < q3) {
+            const double tc = kde_cut(pts.data(), k, lo, hi, w, q1, q3);
+            if (lo < tc && tc < hi) t = tc;
+        }
+    }
+    const double infl = parent.r / (0.5 * (hi - lo));
+    out[0].c = 0.5 * (lo + t); out[0].r = infl * 0.5 * (t - lo); out[0].lo = lo; out[0].hi = t;
+    out[1].c = 0.5 * (t + hi); out[1].r = infl * 0.5 * (hi - t); out[1].lo = t; out[1].hi = hi;
+}
+
+namespace {
 
 // step 2 on a list of intervals; returns the final intervals in ascending order
 std::vector<std::pair<double, double>> split_all(const Spectrum &S, std::vector<std::pair<double, double>> work,
@@ -100,7 +143,7 @@ std::vector<std::pair<double, double>> split_all(const Spectrum &S, std::vector<
             done.push_back(iv);
             continue;
         }
-        const double t = kde_cut(S, r.first, r.second, iv.first, iv.second, w);
+        const double t = kde_cut(S.p.data() + r.first, nk, iv.first, iv.second, w, S.p[r.first], S.p[r.second - 1]);
         work.push_back({iv.first, t});
         work.push_back({t, iv.second});
     }
@@ -181,5 +224,26 @@ extern "C" int gcie_kde_contours(const double *pred, int32_t npred, int32_t nmin
         out[i].r = (1.0 + alpha) * 0.5 * (b - a);
         counts[i] = (int32_t)S.count(a, b);
     }
+    return GCIE_OK;
+}
+
+extern "C" int gcie_count_miss(double est, double se, const double *theta, const double *res, int32_t q, double c,
+                               double r, int32_t rank, double tol, int32_t *miss)
+{
+    if (!miss || q < 0 || (q > 0 && (!theta || !res)) || !(r > 0) || rank < 0) {
+        gcie::set_error("count_miss: null pointer or bad size");
+        return GCIE_EINVAL;
+    }
+    *miss = gcie::count_miss(est, se, theta, res, q, c, r, rank, tol) ? 1 : 0;
+    return GCIE_OK;
+}
+
+extern "C" int gcie_resplit(const double *theta, int32_t q, const gcie_contour *parent, double w, gcie_contour *out)
+{
+    if (!parent || !out || q < 0 || (q > 0 && !theta) || !(parent->hi > parent->lo) || !(parent->r > 0) || !(w > 0)) {
+        gcie::set_error("resplit: need lo < hi, r > 0, w > 0 and non-null pointers");
+        return GCIE_EINVAL;
+    }
+    gcie::resplit(theta, q, *parent, w, out);
     return GCIE_OK;
 }

@@ -13,6 +13,12 @@ struct BandCache {
     Ctx *ctx = nullptr;      // the context whose pool holds the factors
     // device array of per-shift factor pointers (caller frees it with cudaFreeAsync)
     int get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float2 ***d_ptrs_out);
+    // frees every factor (the shifts of finished contours)
+    void clear()
+    {
+        for (auto &e : entries) ctx_free(ctx, e.AB);
+        entries.clear();
+    }
     ~BandCache();
 };
 

@@ -138,3 +138,46 @@ def test_resplit_keeps_a_quarter_on_each_side_of_a_widening_spectrum():
     assert 6 <= below <= 18 and lam[6] <= t <= lam[17]
     plain = O.kde_cut(lam, s, e, 10.0)
     assert np.sum(lam < plain) > 18
+
+
+# --------------------------------------------------------------------------- library vs oracle (host)
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_2511_01927_gb300 import build
+    build.build()
+    import paper_2511_01927_gb300 as G
+    G.lib()
+    return G
+
+
+def test_library_count_miss_matches_oracle(G):
+    rng = np.random.default_rng(21)
+    for _ in range(300):
+        q = int(rng.integers(1, 40))
+        th = rng.uniform(0.0, 10.0, q)
+        res = 10.0 ** rng.uniform(-14, -4, q)
+        c, r = rng.uniform(2.0, 8.0), rng.uniform(0.5, 4.0)
+        est, se = rng.uniform(0.0, 30.0), rng.uniform(0.0, 3.0)
+        rank = int(rng.integers(1, 45))
+        assert G.gcie_count_miss(est, se, th, res, c, r, rank, 1e-10) == O.count_miss(est, se, th, res, c, r, rank, 1e-10)
+
+
+def test_library_resplit_matches_oracle(G):
+    rng = np.random.default_rng(22)
+    for k in range(40):
+        s, e = 0.0, float(rng.uniform(5.0, 50.0))
+        if k % 3 == 0:
+            th = rng.uniform(s - 2.0, e + 2.0, int(rng.integers(0, 40)))
+        elif k % 3 == 1:
+            th = np.concatenate([x + 0.1 * rng.standard_normal(6) for x in rng.uniform(s, e, 4)])
+        else:
+            th = np.full(5, 0.5 * e)
+        infl = 1.0 + float(rng.uniform(0.0, 0.3))
+        c, R = 0.5 * (s + e), infl * 0.5 * (e - s)
+        a = O.resplit(th, c, R, s, e)
+        b = G.gcie_resplit(th, c, R, s, e)
+        for x, y in zip(a, b):
+            assert np.allclose(x, y, rtol=0, atol=1e-9 * e)
+    with pytest.raises(G.GcieError):
+        G.gcie_resplit([1.0], 1.0, 0.5, 2.0, 1.0)
