@@ -512,7 +512,7 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     constexpr int CPT = sizeof(T) == 4 ? 2 : 1;
     const int64_t n = p->n;
     if (ncol % CPT || ncol > 1024 || ncol <= 0) { set_error("cocg: ncol must be even and <= 1024"); return GCIE_EINVAL; }
-    Geo g = make_geo(c, n, nshift, ncol, CPT);
+    Geo g = make_geo(c, n, nshift, ncol, CPT, p->bw);
     const Geo &gr = g;   // refinement sweep: same tiles, so partial sums of both land in the same slots
     const int64_t blk = (int64_t)nshift * n * ncol;
     const int ntiles = nshift * g.chunks, ntiles_r = nshift * gr.chunks;

@@ -12,7 +12,11 @@ struct Geo {
     int tpr, rpb, threads, chunks;
     int64_t rows_per_chunk;
 };
-Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt);
+// Tiles of the row sweeps: CTA (s, chunk) takes rows [chunk * rows_per_chunk, ...) of block s.
+// band > 0 (the matrix bandwidth): chunks of about one bandwidth of rows, so that the CTAs running at
+// the same time sweep adjacent chunks of one shift in step and the rows a chunk gathers from its
+// neighbours are read from DRAM once and then found in L2.
+Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt, int64_t band = 0);
 
 // a4: Q[s] = z_s M P[s] - K P[s] for s < nshift (FP32 or FP64 complex blocks, n x ncol row-major).
 int shifted_spmm_f32(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, int ncol, const float2 *P, float2 *Q);

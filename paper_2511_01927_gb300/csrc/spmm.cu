@@ -8,11 +8,13 @@
 //
 // Layout: block s is n x ncol row-major complex (ncol right-hand sides contiguous), so a row of
 // one block is one coalesced segment; consecutive threads own consecutive column pairs.
+#include <algorithm>
+
 #include "kernels.cuh"
 
 namespace gcie {
 
-Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt)
+Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt, int64_t band)
 {
     Geo g;
     g.tpr = ncol / cpt;
@@ -23,6 +25,10 @@ Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt)
     int64_t chunks = (target + nshift - 1) / nshift;
     if (chunks < 1) chunks = 1;
     int64_t rpc = (n + chunks - 1) / chunks;
+    // with a wide band, the gathers of CTAs far apart in the rows share nothing: all resident CTAs'
+    // windows of 2 band rows would have to stay in L2 between a row's first and last use.  Chunks of
+    // one bandwidth make neighbouring CTAs read the same rows at about the same time instead.
+    if (band >= 64) rpc = std::min(rpc, band);
     rpc = ((rpc + g.rpb - 1) / g.rpb) * g.rpb;
     if (rpc < g.rpb) rpc = g.rpb;
     g.rows_per_chunk = rpc;
