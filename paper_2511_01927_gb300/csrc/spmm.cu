@@ -27,8 +27,10 @@ Geo make_geo(const Ctx *c, int64_t n, int nshift, int ncol, int cpt, int64_t ban
     int64_t rpc = (n + chunks - 1) / chunks;
     // with a wide band, the gathers of CTAs far apart in the rows share nothing: all resident CTAs'
     // windows of 2 band rows would have to stay in L2 between a row's first and last use.  Chunks of
-    // one bandwidth make neighbouring CTAs read the same rows at about the same time instead.
-    if (band >= 64) rpc = std::min(rpc, band);
+    // one bandwidth make the CTAs of adjacent chunks, which run at the same time, read the same rows
+    // at about the same time instead (shorter chunks put a row's readers several chunks apart, and
+    // they drift apart in time); used while it still gives two CTAs per SM.
+    if (band >= 64 && (n + band - 1) / band * nshift >= (int64_t)c->num_sms * 2) rpc = band;
     rpc = ((rpc + g.rpb - 1) / g.rpb) * g.rpb;
     if (rpc < g.rpb) rpc = g.rpb;
     g.rows_per_chunk = rpc;
