@@ -92,3 +92,17 @@ def test_judge_rejects_bad_options(G, ctx):
         with pytest.raises(G.GcieError) as e:
             G.gcie_solve(ctx, K, M, 1.0, 100.0, L=8, **kw)
         assert e.value.code == 1
+
+
+def test_judge_reports_a_miss_left_at_the_last_level(G, ctx):
+    """The saturated contour with no re-split allowed: the check fails, the contour keeps what it
+    found and the solve reports GCIE_ENOCONV for it."""
+    n = 300
+    K, M = P.fem1d(n)
+    lam = P.fem1d_eigenvalue(np.arange(1, 40), n)
+    lo, hi = 0.5 * (lam[4] + lam[5]), 0.5 * (lam[28] + lam[29])
+    V = P.gaussian_block(n, 6, 3)
+    r = G.gcie_solve(ctx, K, M, lo, hi, nodes=16, moments=2, nuniform=1, V0=V, tol=1e-10, judge=1, max_resplit=0,
+                     allow_noconv=True)
+    assert r["rc"] == 5 and r["status"] == [5] and r["resplits"] == 0
+    assert 0 < len(r["evals"]) < 24 and r["count_estimate"][0] > len(r["evals"]) + 1.5
