@@ -105,4 +105,4 @@ def test_judge_reports_a_miss_left_at_the_last_level(G, ctx):
     r = G.gcie_solve(ctx, K, M, lo, hi, nodes=16, moments=2, nuniform=1, V0=V, tol=1e-10, judge=1, max_resplit=0,
                      allow_noconv=True)
     assert r["rc"] == 5 and r["status"] == [5] and r["resplits"] == 0
-    assert 0 < len(r["evals"]) < 24 and r["count_estimate"][0] > len(r["evals"]) + 1.5
+    assert len(r["evals"]) < 24 and r["count_estimate"][0] > len(r["evals"]) + 1.5
