@@ -318,6 +318,17 @@ def test_solve_fem2d_matches_oracle_ci(G, ctx, small2d):
     _check_against(r, ro["evals"], K, M, ro["evecs"])
 
 
+def test_solve_fem2d_32_nodes_matches_oracle(G, ctx, small2d):
+    """The paper's N_q = 32 trapezoid nodes per circle (Section 4.2): 16 shifted systems per
+    contour in one batch, same set and values as the oracle with 32 nodes."""
+    K, M, spec, pen = small2d
+    V = P.gaussian_block(K.n, 32, 5)
+    r = G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], nodes=32, moments=2, nuniform=2, V0=V)
+    ro = O.ci_solve(K, M, spec["lo"], spec["hi"], V, ncontours=2, nodes=32, moments_m=2, tol=1e-10)
+    assert len(r["evals"]) == spec["count"] == len(ro["evals"])
+    _check_against(r, ro["evals"], K, M, ro["evecs"])
+
+
 def test_solve_split_invariance_and_boundaries(G, ctx, small2d):
     K, M, spec, pen = small2d
     V = P.gaussian_block(K.n, 32, 7)
