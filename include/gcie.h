@@ -171,6 +171,14 @@ int gcie_solve(gcie_ctx *ctx, const gcie_csr *K, const gcie_csr *M, double lo, d
                const gcie_opts *opts, gcie_result *out);
 int gcie_solve_pencil(gcie_ctx *ctx, gcie_pencil *p, double lo, double hi, const gcie_opts *opts,
                       gcie_result *out);
+/* Independent pencils (the serving case): pencil i is K[i], M[i] with the interval [lo[i], hi[i]],
+ * solved into out[i] with the same options, one after another on the context's stream (the pencils
+ * share nothing, so they can also go to different contexts or GPUs).  K, M, lo, hi, out: host
+ * arrays of npencils >= 1; each out[i] is released with gcie_result_free.  A pencil that ends with
+ * GCIE_ENOCONV does not stop the batch; any other error does, leaving the later results zeroed.
+ * Returns GCIE_OK when every solve did, else the first status other than GCIE_OK. */
+int gcie_solve_batch(gcie_ctx *ctx, int32_t npencils, const gcie_csr *K, const gcie_csr *M, const double *lo,
+                     const double *hi, const gcie_opts *opts, gcie_result *out);
 void gcie_result_free(gcie_result *r);
 /* Frees one array of a gcie_result that the caller took out of the struct (and set to NULL there,
  * so that gcie_result_free skips it), e.g. to hand the eigenvectors to another owner without a

@@ -17,7 +17,7 @@ MIXED, FP64 = 0, 1
 EXPORTED_SYMBOLS = [
     "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
-    "gcie_solve", "gcie_solve_pencil", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_solve", "gcie_solve_pencil", "gcie_solve_batch", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
@@ -96,6 +96,7 @@ def lib():
         "gcie_pencil_nnz": (i64, [vp]),
         "gcie_solve": (C.c_int, [vp, C.POINTER(Csr), C.POINTER(Csr), d, d, C.POINTER(Opts), C.POINTER(Result)]),
         "gcie_solve_pencil": (C.c_int, [vp, vp, d, d, C.POINTER(Opts), C.POINTER(Result)]),
+        "gcie_solve_batch": (C.c_int, [vp, i32, vp, vp, vp, vp, C.POINTER(Opts), vp]),
         "gcie_result_free": (None, [C.POINTER(Result)]),
         "gcie_buffer_free": (None, [vp]),
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
@@ -247,6 +248,40 @@ def _take_result(r: Result) -> dict:
     return out
 
 
+def _check_result(rc: int, r: Result, where: str, allow_noconv: bool):
+    """Raise for a failed solve, releasing what the library put into the result first."""
+    try:
+        _check(rc, where, allow=(5,) if allow_noconv else ())
+    except GcieError:
+        lib().gcie_result_free(C.byref(r))
+        raise
+
+
+def gcie_solve_batch(ctx, pencils, allow_noconv: bool = False, **opts) -> list:
+    """Independent pencils [(K, M, lo, hi), ...] with the same options (gcie_opts fields as keywords);
+    a list of results as gcie_solve returns them."""
+    hs = [(_HostCsr(K), _HostCsr(M)) for K, M, _, _ in pencils]
+    npen = len(hs)
+    Ks = (Csr * npen)(*[h[0].s for h in hs])
+    Ms = (Csr * npen)(*[h[1].s for h in hs])
+    lo = np.ascontiguousarray([float(p[2]) for p in pencils], dtype=np.float64)
+    hi = np.ascontiguousarray([float(p[3]) for p in pencils], dtype=np.float64)
+    oh = _OptsHolder(opts)
+    res = (Result * max(npen, 1))()
+    rc = lib().gcie_solve_batch(ctx, npen, C.cast(Ks, C.c_void_p), C.cast(Ms, C.c_void_p), lo.ctypes.data,
+                                hi.ctypes.data, C.byref(oh.o), C.cast(res, C.c_void_p))
+    if rc != 0 and not (allow_noconv and rc == 5):
+        for i in range(npen):
+            lib().gcie_result_free(C.byref(res[i]))
+        _check(rc, "gcie_solve_batch")
+    outs = []
+    for i in range(npen):
+        o = _take_result(res[i])
+        o["rc"] = rc
+        outs.append(o)
+    return outs
+
+
 def gcie_solve(ctx, K, M, lo: float, hi: float, allow_noconv: bool = False, **opts) -> dict:
     """All eigenpairs in [lo, hi] from host CSR matrices (pencils.Csr-like objects).  Keyword
     options are the gcie_opts fields; `contours` = list of (c, r, lo, hi); `V0` = n x L block."""
@@ -254,7 +289,7 @@ def gcie_solve(ctx, K, M, lo: float, hi: float, allow_noconv: bool = False, **op
     oh = _OptsHolder(opts)
     r = Result()
     rc = lib().gcie_solve(ctx, C.byref(hk.s), C.byref(hm.s), float(lo), float(hi), C.byref(oh.o), C.byref(r))
-    _check(rc, "gcie_solve", allow=(5,) if allow_noconv else ())
+    _check_result(rc, r, "gcie_solve", allow_noconv)
     out = _take_result(r)
     out["rc"] = rc
     return out
@@ -264,7 +299,7 @@ def gcie_solve_pencil(ctx, pencil, lo: float, hi: float, allow_noconv: bool = Fa
     oh = _OptsHolder(opts)
     r = Result()
     rc = lib().gcie_solve_pencil(ctx, pencil, float(lo), float(hi), C.byref(oh.o), C.byref(r))
-    _check(rc, "gcie_solve_pencil", allow=(5,) if allow_noconv else ())
+    _check_result(rc, r, "gcie_solve_pencil", allow_noconv)
     out = _take_result(r)
     out["rc"] = rc
     return out

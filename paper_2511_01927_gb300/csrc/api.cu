@@ -1291,6 +1291,23 @@ int gcie_solve(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, double lo, dou
     return rc;
 }
 
+int gcie_solve_batch(gcie_ctx *c, int32_t npencils, const gcie_csr *K, const gcie_csr *M, const double *lo,
+                     const double *hi, const gcie_opts *opts, gcie_result *out)
+{
+    if (!c || !K || !M || !lo || !hi || !out || npencils < 1) { set_error("solve_batch: null argument or no pencil"); return GCIE_EINVAL; }
+    for (int32_t i = 0; i < npencils; ++i) std::memset(&out[i], 0, sizeof(out[i]));
+    int first = GCIE_OK;
+    for (int32_t i = 0; i < npencils; ++i) {
+        const int rc = gcie_solve(c, &K[i], &M[i], lo[i], hi[i], opts, &out[i]);
+        if (rc != GCIE_OK && first == GCIE_OK) first = rc;
+        if (rc != GCIE_OK && rc != GCIE_ENOCONV) {
+            set_error("solve_batch: pencil " + std::to_string(i) + ": " + gcie_last_error());
+            break;
+        }
+    }
+    return first;
+}
+
 void gcie_buffer_free(void *p) { std::free(p); }
 
 void gcie_result_free(gcie_result *r)

@@ -380,3 +380,26 @@ def test_invalid_inputs(G, ctx):
     with pytest.raises(G.GcieError) as e:
         G.gcie_solve(ctx, K, M, 1.0, 100.0, nodes=7)
     assert e.value.code == 1
+
+
+def test_solve_batch_of_uneven_pencils(G, ctx, small2d):
+    """Independent pencils of different kinds and sizes in one call: each result is the one a
+    single solve gives, and each set is the definition's (closed form / inertia count)."""
+    K2, M2, spec2, _ = small2d
+    items = []
+    for n in (300, 700):
+        K, M = P.fem1d(n)
+        lam = P.fem1d_eigenvalue(np.arange(1, 30), n)
+        items.append((K, M, 0.5 * (lam[2] + lam[3]), 0.5 * (lam[19] + lam[20]), lam[3:20]))
+    items.append((K2, M2, spec2["lo"], spec2["hi"], None))
+    outs = G.gcie_solve_batch(ctx, [(K, M, lo, hi) for K, M, lo, hi, _ in items], L=32, nuniform=2, seed=9)
+    assert len(outs) == 3 and all(o["rc"] == 0 for o in outs)
+    for (K, M, lo, hi, want), o in zip(items, outs):
+        one = G.gcie_solve(ctx, K, M, lo, hi, L=32, nuniform=2, seed=9)
+        assert len(o["evals"]) == len(one["evals"]) == O.count_in(K, M, lo, hi)
+        assert np.max(np.abs(o["evals"] - one["evals"]) / np.abs(one["evals"])) <= 1e-12
+        if want is not None:
+            assert np.max(np.abs(o["evals"] - want) / want) < 1e-10
+        assert np.max(o["resid"]) <= 1e-10
+    with pytest.raises(G.GcieError):
+        G.gcie_solve_batch(ctx, [(K2, M2, 1.0, 0.5)])
