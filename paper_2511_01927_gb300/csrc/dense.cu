@@ -415,7 +415,7 @@ k_jacobi_cl(const __grid_constant__ JacobiBatch jb, double tol, int maxsweep)
         return tot;
     };
 
-    // rows of round 0 and V = I
+    // rows of the first pairing of the round-robin order, and V = I
     double loc = 0.0;
     for (int e = tid; e < 2 * npl * pe; e += JT) {
         const int sl = e / pe, j = e % pe;
