@@ -4,9 +4,13 @@ pencil of a 500 x 500 grid (n = 249001, log-normal coefficient fields in K and M
 FP64 refinement, residual tolerance 1e-10.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
+                    [--contours uniform|kde [--pred-noise S]]
 
 One step = one complete solve (ingested pencil resident on the GPU; every step repeats the shifted
-solves, moments, basis, Rayleigh-Ritz and merge).  Prints one JSON line on rank 0.  Under torchrun
+solves, moments, basis, Rayleigh-Ritz and merge).  `--contours kde` times the same workload with
+contours from Algorithm 2 instead: the predicted spectrum is the solver's own eigenvalues of an
+untimed uniform solve plus seeded Gaussian noise of S mean spacings (a stand-in for a trained
+predictor, at its best), the solve runs with the count check on.  Prints one JSON line on rank 0.  Under torchrun
 each rank solves its own replica of the workload (independent problems, no collective).
 """
 from __future__ import annotations
@@ -28,6 +32,7 @@ sys.path.insert(0, ROOT)
 import pencils as P  # noqa: E402
 
 METRIC = "converged eigenpairs/s at residual<=1e-10 (uniform contours)"
+METRIC_KDE = "converged eigenpairs/s at residual<=1e-10 (KDE contours from a perturbed spectrum)"
 UNIT = "eigenpairs/s"
 
 
@@ -40,6 +45,9 @@ def parse():
     ap.add_argument("--workload", default="fem2d-p1-500")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--contours", default="uniform", choices=["uniform", "kde"])
+    ap.add_argument("--pred-noise", type=float, default=0.1,
+                    help="with --contours kde: noise of the predicted spectrum in mean eigenvalue spacings")
     ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",
                     help="run only a small shifted solve (NODES nodes of the first contour, L columns, band "
                          "preconditioner, 4 iterations) for kernel profiling, then exit")
@@ -135,6 +143,9 @@ def run_ours(args, rank, world):
     ctx = G.gcie_create(dev, stream.cuda_stream)
     pen = G.gcie_pencil_create(ctx, K, M)
     opts = solver_opts(spec, V)
+    kde = None
+    if args.contours == "kde":
+        opts, kde = kde_opts(G, ctx, pen, spec, opts, args.pred_noise)
 
     def step(profile):
         return G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], profile=int(profile), **opts)
@@ -170,7 +181,31 @@ def run_ours(args, rank, world):
     e2e = e2e_measure(G, ctx, K, M, spec, opts, args.steps)
     G.gcie_pencil_destroy(pen)
     G.gcie_destroy(ctx)
-    return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e)
+    return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e,
+                kde=kde)
+
+
+def kde_opts(G, ctx, pen, spec, opts, noise):
+    """Options for a solve on contours from Algorithm 2.  The prediction: the eigenvalues of one
+    untimed uniform solve plus N(0, (noise x mean spacing)^2), seed 7.  N_max is the smallest value
+    (from 38 up, N_min = 10, w = 10 as in the paper) for which Algorithm 2 gives no more contours
+    than the uniform layout, so both use the same number of nodes; the outer ends are the target
+    interval's.  The count check is on."""
+    ref = G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], **opts)
+    lam = np.sort(ref["evals"])
+    spacing = (lam[-1] - lam[0]) / max(len(lam) - 1, 1)
+    pred = lam + np.random.default_rng(7).normal(0.0, noise * spacing, lam.size)
+    for nmax in range(38, 400):
+        cts = G.gcie_kde_contours(pred, nmin=10, nmax=nmax, w=10.0)
+        if len(cts) <= spec["contours"]:
+            break
+    edges = [spec["lo"]] + [c[1] for c in cts[:-1]] + [spec["hi"]]
+    contours = [(0.5 * (a + b), 0.5 * (b - a), a, b) for a, b in zip(edges[:-1], edges[1:])]
+    o = {k: v for k, v in opts.items() if k != "nuniform"}
+    o.update(contours=contours, judge=1)
+    info = {"nmin": 10, "nmax": nmax, "w": 10.0, "noise_spacings": noise, "edges": [float(e) for e in edges],
+            "predicted_counts": [int(c[4]) for c in cts]}
+    return o, info
 
 
 def source_digest(text):
@@ -325,6 +360,7 @@ def main():
     spec, stats = r["spec"], r["stats"]
     ms_step = r["ms"] / args.steps
     value = r["count"] / (r["ms"] / 1e3)
+    metric = METRIC if args.contours == "uniform" else METRIC_KDE
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -354,7 +390,7 @@ def main():
                 "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
     spmm_ms = stats["spmm_dir"]["ms"] + stats["spmm_upd"]["ms"]
     spmm_gbs = (stats["spmm_dir"]["bytes"] + stats["spmm_upd"]["bytes"]) / max(spmm_ms, 1e-9) / 1e6
-    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+    out = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
            "config": {"workload": args.workload, "n": int(r["K"].n), "pairs_per_step": spec["count"],
@@ -362,13 +398,16 @@ def main():
                       "moments": spec["moments"], "tol": 1e-10, "l2": "inputs larger than L2 (16 GB block)",
                       "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
                       "feast_iters_per_contour": r["last"]["iters"],
-                      "cocg_iters": r["last"]["cocg_iters"]},
+                      "cocg_iters": r["last"]["cocg_iters"], "contour_layout": args.contours},
            "roofline": roof,
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
                         "nameplate_frac": spmm_gbs / 8000.0},
            "kernel_ms": {k: round(v["ms"], 2) for k, v in classes.items()},
            "gpu_launches": int(stats["total_launches"]),
            "clocks": r["clocks"], "e2e": r["e2e"]}
+    if r["kde"] is not None:
+        out["config"]["kde"] = r["kde"] | {"resplits": r["last"]["resplits"],
+                                           "count_estimate": [round(float(x), 2) for x in r["last"]["count_estimate"]]}
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         v, tot, sample = oracle_sample(args, spec, *P.workload(args.workload)[:2], args.cpu_sample_seconds)
         out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
