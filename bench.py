@@ -186,24 +186,20 @@ def run_ours(args, rank, world):
 
 
 def kde_opts(G, ctx, pen, spec, opts, noise):
-    """Options for a solve on contours from Algorithm 2.  The prediction: the eigenvalues of one
-    untimed uniform solve plus N(0, (noise x mean spacing)^2), seed 7.  N_max is the smallest value
-    (from 38 up, N_min = 10, w = 10 as in the paper) for which Algorithm 2 gives no more contours
-    than the uniform layout, so both use the same number of nodes; the outer ends are the target
-    interval's.  The count check is on."""
+    """Options for a solve on contours from Algorithm 2 with the paper's parameters (N_min = 10,
+    N_max = 50, w = 10).  The prediction: the eigenvalues of one untimed uniform solve plus
+    N(0, (noise x mean spacing)^2), seed 7.  The outer ends are the target interval's; the count
+    check is on."""
     ref = G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], **opts)
     lam = np.sort(ref["evals"])
     spacing = (lam[-1] - lam[0]) / max(len(lam) - 1, 1)
     pred = lam + np.random.default_rng(7).normal(0.0, noise * spacing, lam.size)
-    for nmax in range(38, 400):
-        cts = G.gcie_kde_contours(pred, nmin=10, nmax=nmax, w=10.0)
-        if len(cts) <= spec["contours"]:
-            break
+    cts = G.gcie_kde_contours(pred, nmin=10, nmax=50, w=10.0)
     edges = [spec["lo"]] + [c[1] for c in cts[:-1]] + [spec["hi"]]
     contours = [(0.5 * (a + b), 0.5 * (b - a), a, b) for a, b in zip(edges[:-1], edges[1:])]
     o = {k: v for k, v in opts.items() if k != "nuniform"}
     o.update(contours=contours, judge=1)
-    info = {"nmin": 10, "nmax": nmax, "w": 10.0, "noise_spacings": noise, "edges": [float(e) for e in edges],
+    info = {"nmin": 10, "nmax": 50, "w": 10.0, "noise_spacings": noise, "edges": [float(e) for e in edges],
             "predicted_counts": [int(c[4]) for c in cts]}
     return o, info
 
