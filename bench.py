@@ -4,12 +4,13 @@ pencil of a 500 x 500 grid (n = 249001, log-normal coefficient fields in K and M
 FP64 refinement, residual tolerance 1e-10.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                    [--contours uniform|kde [--pred-noise S]]
+                    [--contours uniform|kde|planned [--pred-noise S]]
 
 One step = one complete solve (ingested pencil resident on the GPU; every step repeats the shifted
 solves, moments, basis, Rayleigh-Ritz and merge).  `--contours kde` times the same workload with
-contours from Algorithm 2 instead: the predicted spectrum is the solver's own eigenvalues of an
-untimed uniform solve plus seeded Gaussian noise of S mean spacings (a stand-in for a trained
+contours from Algorithm 2 instead, `--contours planned` with as many contours as the uniform layout
+cut in the widest gaps (gcie_plan_contours): the predicted spectrum is the solver's own eigenvalues
+of an untimed uniform solve plus seeded Gaussian noise of S mean spacings (a stand-in for a trained
 predictor, at its best), the solve runs with the count check on.  Prints one JSON line on rank 0.  Under torchrun
 each rank solves its own replica of the workload (independent problems, no collective).
 """
@@ -33,6 +34,7 @@ import pencils as P  # noqa: E402
 
 METRIC = "converged eigenpairs/s at residual<=1e-10 (uniform contours)"
 METRIC_KDE = "converged eigenpairs/s at residual<=1e-10 (KDE contours from a perturbed spectrum)"
+METRIC_PLANNED = "converged eigenpairs/s at residual<=1e-10 (gap-planned contours from a perturbed spectrum)"
 UNIT = "eigenpairs/s"
 
 
@@ -45,9 +47,9 @@ def parse():
     ap.add_argument("--workload", default="fem2d-p1-500")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--contours", default="uniform", choices=["uniform", "kde"])
+    ap.add_argument("--contours", default="uniform", choices=["uniform", "kde", "planned"])
     ap.add_argument("--pred-noise", type=float, default=0.1,
-                    help="with --contours kde: noise of the predicted spectrum in mean eigenvalue spacings")
+                    help="with --contours kde|planned: noise of the predicted spectrum in mean eigenvalue spacings")
     ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",
                     help="run only a small shifted solve (NODES nodes of the first contour, L columns, band "
                          "preconditioner, 4 iterations) for kernel profiling, then exit")
@@ -144,8 +146,8 @@ def run_ours(args, rank, world):
     pen = G.gcie_pencil_create(ctx, K, M)
     opts = solver_opts(spec, V)
     kde = None
-    if args.contours == "kde":
-        opts, kde = kde_opts(G, ctx, pen, spec, opts, args.pred_noise)
+    if args.contours != "uniform":
+        opts, kde = predicted_opts(G, ctx, pen, spec, opts, args.pred_noise, args.contours)
 
     def step(profile):
         return G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], profile=int(profile), **opts)
@@ -185,22 +187,27 @@ def run_ours(args, rank, world):
                 kde=kde)
 
 
-def kde_opts(G, ctx, pen, spec, opts, noise):
-    """Options for a solve on contours from Algorithm 2 with the paper's parameters (N_min = 10,
-    N_max = 50, w = 10).  The prediction: the eigenvalues of one untimed uniform solve plus
-    N(0, (noise x mean spacing)^2), seed 7.  The outer ends are the target interval's; the count
+def predicted_opts(G, ctx, pen, spec, opts, noise, kind):
+    """Options for a solve on contours from a predicted spectrum: the eigenvalues of one untimed
+    uniform solve plus N(0, (noise x mean spacing)^2), seed 7.  kind "kde": Algorithm 2 with the
+    paper's parameters (N_min = 10, N_max = 50, w = 10), outer ends moved to the target interval's;
+    kind "planned": gcie_plan_contours with the uniform layout's number of contours.  The count
     check is on."""
     ref = G.gcie_solve_pencil(ctx, pen, spec["lo"], spec["hi"], **opts)
     lam = np.sort(ref["evals"])
     spacing = (lam[-1] - lam[0]) / max(len(lam) - 1, 1)
     pred = lam + np.random.default_rng(7).normal(0.0, noise * spacing, lam.size)
-    cts = G.gcie_kde_contours(pred, nmin=10, nmax=50, w=10.0)
+    if kind == "kde":
+        cts = G.gcie_kde_contours(pred, nmin=10, nmax=50, w=10.0)
+        info = {"nmin": 10, "nmax": 50, "w": 10.0}
+    else:
+        cts = G.gcie_plan_contours(pred, spec["lo"], spec["hi"], spec["contours"])
+        info = {"max_contours": spec["contours"]}
     edges = [spec["lo"]] + [c[1] for c in cts[:-1]] + [spec["hi"]]
     contours = [(0.5 * (a + b), 0.5 * (b - a), a, b) for a, b in zip(edges[:-1], edges[1:])]
     o = {k: v for k, v in opts.items() if k != "nuniform"}
     o.update(contours=contours, judge=1)
-    info = {"nmin": 10, "nmax": 50, "w": 10.0, "noise_spacings": noise, "edges": [float(e) for e in edges],
-            "predicted_counts": [int(c[4]) for c in cts]}
+    info.update(noise_spacings=noise, edges=[float(e) for e in edges], predicted_counts=[int(c[4]) for c in cts])
     return o, info
 
 
@@ -356,7 +363,7 @@ def main():
     spec, stats = r["spec"], r["stats"]
     ms_step = r["ms"] / args.steps
     value = r["count"] / (r["ms"] / 1e3)
-    metric = METRIC if args.contours == "uniform" else METRIC_KDE
+    metric = {"uniform": METRIC, "kde": METRIC_KDE, "planned": METRIC_PLANNED}[args.contours]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -402,7 +409,7 @@ def main():
            "gpu_launches": int(stats["total_launches"]),
            "clocks": r["clocks"], "e2e": r["e2e"]}
     if r["kde"] is not None:
-        out["config"]["kde"] = r["kde"] | {"resplits": r["last"]["resplits"],
+        out["config"]["predicted_contours"] = r["kde"] | {"resplits": r["last"]["resplits"],
                                            "count_estimate": [round(float(x), 2) for x in r["last"]["count_estimate"]]}
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
         v, tot, sample = oracle_sample(args, spec, *P.workload(args.workload)[:2], args.cpu_sample_seconds)

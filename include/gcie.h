@@ -201,6 +201,22 @@ void gcie_buffer_free(void *p);
 int gcie_kde_contours(const double *pred, int32_t npred, int32_t nmin, int32_t nmax, double w, double alpha,
                       double beta, gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout);
 
+/* Contours for a fixed budget: [lo, hi] is cut in gaps of the predicted spectrum until it has
+ * max_contours pieces (fewer when no piece can be cut).  While the budget is not reached, the piece
+ * with the most predictions in its closed interval [a, b] (leftmost on ties) is cut at the middle of
+ * the widest gap between consecutive sorted predictions of ranks k/4 .. k-1-k/4 (k in the piece;
+ * first such gap on ties), so each half keeps a quarter of them; a piece whose widest such gap is
+ * empty stops the planning.  This keeps the number of shifted systems fixed (the solve runs them all
+ * in one wave when it fits) and puts every boundary in a gap, where the quadrature filter converges
+ * fastest; Algorithm 2 instead fixes N_max per contour and lets the count follow.
+ * Contour i: c = (lo_i + hi_i)/2, r = (1 + alpha)(hi_i - lo_i)/2 (Section 4.2).  Host only.
+ *   pred: host, npred >= 0 finite predicted eigenvalues, any order (those outside [lo, hi] are ignored).
+ *   out, counts: host arrays of cap entries: the contours in ascending order and the predictions in
+ *   each closed interval.  *nout: number of contours (also set when cap is too small).
+ * Errors: GCIE_EINVAL for bad arguments or cap < *nout (nothing written then). */
+int gcie_plan_contours(const double *pred, int32_t npred, double lo, double hi, int32_t max_contours, double alpha,
+                       gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout);
+
 /* Count check of a finished contour (the judge of gcie_opts).  est is the stochastic trace estimate
  * of the number of eigenvalues the contour encloses, mean_l v_l^T (S_0)_l over the L columns of the
  * Gaussian starting block V (Section 2, CI eigensolvers: eigenvalue counts by stochastic trace

@@ -17,6 +17,8 @@ for Fast Large-Scale Generalized Eigensolvers"):
   basis, projection, reduced GEP, Ritz recovery and "keep lambda in I_k" (Algorithm 1), the
   subspace iteration of FEAST (Appendix A.3.3, U_{i+1} = orth(P_k U_i)) until the residual
   tolerance is met (Section 5.1 / Appendix B.2), and the merge/de-duplication across contours;
+* contours for a fixed budget (`plan_contours`): cuts of [lo, hi] in the widest gaps of a predicted
+  spectrum, the fullest piece first, until the budget is reached;
 * the count check of a contour (`trace_estimate`, `count_miss`, `resplit`): the stochastic trace
   estimate of the enclosed eigenvalue count (Section 2, CI eigensolvers) against the Ritz count,
   and the re-split of a contour that misses eigenvalues at a KDE cut (Algorithm 2).
@@ -353,6 +355,44 @@ def resplit(theta, c: float, R: float, s: float, e: float, w: float = 10.0):
                 t = tc
     infl = R / (0.5 * (e - s))
     return [(0.5 * (s + t), infl * 0.5 * (t - s), s, t), (0.5 * (t + e), infl * 0.5 * (e - t), t, e)]
+
+
+def plan_contours(pred, lo: float, hi: float, max_contours: int, alpha: float = 0.0):
+    """Contours for a fixed budget of contours: [lo, hi] is cut in gaps of the predicted spectrum
+    until it has max_contours pieces.  Algorithm 2 stops at N_max predictions per interval, so its
+    piece count follows from the spectrum, and its G_k with w = 10 is a third of the interval wide:
+    on an even spectrum it sees only the broad shape and cuts near the ends.  A GPU solve whose
+    shifted systems all run in one wave wants the count fixed instead, and FEAST converges fastest
+    when no eigenvalue lies near a circle, so the cut goes in the widest gap (the argmin of G_k in
+    the limit of a narrow kernel).  Reading: while fewer than max_contours pieces exist, the piece
+    with the most predictions in [a, b] (leftmost on ties) is cut at the middle of the widest gap
+    between consecutive predictions of ranks k // 4 .. k - 1 - k // 4 (k sorted predictions; first
+    such gap on ties), so each half keeps a quarter of them; a piece whose widest such gap is empty
+    (fewer than two distinct predictions) is not cut and planning stops.  Contour k: c = (a + b)/2,
+    r = (1 + alpha)(b - a)/2 (Section 4.2).  Returns a list of (lo, hi, c, r, count), ascending."""
+    p = np.sort(np.asarray(pred, dtype=np.float64))
+
+    def inside(a, b):
+        return p[(p >= a) & (p <= b)]
+
+    pieces = [(float(lo), float(hi))]
+    while len(pieces) < max_contours:
+        counts = [inside(a, b).size for a, b in pieces]
+        k = int(np.argmax(counts))
+        a, b = pieces[k]
+        q = inside(a, b)
+        m = q.size
+        if m < 2:
+            break
+        i0, i1 = m // 4, m - 1 - m // 4          # gaps q[i] .. q[i + 1] for i0 <= i < i1 (at least one)
+        i1 = max(i1, i0 + 1)
+        gaps = q[i0 + 1:i1 + 1] - q[i0:i1]
+        j = int(np.argmax(gaps))
+        if not gaps[j] > 0.0:
+            break
+        t = 0.5 * (q[i0 + j] + q[i0 + j + 1])
+        pieces[k:k + 1] = [(a, t), (t, b)]
+    return [(a, b, 0.5 * (a + b), (1.0 + alpha) * 0.5 * (b - a), int(inside(a, b).size)) for a, b in pieces]
 
 
 def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, nodes: int = 16,

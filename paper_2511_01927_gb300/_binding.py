@@ -17,7 +17,7 @@ MIXED, FP64 = 0, 1
 EXPORTED_SYMBOLS = [
     "gcie_create", "gcie_destroy", "gcie_default_opts", "gcie_strerror", "gcie_last_error", "gcie_get_stats",
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
-    "gcie_solve", "gcie_solve_pencil", "gcie_solve_batch", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
+    "gcie_solve", "gcie_solve_pencil", "gcie_solve_batch", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_plan_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
 ]
@@ -101,6 +101,7 @@ def lib():
         "gcie_buffer_free": (None, [vp]),
         "gcie_trapezoid_nodes": (C.c_int, [d, d, i32, vp, vp]),
         "gcie_kde_contours": (C.c_int, [vp, i32, i32, i32, d, d, d, vp, vp, i32, C.POINTER(i32)]),
+        "gcie_plan_contours": (C.c_int, [vp, i32, d, d, i32, d, vp, vp, i32, C.POINTER(i32)]),
         "gcie_count_miss": (C.c_int, [d, d, vp, vp, i32, d, d, i32, d, C.POINTER(i32)]),
         "gcie_resplit": (C.c_int, [vp, i32, C.POINTER(Contour), d, vp]),
         "gcie_shifted_spmm_f32": (C.c_int, [vp, vp, i32, vp, i32, vp, vp]),
@@ -318,6 +319,20 @@ def gcie_kde_contours(pred, nmin: int = 10, nmax: int = 50, w: float = 10.0, alp
     _check(lib().gcie_kde_contours(p.ctypes.data, int(p.size), int(nmin), int(nmax), float(w), float(alpha),
                                    float(beta), C.cast(out, C.c_void_p), counts.ctypes.data, cap, C.byref(n)),
            "gcie_kde_contours")
+    return [(out[i].lo, out[i].hi, out[i].c, out[i].r, int(counts[i])) for i in range(n.value)]
+
+
+def gcie_plan_contours(pred, lo: float, hi: float, max_contours: int, alpha: float = 0.0) -> list:
+    """Contours for a fixed budget, cut in gaps of the predicted spectrum; a list of
+    (lo, hi, c, r, count)."""
+    p = np.ascontiguousarray(np.asarray(pred, dtype=np.float64).ravel())
+    n = C.c_int32(0)
+    cap = max(1, int(max_contours))
+    out = (Contour * cap)()
+    counts = np.zeros(cap, dtype=np.int32)
+    _check(lib().gcie_plan_contours(p.ctypes.data if p.size else None, int(p.size), float(lo), float(hi),
+                                    int(max_contours), float(alpha), C.cast(out, C.c_void_p), counts.ctypes.data,
+                                    cap, C.byref(n)), "gcie_plan_contours")
     return [(out[i].lo, out[i].hi, out[i].c, out[i].r, int(counts[i])) for i in range(n.value)]
 
 

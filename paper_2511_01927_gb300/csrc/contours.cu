@@ -247,3 +247,68 @@ extern "C" int gcie_resplit(const double *theta, int32_t q, const gcie_contour *
     gcie::resplit(theta, q, *parent, w, out);
     return GCIE_OK;
 }
+
+extern "C" int gcie_plan_contours(const double *pred, int32_t npred, double lo, double hi, int32_t max_contours,
+                                  double alpha, gcie_contour *out, int32_t *counts, int32_t cap, int32_t *nout)
+{
+    using gcie::set_error;
+    if ((npred > 0 && !pred) || npred < 0 || !out || !counts || !nout || cap < 0) {
+        set_error("plan_contours: null pointer or bad size");
+        return GCIE_EINVAL;
+    }
+    if (!(lo < hi) || !std::isfinite(lo) || !std::isfinite(hi) || max_contours < 1 || !(alpha >= 0) ||
+        !std::isfinite(alpha)) {
+        set_error("plan_contours: need finite lo < hi, max_contours >= 1, alpha >= 0");
+        return GCIE_EINVAL;
+    }
+    std::vector<double> p(pred, pred + npred);
+    for (double v : p)
+        if (!std::isfinite(v)) { set_error("plan_contours: non-finite prediction"); return GCIE_EINVAL; }
+    std::sort(p.begin(), p.end());
+    // predictions in the closed piece [a, b] as the index range [i0, i1)
+    auto inside = [&](double a, double b) {
+        const size_t i0 = std::lower_bound(p.begin(), p.end(), a) - p.begin();
+        const size_t i1 = std::upper_bound(p.begin(), p.end(), b) - p.begin();
+        return std::make_pair(i0, std::max(i0, i1));
+    };
+    std::vector<std::pair<double, double>> pieces{{lo, hi}};
+    while ((int32_t)pieces.size() < max_contours) {
+        // the piece with the most predictions (leftmost on ties)
+        size_t k = 0, best = 0;
+        for (size_t i = 0; i < pieces.size(); ++i) {
+            const auto r = inside(pieces[i].first, pieces[i].second);
+            if (i == 0 || r.second - r.first > best) { best = r.second - r.first; k = i; }
+        }
+        const auto r = inside(pieces[k].first, pieces[k].second);
+        const size_t m = r.second - r.first;
+        if (m < 2) break;
+        const double *q = p.data() + r.first;
+        // widest gap q[i] .. q[i + 1] for ranks m/4 <= i < max(m - 1 - m/4, m/4 + 1) (first on ties)
+        const size_t g0 = m / 4, g1 = std::max(m - 1 - m / 4, g0 + 1);
+        size_t j = g0;
+        double wbest = q[g0 + 1] - q[g0];
+        for (size_t i = g0 + 1; i < g1; ++i)
+            if (q[i + 1] - q[i] > wbest) { wbest = q[i + 1] - q[i]; j = i; }
+        if (!(wbest > 0.0)) break;
+        const double t = 0.5 * (q[j] + q[j + 1]);
+        const double a = pieces[k].first, b = pieces[k].second;
+        pieces[k] = {a, t};
+        pieces.insert(pieces.begin() + k + 1, {t, b});
+    }
+    *nout = (int32_t)pieces.size();
+    if ((int32_t)pieces.size() > cap) {
+        set_error("plan_contours: output capacity " + std::to_string(cap) + " < " + std::to_string(pieces.size()) +
+                  " contours");
+        return GCIE_EINVAL;
+    }
+    for (size_t i = 0; i < pieces.size(); ++i) {
+        const double a = pieces[i].first, b = pieces[i].second;
+        out[i].lo = a;
+        out[i].hi = b;
+        out[i].c = 0.5 * (a + b);
+        out[i].r = (1.0 + alpha) * 0.5 * (b - a);
+        const auto rr = inside(a, b);
+        counts[i] = (int32_t)(rr.second - rr.first);
+    }
+    return GCIE_OK;
+}
