@@ -35,6 +35,7 @@ import pencils as P  # noqa: E402
 METRIC = "converged eigenpairs/s at residual<=1e-10 (uniform contours)"
 METRIC_KDE = "converged eigenpairs/s at residual<=1e-10 (KDE contours from a perturbed spectrum)"
 METRIC_PLANNED = "converged eigenpairs/s at residual<=1e-10 (gap-planned contours from a perturbed spectrum)"
+METRICS = {"uniform": METRIC, "kde": METRIC_KDE, "planned": METRIC_PLANNED}
 UNIT = "eigenpairs/s"
 
 
@@ -317,6 +318,13 @@ def oracle_sample(args, spec, K, M, seconds):
     return value, total, sample
 
 
+def workload_config(args, spec, n):
+    """The config keys both arms report: the workload and the solver configuration it is run with."""
+    return {"workload": args.workload, "n": int(n), "pairs_per_step": spec["count"], "contours": spec["contours"],
+            "nodes": spec["nodes"], "L": spec["L"], "moments": spec["moments"], "tol": 1e-10,
+            "l2": "inputs larger than L2 (16 GB block)", "contour_layout": args.contours}
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -348,10 +356,10 @@ def main():
             vals.append(v)
             secs.append(tot)
         value = float(np.mean(vals))
-        out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        out = {"impl": "reference", "metric": METRICS[args.contours], "value": value, "unit": UNIT, "n_gpus": args.gpus,
                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-               "data": "synthetic", "config": {"workload": args.workload},
+               "data": "synthetic", "config": workload_config(args, spec, K.n),
                "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
@@ -363,7 +371,7 @@ def main():
     spec, stats = r["spec"], r["stats"]
     ms_step = r["ms"] / args.steps
     value = r["count"] / (r["ms"] / 1e3)
-    metric = {"uniform": METRIC, "kde": METRIC_KDE, "planned": METRIC_PLANNED}[args.contours]
+    metric = METRICS[args.contours]
     peaks = {}
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -396,12 +404,9 @@ def main():
     out = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
-           "config": {"workload": args.workload, "n": int(r["K"].n), "pairs_per_step": spec["count"],
-                      "contours": spec["contours"], "nodes": spec["nodes"], "L": spec["L"],
-                      "moments": spec["moments"], "tol": 1e-10, "l2": "inputs larger than L2 (16 GB block)",
+           "config": workload_config(args, spec, r["K"].n) | {
                       "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
-                      "feast_iters_per_contour": r["last"]["iters"],
-                      "cocg_iters": r["last"]["cocg_iters"], "contour_layout": args.contours},
+                      "feast_iters_per_contour": r["last"]["iters"], "cocg_iters": r["last"]["cocg_iters"]},
            "roofline": roof,
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
                         "nameplate_frac": spmm_gbs / 8000.0},
