@@ -43,9 +43,15 @@ enum {
     GCIE_ENOMEM = 4,      /* device or host allocation failed, or the budget is too small */
     GCIE_ENOCONV = 5,     /* some contour did not reach the tolerance; converged pairs returned */
     GCIE_EBREAKDOWN = 6,  /* COCG breakdown (p^T A p = 0) that refinement could not recover */
-    GCIE_ETIMEOUT = 7,    /* a bounded device-side wait expired */
+    GCIE_ETIMEOUT = 7,    /* a bounded device-side wait expired (about one second of SM clock); the
+                             waiting CTAs let their copies in flight land and returned, and the
+                             context stays usable (see GCIE_ECONTEXT for when it does not) */
     GCIE_ECOUNT = 8,      /* returned count differs from a caller-supplied expected count */
-    GCIE_ECUDA = 9        /* CUDA runtime error */
+    GCIE_ECUDA = 9,       /* CUDA runtime error */
+    GCIE_ECONTEXT = 10    /* the context is unusable: after a bounded wait gave up, a bulk copy into
+                             shared memory could not be confirmed complete before its CTA exited
+                             (a second bounded wait ran out too); every later call on the context
+                             returns this code: destroy it and create a new one */
 };
 
 enum { GCIE_MIXED = 0, GCIE_FP64 = 1 };   /* precision of the shifted solves */
@@ -115,7 +121,9 @@ typedef struct {
     gcie_contour *contours;     /* ncontours: the final contours, each re-split one replaced in place
                                    by its two halves (ascending when the input was) */
     double *count_estimate;     /* ncontours: stochastic trace estimate of the enclosed eigenvalue
-                                   count (with judge = 1; NaN otherwise) */
+                                   count, from the contour's first FEAST iteration (formed whether or
+                                   not judge is on: a contour that stops on the stall rule is checked
+                                   against it) */
     int32_t resplits;           /* contours replaced by their halves */
 } gcie_result;
 
@@ -307,7 +315,9 @@ int gcie_jacobi_eig(gcie_ctx *ctx, int32_t p, double *d_A, double *d_w, double *
  *   p: 1..256; larger p returns GCIE_EINVAL ("exceeds the fixed workspace").
  *   d_A, d_w, d_V: as in gcie_jacobi_eig (device, caller-owned).
  * The first call on a device looks up the workspace's device address (once, with that device
- * current); make that first call before any stream capture.  All calls on a device share the
+ * current); make that first call before any stream capture.  The looked-up address is kept for the
+ * life of the process and is not refreshed after a device reset (cudaDeviceReset): do not call this
+ * entry point on a device that was reset after its first call.  All calls on a device share the
  * workspace, so calls that overlap on the GPU (other streams, other threads) race and must be
  * ordered by the caller. */
 int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, double *d_V);

@@ -35,6 +35,7 @@ Notation: the paper's A, B are K (stiffness, symmetric) and M (mass, SPD) here.
 """
 from __future__ import annotations
 
+import concurrent.futures as _cf
 import ctypes
 import os
 import subprocess
@@ -75,6 +76,27 @@ def _L():
 
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def host_threads() -> int:
+    """Host cores this process may run on (its CPU affinity set)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def node_map(fn, items, threads: int | None = None):
+    """[fn(x) for x in items], the items on separate host threads.  The quadrature nodes of a contour
+    are independent (Algorithm 1 solves them "in parallel"), and the C kernels run without Python's
+    lock, so each node's factorization and solves run on a core of their own; the arithmetic of
+    each item is exactly that of the serial loop."""
+    items = list(items)
+    t = min(len(items), threads or host_threads())
+    if t <= 1:
+        return [fn(x) for x in items]
+    with _cf.ThreadPoolExecutor(max_workers=t) as ex:
+        return list(ex.map(fn, items))
 
 
 # ----------------------------------------------------------------------------- matrices
@@ -398,7 +420,7 @@ def plan_contours(pred, lo: float, hi: float, max_contours: int, alpha: float = 
 def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, nodes: int = 16,
              moments_m: int = 2, tol: float = 1e-10, max_outer: int = 10, alpha: float = 0.0,
              contours=None, trace: dict | None = None, judge: bool = False, max_resplit: int = 3,
-             kde_w: float = 10.0):
+             kde_w: float = 10.0, threads: int | None = None):
     """The CI eigensolver of Algorithm 1 with the moment method and FEAST outer iterations.
 
     For each contour (c, R) enclosing I_k = [s, e]:
@@ -414,6 +436,7 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
     `max_resplit` levels; at the last level it keeps its pairs and reports non-convergence).
     Then merge/dedup across contours.  V is the random block (n x L) drawn by the caller.
     `trace`, if given, receives per-contour intermediates of iteration 0 (nodes, S, Q, theta).
+    `threads`: host threads for the nodes of a contour (default: every core of the affinity set).
     Returns dict(evals, evecs, resid, contour_of, outer_iters, status, contours, estimates,
     resplits); contour_of indexes the final contours."""
     Ks, Ms = as_scipy(K), as_scipy(M)
@@ -427,13 +450,13 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
     while work:
         (c, R, s, e), depth = work.pop(0)
         z, w = trapezoid_nodes(c, R, nodes)
-        solvers = [ShiftedSolver(Ks, Ms, zj, bw) for zj in z]
+        solvers = node_map(lambda zj: ShiftedSolver(Ks, Ms, zj, bw), z, threads)
         Vk = np.asarray(V, dtype=np.float64)
         m = moments_m
         ok = False
         for it in range(max_outer):
             B = Ms @ Vk
-            X = [sv.solve(B) for sv in solvers]
+            X = node_map(lambda sv: sv.solve(B), solvers, threads)
             S = moments(X, z, w, c, R, m)
             if it == 0:
                 est, se = trace_estimate(Vk, S[0])

@@ -11,7 +11,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libgcie.so")
 
 STATUS = {0: "GCIE_OK", 1: "GCIE_EINVAL", 2: "GCIE_ENOTSYM", 3: "GCIE_ENOTSPD", 4: "GCIE_ENOMEM",
-          5: "GCIE_ENOCONV", 6: "GCIE_EBREAKDOWN", 7: "GCIE_ETIMEOUT", 8: "GCIE_ECOUNT", 9: "GCIE_ECUDA"}
+          5: "GCIE_ENOCONV", 6: "GCIE_EBREAKDOWN", 7: "GCIE_ETIMEOUT", 8: "GCIE_ECOUNT", 9: "GCIE_ECUDA",
+          10: "GCIE_ECONTEXT"}
 MIXED, FP64 = 0, 1
 
 EXPORTED_SYMBOLS = [

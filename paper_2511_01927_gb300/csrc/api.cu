@@ -216,6 +216,7 @@ const char *gcie_strerror(int code)
     case GCIE_ETIMEOUT: return "device wait timed out";
     case GCIE_ECOUNT: return "eigenvalue count mismatch";
     case GCIE_ECUDA: return "CUDA error";
+    case GCIE_ECONTEXT: return "context unusable";
     default: return "unknown status";
     }
 }
@@ -336,6 +337,7 @@ void gcie_reset_stats(gcie_ctx *c)
 
 int gcie_pencil_create(gcie_ctx *c, const gcie_csr *K, const gcie_csr *M, gcie_pencil **out)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !out) { set_error("gcie_pencil_create: null argument"); return GCIE_EINVAL; }
     *out = nullptr;
     GCIE_TRY(check_csr(K, "K"));
@@ -492,6 +494,7 @@ static int upload_shifts(gcie_ctx *c, int nshift, const double *h_z, double2 **d
 int gcie_shifted_spmm_f32(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const float *d_P,
                           float *d_Q)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !h_z || !d_P || !d_Q || nshift < 0 || ncol <= 0) { set_error("spmm_f32: bad argument"); return GCIE_EINVAL; }
     double2 *dz = nullptr;
     GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
@@ -505,6 +508,7 @@ int gcie_shifted_spmm_f32(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const dou
 int gcie_shifted_spmm_f64(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double *h_z, int32_t ncol, const double *d_P,
                           double *d_Q)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !h_z || !d_P || !d_Q || nshift < 0 || ncol <= 0) { set_error("spmm_f64: bad argument"); return GCIE_EINVAL; }
     double2 *dz = nullptr;
     GCIE_TRY(upload_shifts(c, nshift, h_z, &dz));
@@ -519,6 +523,7 @@ int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double
                        double *d_X, int32_t x0, double lin_tol, int32_t max_iters, int32_t precision, int32_t precond,
                        int64_t *h_iters)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !h_z || !d_B || !d_X || nshift <= 0 || ncol <= 0 || !(lin_tol > 0) || max_iters < 0) {
         set_error("shifted_solve: bad argument");
         return GCIE_EINVAL;
@@ -538,6 +543,7 @@ int gcie_shifted_solve(gcie_ctx *c, gcie_pencil *p, int32_t nshift, const double
 int gcie_moments(gcie_ctx *c, int64_t n, int32_t nshift, const double *h_z, const double *h_w, double cc, double r,
                  int32_t m, int32_t ncol, const double *d_X, double *d_S)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !h_z || !h_w || !d_X || !d_S || n <= 0 || nshift <= 0 || m < 1 || m > 8 || ncol <= 0 || !(r > 0)) {
         set_error("moments: bad argument");
         return GCIE_EINVAL;
@@ -562,6 +568,7 @@ int gcie_moments(gcie_ctx *c, int64_t n, int32_t nshift, const double *h_z, cons
 int gcie_m_orthonormalize(gcie_ctx *c, gcie_pencil *p, int32_t ncolY, const double *d_Y, double drop, double *d_Q,
                           int32_t *h_rank)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !d_Y || !d_Q || ncolY <= 0 || ncolY > 256 || !(drop >= 0)) { set_error("m_orthonormalize: bad argument"); return GCIE_EINVAL; }
     int rank = 0;
     int rc = m_orthonormalize(c, p, p->n, ncolY, d_Y, drop, d_Q, &rank);
@@ -574,6 +581,7 @@ int gcie_m_orthonormalize(gcie_ctx *c, gcie_pencil *p, int32_t ncolY, const doub
 int gcie_rayleigh_ritz(gcie_ctx *c, gcie_pencil *p, int32_t q, const double *d_Q, double *d_Z, double *h_theta,
                        double *h_res)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !d_Q || !d_Z || !h_theta || !h_res || q <= 0 || q > 256) { set_error("rayleigh_ritz: bad argument"); return GCIE_EINVAL; }
     return rayleigh_ritz(c, p, q, d_Q, d_Z, h_theta, h_res);
 }
@@ -585,6 +593,7 @@ int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, d
 
 int gcie_jacobi_eig(gcie_ctx *c, int32_t p, double *d_A, double *d_w, double *d_V)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !d_A || !d_w || !d_V || p <= 0 || p > 1024) { set_error("jacobi: bad argument"); return GCIE_EINVAL; }
     int rc = jacobi(c, 1, p, d_A, d_w, d_V);
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -952,7 +961,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                         for (int k = 0; k < m; ++k) { coef[(size_t)j * m + k] = cmul(ww[bi][j], pw); pw = cmul(pw, sn); }
                     }
                     GCIE_TRY(moments(c, n, half, coef.data(), m, ncol, dX + (size_t)bi * half * n * ncol, Yb[bi], pY));
-                    if (o->judge && it == 0) GCIE_TRY(trace_estimate(c, n, L0, dV0, L, Yb[bi], pY, &s.est, &s.se));
+                    // the trace estimate of the enclosed count: the judge of opts.judge, and the check
+                    // of a contour that stops on the stall rule below (always formed: one pass over V, S_0)
+                    if (it == 0) GCIE_TRY(trace_estimate(c, n, L0, dV0, L, Yb[bi], pY, &s.est, &s.se));
                 }
                 mark("moments");
                 GCIE_TRY(m_orthonormalize_batch(c, p, n, nb, pYb.data(), Yb.data(), 1e-14, Qb.data(), rankb.data()));
@@ -1007,11 +1018,14 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     }
                     // An iteration that adds no converged pair and does not improve the worst remaining
                     // residual 10x leaves only Ritz values that do not converge: spurious ones, built from
-                    // basis directions dominated by solve noise, which move from one iteration to the next.
-                    // The contour stops; remaining residuals above 1e-6 are taken as spurious (status OK),
-                    // lower ones as a stalled eigenpair (GCIE_ENOCONV).
-                    // The same holds as soon as every unconverged value is a wanderer: a true eigenpair
-                    // keeps its Ritz value in place from one iteration to the next.
+                    // basis directions dominated by solve noise, which move from one iteration to the next,
+                    // or a true eigenpair that converges too slowly.  The same holds as soon as every
+                    // unconverged value is a wanderer (a true eigenpair keeps its Ritz value in place from
+                    // one iteration to the next).  The contour stops; residuals at or below 1e-6 mean a
+                    // stalled eigenpair (GCIE_ENOCONV); above 1e-6 the values count as spurious only when
+                    // the count check agrees (the trace estimate of the enclosed count exceeds the
+                    // converged pairs by no more than gcie_count_miss allows, and the basis has a spare
+                    // direction), otherwise the contour reports GCIE_ENOCONV.
                     bool stalled = false;
                     if (unconverged_inside && it > 0 && (int)keep.size() <= s.prev_conv && worst >= 0.1 * s.prev_worst)
                         stalled = true;
@@ -1060,7 +1074,13 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                             for (int l : keep) { s.kv.push_back(th[l]); s.kr.push_back(rs[l]); }
                         }
                         s.done = true;
-                        s.status = (unconverged_inside && !(stalled && worst > 1e-6)) ? GCIE_ENOCONV : GCIE_OK;
+                        if (!unconverged_inside)
+                            s.status = GCIE_OK;
+                        else if (stalled && worst > 1e-6)
+                            s.status = count_miss(s.est, s.se, th.data(), rs.data(), rank, s.c, s.r, rank, o->tol)
+                                           ? GCIE_ENOCONV : GCIE_OK;
+                        else
+                            s.status = GCIE_ENOCONV;
                         ctx_free(c, Z);
                         if (s.Z) { ctx_free(c, s.Z); s.Z = nullptr; }
                     } else {
@@ -1255,6 +1275,7 @@ extern "C" {
 
 int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const gcie_opts *opts, gcie_result *out)
 {
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     if (!c || !p || !out) { set_error("solve: null argument"); return GCIE_EINVAL; }
     std::memset(out, 0, sizeof(*out));
     gcie_opts o;

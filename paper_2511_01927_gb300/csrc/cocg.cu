@@ -787,14 +787,19 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
                                   bandAB, info);
     if (bandAB) {
         ctx_free(c, bandAB);
-        // the band sweeps give up (and count it) when an asynchronous copy never completes
-        unsigned int to = 0;
-        if (cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        // the band sweeps give up (and count it) when an asynchronous copy never completes; a CTA that
+        // could not confirm its copies landed before it exited leaves the context unusable
+        unsigned int to[2] = {0, 0};   // wait_timeouts, drain_timeouts (adjacent in DbgRec)
+        if (cudaMemcpyAsync(to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
             cudaStreamSynchronize(c->stream) != cudaSuccess) {
             set_error("cocg: status read failed");
             rc = GCIE_ECUDA;
-        } else if (to) {
-            cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(to), c->stream);
+        } else if (to[1]) {
+            c->unusable = true;
+            set_error("band sweep: a bulk copy could not be confirmed complete; destroy and recreate the context");
+            rc = GCIE_ECONTEXT;
+        } else if (to[0]) {
+            cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(unsigned int), c->stream);
             set_error("band sweep: an asynchronous copy did not complete in time");
             rc = GCIE_ETIMEOUT;
         }

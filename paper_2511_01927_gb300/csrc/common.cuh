@@ -37,6 +37,7 @@ struct DbgRec {
     unsigned long long count;
     long long tag, idx, bound;
     unsigned int wait_timeouts;   // bounded waits that gave up (any build); checked after each solve
+    unsigned int drain_timeouts;  // of those, CTAs whose copies in flight could not be confirmed landed
 };
 #ifdef GCIE_CHECKED
 __device__ __forceinline__ bool gchk(DbgRec *d, long long idx, long long bound, int tag)
@@ -91,6 +92,7 @@ struct Ctx {
     cudaMemPool_t pool = nullptr;    // stream-ordered pool of the solve-time buffers
     void *h_stage = nullptr;         // pinned host staging for results copied out (grown on demand)
     size_t h_stage_bytes = 0;
+    bool unusable = false;           // set after a drain timeout (GCIE_ECONTEXT): every later call fails
 };
 
 // Stream-ordered allocation from the context's pool.  The pool keeps what it has reserved between

@@ -654,6 +654,22 @@ int jacobi_noalloc(cudaStream_t stream, int p, double *A, double *w, double *V)
     GCIE_TRY(jacobi_static_setup(dev, &ws, &dbg));
     k_jacobi<<<1, 1024, 0, stream>>>(p, A, w, V, ws, 1e-15, 60, dbg);
     GCIE_CUDA_TRY(cudaGetLastError());
+#ifdef GCIE_CHECKED
+    {
+        // checked builds: read back the index record of this call (the fixed array's own), report and
+        // clear a violation; only these builds synchronise the stream here
+        DbgRec h{};
+        GCIE_CUDA_TRY(cudaStreamSynchronize(stream));
+        GCIE_CUDA_TRY(cudaMemcpy(&h, dbg, sizeof(h), cudaMemcpyDeviceToHost));
+        if (h.count) {
+            const DbgRec z{};
+            cudaMemcpy(dbg, &z, sizeof(z), cudaMemcpyHostToDevice);
+            set_error("jacobi_noalloc: " + std::to_string(h.count) + " index violations, first tag " + std::to_string(h.tag) +
+                      " index " + std::to_string(h.idx) + " bound " + std::to_string(h.bound));
+            return GCIE_ECUDA;
+        }
+    }
+#endif
     return GCIE_OK;
 }
 

@@ -463,10 +463,14 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         return ok;
     };
     // after a failed wait: record it, let the bulk copies still in flight land (bounded), leave
+    // (a copy that did not land within that second bound may still write this CTA's shared memory after
+    //  it exits: counted apart, the host then marks the context unusable)
     auto give_up = [&]() {
         if (tid == 0) atomicAdd(&dbg->wait_timeouts, 1u);
-        if (pend0) mbar_wait(&bars[0], uses0 & 1);
-        if (pend1) mbar_wait(&bars[1], uses1 & 1);
+        bool drained = true;
+        if (pend0) drained = mbar_wait(&bars[0], uses0 & 1) && drained;
+        if (pend1) drained = mbar_wait(&bars[1], uses1 & 1) && drained;
+        if (tid == 0 && !drained) atomicAdd(&dbg->drain_timeouts, 1u);
         cp_async_wait_all();
     };
 

@@ -20,7 +20,7 @@ import numpy as np
 import scipy.sparse as sp
 
 __all__ = [
-    "Csr", "fem1d", "fem2d_p1", "grf_lognormal", "fem2d_p1_lognormal", "fem_q1",
+    "Csr", "fem1d", "fem2d_p1", "fem2d_p1_rect", "fem2d_p1_strip", "grf_lognormal", "fem2d_p1_lognormal", "fem_q1",
     "octant_coefficients", "gaussian_block", "fem1d_eigenvalue", "workload", "WORKLOADS",
 ]
 
@@ -104,17 +104,24 @@ def fem2d_p1(nc: int, kappa=None, rho=None) -> tuple[Csr, Csr]:
     with kappa, rho constant per cell (both triangles of a cell share the value).  The
     hypotenuse couplings of K vanish exactly for right isosceles triangles, so K has the
     5-point pattern and M the 7-point pattern."""
+    return fem2d_p1_rect(nc, nc, kappa, rho)
+
+
+def fem2d_p1_rect(nci: int, ncj: int, kappa=None, rho=None) -> tuple[Csr, Csr]:
+    """The same P1 discretisation on a rectangle of nci x ncj square cells of side h = 1/max(nci, ncj)
+    (kappa, rho of shape (nci, ncj)); n = (nci-1)(ncj-1) interior nodes numbered with j fastest
+    (index = (i-1)(ncj-1) + (j-1)), so the bandwidth is ncj (the diagonal neighbour (i+1, j+1))."""
     if kappa is None:
-        kappa = np.ones((nc, nc))
+        kappa = np.ones((nci, ncj))
     if rho is None:
-        rho = np.ones((nc, nc))
-    h = 1.0 / nc
-    N1 = nc + 1
-    I, J = np.meshgrid(np.arange(nc), np.arange(nc), indexing="ij")
-    a = I * N1 + J
-    b = (I + 1) * N1 + J
-    c = (I + 1) * N1 + (J + 1)
-    d = I * N1 + (J + 1)
+        rho = np.ones((nci, ncj))
+    h = 1.0 / max(nci, ncj)
+    Nj = ncj + 1
+    I, J = np.meshgrid(np.arange(nci), np.arange(ncj), indexing="ij")
+    a = I * Nj + J
+    b = (I + 1) * Nj + J
+    c = (I + 1) * Nj + (J + 1)
+    d = I * Nj + (J + 1)
     # triangle (a, b, c): right angle at b; triangle (a, c, d): right angle at d
     k1 = np.array([[0.5, -0.5, 0.0], [-0.5, 1.0, -0.5], [0.0, -0.5, 0.5]])
     k2 = np.array([[0.5, 0.0, -0.5], [0.0, 0.5, -0.5], [-0.5, -0.5, 1.0]])
@@ -129,14 +136,23 @@ def fem2d_p1(nc: int, kappa=None, rho=None) -> tuple[Csr, Csr]:
                 mv.append((rho * ml[p, q]).ravel())
     rows = np.concatenate(rows)
     cols = np.concatenate(cols)
-    nt = N1 * N1
+    nt = (nci + 1) * Nj
     K = sp.csr_matrix((np.concatenate(kv), (rows, cols)), shape=(nt, nt))
     M = sp.csr_matrix((np.concatenate(mv), (rows, cols)), shape=(nt, nt))
-    ii, jj = np.meshgrid(np.arange(N1), np.arange(N1), indexing="ij")
-    keep = np.nonzero(((ii > 0) & (ii < nc) & (jj > 0) & (jj < nc)).ravel())[0]
+    ii, jj = np.meshgrid(np.arange(nci + 1), np.arange(Nj), indexing="ij")
+    keep = np.nonzero(((ii > 0) & (ii < nci) & (jj > 0) & (jj < ncj)).ravel())[0]
     K = K[keep][:, keep]
     M = M[keep][:, keep]
     return Csr.from_scipy(K), Csr.from_scipy(M)
+
+
+def fem2d_p1_strip(nci: int, ncj: int, seeds=(2, 3), sigma: float = 1.0, ell: float = 0.1):
+    """A strip of the 2D log-normal P1 family: the first nci rows of cells of the ncj x ncj field's
+    grid (same covariance, spacing 1/ncj), so its bandwidth is that of the ncj x ncj pencil (ncj)
+    while n = (nci - 1)(ncj - 1) stays small."""
+    kappa = grf_lognormal(ncj, ell, sigma, seeds[0])[:nci]
+    rho = grf_lognormal(ncj, ell, sigma, seeds[1])[:nci]
+    return fem2d_p1_rect(nci, ncj, kappa, rho)
 
 
 def fem2d_p1_lognormal(nc: int, seeds=(2, 3), sigma: float = 1.0, ell: float = 0.1):
@@ -232,6 +248,10 @@ WORKLOADS = {
     # Smaller members of the same 2D family (parity sizes the oracle finishes in seconds).
     "fem2d-p1-40": dict(kind="fem2d", nc=40, seeds=(2, 3), first=11, last=60, contours=2, nodes=16,
                         L=32, moments=2, golden="fem2d_p1_40.json"),
+    # A strip of the 500 x 500 family (12 x 500 cells, n = 11 x 499 = 5489) with the bench workload's
+    # bandwidth (500): parity of the band kernels at full bandwidth, eigenvalues 21..60.
+    "fem2d-p1-strip": dict(kind="fem2d_strip", nci=12, ncj=500, seeds=(2, 3), first=21, last=60, contours=2,
+                           nodes=16, L=32, moments=2, golden="fem2d_p1_strip.json"),
 }
 
 
@@ -246,8 +266,11 @@ def workload(name: str):
         spec["lo"] = 0.5 * (lam[f - 2] + lam[f - 1])
         spec["hi"] = 0.5 * (lam[l - 1] + lam[l])
         spec["count"] = l - f + 1
-    elif spec["kind"] == "fem2d":
-        K, M = fem2d_p1_lognormal(spec["nc"], spec["seeds"])
+    elif spec["kind"] in ("fem2d", "fem2d_strip"):
+        if spec["kind"] == "fem2d":
+            K, M = fem2d_p1_lognormal(spec["nc"], spec["seeds"])
+        else:
+            K, M = fem2d_p1_strip(spec["nci"], spec["ncj"], spec["seeds"])
         g = spec.get("golden")
         if g and os.path.exists(os.path.join(_GOLDEN, g)):
             with open(os.path.join(_GOLDEN, g)) as fh:

@@ -153,14 +153,37 @@ def test_band_lu_pivoting_needed():
     assert np.max(np.abs(A @ x - b)) < 1e-13
 
 
-def test_shifted_apply_definition():
-    K, M = P.fem1d(30)
+def test_shifted_apply_closed_form_modes():
+    """Closed form on the 1D pencil: the sine modes x_k(i) = sin(k pi i h) satisfy K x_k = lambda_k M x_k
+    and M x_k = (h/6)(4 + 2 cos(k pi h)) x_k, so (z M - K) x_k = (z - lambda_k)(h/6)(4 + 2 cos(k pi h)) x_k
+    for every complex z.  A block of complex combinations of modes pins the sign of the operator
+    (z M - K, not K - z M), that z enters unconjugated, and that P is not conjugated."""
+    n = 30
+    K, M = P.fem1d(n)
+    h = 1.0 / (n + 1)
+    ks = np.array([1, 4, 9, 17])
+    X = np.sin(np.outer(np.arange(1, n + 1), ks) * np.pi * h)
+    lam = P.fem1d_eigenvalue(ks, n)
+    mu = (h / 6.0) * (4.0 + 2.0 * np.cos(ks * np.pi * h))
     rng = np.random.default_rng(1)
-    Pm = rng.standard_normal((30, 3)) + 1j * rng.standard_normal((30, 3))
-    z = 2.0 - 7.0j
-    Q = O.shifted_apply(K, M, z, Pm)
-    dense = z * M.to_scipy().toarray() - K.to_scipy().toarray()
-    assert np.max(np.abs(Q - dense @ Pm)) < 1e-12
+    A = rng.standard_normal((ks.size, 3)) + 1j * rng.standard_normal((ks.size, 3))
+    Pm = X @ A
+    for z in (2.0 - 7.0j, -3.0 + 1e3j, 5e3 + 0.5j):
+        Q = O.shifted_apply(K, M, z, Pm)
+        expect = X @ (((z - lam) * mu)[:, None] * A)
+        assert np.max(np.abs(Q - expect)) <= 1e-10 * np.max(np.abs(expect))
+
+
+def test_norm1_hand_values():
+    """||K||_1 of the 1D stiffness tridiag(-1, 2, -1)/h is 4/h = 4(n + 1) (interior columns), of the
+    mass (h/6) tridiag(1, 4, 1) it is h; on a non-symmetric 2 x 2 it is the largest column sum (8),
+    not the largest row sum (6)."""
+    n = 30
+    K, M = P.fem1d(n)
+    assert abs(O.norm1(K) - 4.0 * (n + 1)) <= 1e-12 * 4.0 * (n + 1)
+    assert abs(O.norm1(M) - 1.0 / (n + 1)) <= 1e-15
+    import scipy.sparse as sps
+    assert O.norm1(sps.csr_matrix(np.array([[1.0, -5.0], [2.0, 3.0]]))) == 8.0
 
 
 # --------------------------------------------------------------------------- nodes, weights, moments
@@ -273,7 +296,8 @@ def test_residual_definition_scaling():
     assert abs(O.residuals(K, M, lam, 7.0 * X)[0] - r_exact) < 1e-14
     r_bad = O.residuals(K, M, lam * (1 + 1e-6), X)[0]
     Ms, Ks = M.to_scipy(), K.to_scipy()
-    expect = np.linalg.norm(lam[0] * 1e-6 * (Ms @ X[:, 0])) / (O.norm1(Ks) * np.linalg.norm(X[:, 0]))
+    # ||K||_1 = 4 (n + 1) for the 1D stiffness (hand value, see test_norm1_hand_values)
+    expect = np.linalg.norm(lam[0] * 1e-6 * (Ms @ X[:, 0])) / (4.0 * (n + 1) * np.linalg.norm(X[:, 0]))
     assert abs(r_bad - expect) < 1e-3 * expect
 
 

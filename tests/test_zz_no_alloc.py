@@ -35,7 +35,8 @@ def test_noalloc_matches_regular_entry_twice(G):
     ctx = G.gcie_create(0)
     try:
         stream = torch.cuda.current_stream()
-        for p, seed in ((128, 1), (37, 2)):           # two calls in a row, different sizes
+        # calls in a row, different sizes: the whole fixed array (p = 256), a middle size, one element
+        for p, seed in ((256, 3), (128, 1), (37, 2), (1, 4)):
             A = sym(p, seed)
             nA = np.linalg.norm(A)
             outs = []
