@@ -4,15 +4,19 @@ pencil of a 500 x 500 grid (n = 249001, log-normal coefficient fields in K and M
 FP64 refinement, residual tolerance 1e-10.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload NAME]
-                    [--contours uniform|kde|planned [--pred-noise S]]
+                    [--contours uniform|kde|planned [--pred-noise S]] [--precision mixed|fp64]
 
 One step = one complete solve (ingested pencil resident on the GPU; every step repeats the shifted
 solves, moments, basis, Rayleigh-Ritz and merge).  `--contours kde` times the same workload with
 contours from Algorithm 2 instead, `--contours planned` with as many contours as the uniform layout
 cut in the widest gaps (gcie_plan_contours): the predicted spectrum is the solver's own eigenvalues
 of an untimed uniform solve plus seeded Gaussian noise of S mean spacings (a stand-in for a trained
-predictor, at its best), the solve runs with the count check on.  Prints one JSON line on rank 0.  Under torchrun
-each rank solves its own replica of the workload (independent problems, no collective).
+predictor, at its best), the solve runs with the count check on.  `--precision fp64` runs the COCG
+recurrences, SpMM and refinement in FP64 (the band factors stay FP32): the in-box FP64 comparator.
+The timed steps run without per-launch events; one extra profiled step after them gives the
+per-kernel times of the roofline.  The CPU baseline is the oracle's whole solve of a reduced member
+(160 x 160) on the host cores.  Prints one JSON line on rank 0.  Under torchrun each rank solves its
+own replica of the workload (independent problems, no collective).
 """
 from __future__ import annotations
 
@@ -46,9 +50,11 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fem2d-p1-500")
-    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--contours", default="uniform", choices=["uniform", "kde", "planned"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
+                    help="shifted solves: FP32 COCG with FP64 refinement (mixed) or FP64 COCG (fp64); both "
+                         "with the FP32 band factors as preconditioner")
     ap.add_argument("--pred-noise", type=float, default=0.1,
                     help="with --contours kde|planned: noise of the predicted spectrum in mean eigenvalue spacings")
     ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",
@@ -127,9 +133,9 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- our path
-def solver_opts(spec, V):
+def solver_opts(spec, V, precision="mixed"):
     return dict(nodes=spec["nodes"], moments=spec["moments"], nuniform=spec["contours"], V0=V, tol=1e-10,
-                lin_tol=1e-11, expected_count=spec["count"])
+                lin_tol=1e-11, expected_count=spec["count"], precision=0 if precision == "mixed" else 1)
 
 
 def run_ours(args, rank, world):
@@ -145,7 +151,7 @@ def run_ours(args, rank, world):
     stream = torch.cuda.current_stream()
     ctx = G.gcie_create(dev, stream.cuda_stream)
     pen = G.gcie_pencil_create(ctx, K, M)
-    opts = solver_opts(spec, V)
+    opts = solver_opts(spec, V, args.precision)
     kde = None
     if args.contours != "uniform":
         opts, kde = predicted_opts(G, ctx, pen, spec, opts, args.pred_noise, args.contours)
@@ -168,12 +174,17 @@ def run_ours(args, rank, world):
     count = 0
     last = None
     for _ in range(args.steps):
-        last = step(True)
+        last = step(False)
         count += len(last["evals"])
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    launches = int(G.gcie_get_stats(ctx)["total_launches"])
+    # one more step, after the timed region, with every launch timed by CUDA events on the library's
+    # stream: the per-kernel-class times of the roofline (the timed steps run without those events)
+    G.gcie_reset_stats(ctx)
+    step(True)
     stats = G.gcie_get_stats(ctx)
     if world > 1:
         ms, count = reduce_over_ranks(ms, count, "cuda")
@@ -184,8 +195,9 @@ def run_ours(args, rank, world):
     e2e = e2e_measure(G, ctx, K, M, spec, opts, args.steps)
     G.gcie_pencil_destroy(pen)
     G.gcie_destroy(ctx)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
     return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e,
-                kde=kde)
+                kde=kde, launches=launches, sms=sms)
 
 
 def predicted_opts(G, ctx, pen, spec, opts, noise, kind):
@@ -281,41 +293,33 @@ def e2e_measure(G, ctx, K, M, spec, opts, steps):
 
 
 # ----------------------------------------------------------------------------- CPU oracle baseline
-def oracle_sample(args, spec, K, M, seconds):
-    """The oracle on a bounded sample of the workload: its banded LU of one shifted matrix on the leading
-    rows of the pencil (cost linear in the rows at fixed bandwidth), timed on this host, extrapolated to
-    the full solve: (n / rows) x (factor + solve with L right-hand sides) per node x nodes x contours
-    x 2 FEAST passes (the second with twice the columns), plus nothing for the dense steps (a lower bound
-    on the oracle's time, so an upper bound on its eigenpairs/s)."""
-    import scipy.sparse as sp
+REDUCED = "fem2d-p1-160"   # the reduced member of the 500 x 500 workload the oracle solves whole
+
+
+def oracle_solve(contour_index=None):
+    """The oracle's whole CI solve (every step of Algorithm 1 with FEAST, dense steps included) of the
+    reduced member of the workload's family: 160 x 160 cells (n = 25281, bandwidth 160), eigenvalues
+    11..40, the workload's solver configuration (8 uniform contours x 16 nodes, L = 64, 2 moments), on
+    the host cores (contours and nodes on separate threads).  contour_index: only that contour (the
+    reference arm's bounded step).  Returns (pairs, seconds, threads, sample description)."""
     import oracle as O
 
-    Ks, Ms = K.to_scipy(), M.to_scipy()
-    bw = O.bandwidth(Ks, Ms)
-    c = 0.5 * (spec["lo"] + spec["hi"])
-    R = 0.5 * (spec["hi"] - spec["lo"]) / spec["contours"]
-    z = O.trapezoid_nodes(c, R, spec["nodes"])[0][0]
-    rows = max(4 * bw, 2000)
-    while True:
-        Ksub, Msub = Ks[:rows, :rows], Ms[:rows, :rows]
-        B = (Msub @ P.gaussian_block(rows, spec["L"], 1)).astype(complex)
-        t0 = time.perf_counter()
-        sv = O.ShiftedSolver(Ksub, Msub, z, bw)
-        t1 = time.perf_counter()
-        sv.solve(B)
-        sv.solve(np.concatenate([B, B], axis=1))
-        t2 = time.perf_counter()
-        if t2 - t0 >= 0.2 * seconds or rows >= K.n:
-            break
-        rows = min(K.n, int(rows * max(2.0, 0.25 * seconds / max(t2 - t0, 1e-3))))
-    per_node = (t2 - t0) * K.n / rows
-    nodes_total = spec["contours"] * spec["nodes"] // 2
-    total = per_node * nodes_total
-    value = spec["count"] / total
-    sample = (f"oracle banded LU (bandwidth {bw}) of z M - K on the leading {rows} of {K.n} rows, one node, "
-              f"factor + solves with L and 2L right-hand sides ({t2 - t0:.1f} s), scaled by n/rows and by "
-              f"{nodes_total} nodes; dense steps not counted")
-    return value, total, sample
+    K, M, spec = P.workload(REDUCED)
+    V = P.gaussian_block(K.n, spec["L"], 1)
+    cts = O.uniform_contours(spec["lo"], spec["hi"], spec["contours"])
+    if contour_index is not None:
+        cts = [cts[contour_index % len(cts)]]
+    cores = O.host_threads()
+    t0 = time.perf_counter()
+    r = O.ci_solve(K, M, spec["lo"], spec["hi"], V, contours=cts, nodes=spec["nodes"], moments_m=spec["moments"],
+                   tol=1e-10, threads=cores)
+    sec = time.perf_counter() - t0
+    used = min(cores, len(cts) * spec["nodes"] // 2)
+    what = "whole solve" if contour_index is None else f"contour {contour_index % spec['contours']} of 8"
+    sample = (f"oracle CI solve ({what}) of the reduced member {REDUCED}: n = {K.n}, bandwidth "
+              f"{O.bandwidth(K, M)}, eigenvalues 11..40, 8 uniform contours x 16 nodes, L = 64, 2 moments, banded LU "
+              f"per node, dense steps included, {used} host threads; {len(r['evals'])} pairs in {sec:.1f} s")
+    return len(r["evals"]), sec, used, sample
 
 
 def workload_config(args, spec, n):
@@ -323,13 +327,6 @@ def workload_config(args, spec, n):
     return {"workload": args.workload, "n": int(n), "pairs_per_step": spec["count"], "contours": spec["contours"],
             "nodes": spec["nodes"], "L": spec["L"], "moments": spec["moments"], "tol": 1e-10,
             "l2": "inputs larger than L2 (16 GB block)", "contour_layout": args.contours}
-
-
-def cpu_cores():
-    try:
-        return len(os.sched_getaffinity(0))
-    except AttributeError:
-        return os.cpu_count() or 1
 
 
 # ----------------------------------------------------------------------------- main
@@ -347,20 +344,24 @@ def main():
         if rank != 0:
             return
         K, M, spec = P.workload(args.workload)
-        vals, secs = [], []
-        for _ in range(args.warmup):
-            oracle_sample(args, spec, K, M, args.cpu_sample_seconds)
-        sample = ""
-        for _ in range(args.steps):
-            v, tot, sample = oracle_sample(args, spec, K, M, args.cpu_sample_seconds)
-            vals.append(v)
-            secs.append(tot)
-        value = float(np.mean(vals))
+        # each step: the oracle's solve of one contour of the reduced member (a bounded sample, a few
+        # seconds), the contours taken in turn; value = pairs / seconds over the timed steps
+        for w in range(args.warmup):
+            oracle_solve(w)
+        pairs, secs, used = 0, 0.0, 1
+        for k in range(args.steps):
+            n_k, s_k, used, _ = oracle_solve(k)
+            pairs += n_k
+            secs += s_k
+        value = pairs / secs
+        sample = (f"oracle CI solve of one of the 8 contours per step (taken in turn) of the reduced member {REDUCED} "
+                  f"(n = 25281, bandwidth 160, eigenvalues 11..40, 16 nodes, L = 64, 2 moments, dense steps "
+                  f"included): {pairs} pairs in {secs:.1f} s over {args.steps} steps, {used} host threads")
         out = {"impl": "reference", "metric": METRICS[args.contours], "value": value, "unit": UNIT, "n_gpus": args.gpus,
-               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+               "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / max(args.steps, 1),
                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
                "data": "synthetic", "config": workload_config(args, spec, K.n),
-               "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+               "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample},
                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
         print(json.dumps(out))
         return
@@ -384,41 +385,46 @@ def main():
     dom = max(classes, key=lambda k: classes[k]["ms"])
     d = classes[dom]
     launches = max(d["launches"], 1)
-    sm_mhz = r["clocks"].get("sm_max_mhz") or 2070.0
-    # FP32 CUDA-core peak: 152 SMs x 128 FMA lanes x 2 flops x clock
-    alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+    sm_mhz = r["clocks"].get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    # FP32 CUDA-core peak: SMs (from the device) x 128 FMA lanes x 2 flops x the maximum SM clock
+    alu_peak = r["sms"] * 128 * 2 * sm_mhz * 1e6 / 1e12
     if dom in ("prec", "factor"):
         achieved = d["flops"] / (d["ms"] / 1e3) / 1e12
         bpf = traffic_per_flop() if dom == "prec" else None
         roof = {"kernel_class": dom, "bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                 "frac": achieved / alu_peak,
                 "traffic": None if bpf is None else bpf * d["flops"] / launches,
-                "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
+                "per_launch_ms": d["ms"] / launches, "launches": d["launches"],
+                "peak_derivation": f"{r['sms']} SMs x 128 FP32 lanes x 2 flops x {sm_mhz:.0f} MHz",
+                "timing": "CUDA events per launch in one profiled step after the timed region"}
     else:
         achieved = d["bytes"] / (d["ms"] / 1e3) / 1e9
         roof = {"kernel_class": dom, "bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved / hbm_peak, "traffic": None,
-                "per_launch_ms": d["ms"] / launches, "launches": d["launches"]}
+                "per_launch_ms": d["ms"] / launches, "launches": d["launches"],
+                "timing": "CUDA events per launch in one profiled step after the timed region"}
     spmm_ms = stats["spmm_dir"]["ms"] + stats["spmm_upd"]["ms"]
     spmm_gbs = (stats["spmm_dir"]["bytes"] + stats["spmm_upd"]["bytes"]) / max(spmm_ms, 1e-9) / 1e6
     out = {"metric": metric, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
+           "vs_baseline": None, "dtype": "c32+f64" if args.precision == "mixed" else "c128 (c64 band factors)",
+           "data": "synthetic",
            "config": workload_config(args, spec, r["K"].n) | {
                       "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
-                      "feast_iters_per_contour": r["last"]["iters"], "cocg_iters": r["last"]["cocg_iters"]},
+                      "feast_iters_per_contour": r["last"]["iters"], "cocg_iters": r["last"]["cocg_iters"],
+                      "precision": args.precision},
            "roofline": roof,
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
                         "nameplate_frac": spmm_gbs / 8000.0},
            "kernel_ms": {k: round(v["ms"], 2) for k, v in classes.items()},
-           "gpu_launches": int(stats["total_launches"]),
+           "gpu_launches": r["launches"],
            "clocks": r["clocks"], "e2e": r["e2e"]}
     if r["kde"] is not None:
         out["config"]["predicted_contours"] = r["kde"] | {"resplits": r["last"]["resplits"],
                                            "count_estimate": [round(float(x), 2) for x in r["last"]["count_estimate"]]}
     if not args.no_cpu_baseline and world == 1 or (world > 1 and rank == 0 and not args.no_cpu_baseline):
-        v, tot, sample = oracle_sample(args, spec, *P.workload(args.workload)[:2], args.cpu_sample_seconds)
-        out["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        pairs, sec, used, sample = oracle_solve()
+        out["cpu_baseline"] = {"value": pairs / sec, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample}
     print(json.dumps(out))
 
 

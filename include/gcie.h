@@ -93,8 +93,8 @@ typedef struct {
     size_t hbm_budget_bytes;/* device memory the solve may use (0: 90% of free memory) */
     int32_t expected_count; /* >= 0: return GCIE_ECOUNT if the merged count differs; -1: off */
     int32_t profile;        /* 1: time every kernel launch with CUDA events (see gcie_stats) */
-    int32_t precond;        /* GCIE_PREC_AUTO (default): banded LDL^T factors when the bandwidth
-                               allows (mixed precision), else the multigrid cycle; or a GCIE_PREC_* */
+    int32_t precond;        /* GCIE_PREC_AUTO (default): banded LDL^T factors (FP32) when the
+                               bandwidth allows, else the multigrid cycle; or a GCIE_PREC_* */
     int32_t judge;          /* 1: count check of every finished contour (see gcie_count_miss): a
                                contour that misses eigenvalues is replaced by the two halves of
                                gcie_resplit (w = 10) and they are solved; 0 (default): off */
@@ -270,7 +270,9 @@ int gcie_shifted_spmm_f64(gcie_ctx *ctx, gcie_pencil *p, int32_t nshift, const d
  * d_B: FP64 real n x ncol row-major (shared by all shifts); d_X: FP64 complex, nshift blocks of
  * n x ncol row-major; if x0 != 0, d_X holds the initial guess on entry.  precond: a GCIE_PREC_*
  * value; GCIE_PREC_BAND factors every shifted matrix as a complex-symmetric band L D L^T in FP32 and
- * uses the factors as the COCG preconditioner (mixed precision, bandwidth limited by shared memory),
+ * uses the factors as the COCG preconditioner (bandwidth limited by shared memory; in GCIE_FP64 mode the
+ * factors stay FP32: the residual is rounded to FP32 for their sweeps and the result widened back,
+ * while the COCG recurrences, the SpMM and the residual checks run in FP64),
  * GCIE_PREC_AMG applies the multigrid V-cycle (hierarchy built on the first call for this pencil and
  * kept with it), GCIE_PREC_AUTO picks the band factors when possible, GCIE_PREC_NONE runs plain COCG.
  * h_iters (host, may be NULL) receives the COCG iterations used.  Errors: GCIE_ENOCONV if a column missed lin_tol

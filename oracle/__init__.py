@@ -436,7 +436,8 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
     `max_resplit` levels; at the last level it keeps its pairs and reports non-convergence).
     Then merge/dedup across contours.  V is the random block (n x L) drawn by the caller.
     `trace`, if given, receives per-contour intermediates of iteration 0 (nodes, S, Q, theta).
-    `threads`: host threads for the nodes of a contour (default: every core of the affinity set).
+    `threads`: host threads (default: every core of the affinity set), shared by the contours of a
+    level and the nodes of each contour.  `trace` holds the input contours (depth 0) in order.
     Returns dict(evals, evecs, resid, contour_of, outer_iters, status, contours, estimates,
     resplits); contour_of indexes the final contours."""
     Ks, Ms = as_scipy(K), as_scipy(M)
@@ -444,19 +445,20 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
     if contours is None:
         contours = uniform_contours(lo, hi, ncontours, alpha)
     bw = bandwidth(Ks, Ms)
-    work = [(tuple(ct), 0) for ct in contours]
-    leaves, all_t, all_z, all_r, iters, status, ests = [], [], [], [], [], [], []
-    resplits = 0
-    while work:
-        (c, R, s, e), depth = work.pop(0)
+    cores = threads or host_threads()
+
+    def one_contour(ct, node_threads):
+        """Steps 1-5 for one contour; the contours are independent until the merge."""
+        c, R, s, e = ct
         z, w = trapezoid_nodes(c, R, nodes)
-        solvers = node_map(lambda zj: ShiftedSolver(Ks, Ms, zj, bw), z, threads)
+        solvers = node_map(lambda zj: ShiftedSolver(Ks, Ms, zj, bw), z, node_threads)
         Vk = np.asarray(V, dtype=np.float64)
         m = moments_m
         ok = False
+        tr = None
         for it in range(max_outer):
             B = Ms @ Vk
-            X = node_map(lambda sv: sv.solve(B), solvers, threads)
+            X = node_map(lambda sv: sv.solve(B), solvers, node_threads)
             S = moments(X, z, w, c, R, m)
             if it == 0:
                 est, se = trace_estimate(Vk, S[0])
@@ -464,25 +466,55 @@ def ci_solve(K, M, lo: float, hi: float, V: np.ndarray, *, ncontours: int = 1, n
             Q = m_orthonormalize(Y, Ms)
             theta, Z = rayleigh_ritz(Ks, Ms, Q)
             res = residuals(Ks, Ms, theta, Z, nK)
-            if trace is not None and it == 0:
-                trace.setdefault("contours", []).append(dict(z=z, w=w, S=S, Q=Q, theta=theta, res=res))
+            if it == 0:
+                tr = dict(z=z, w=w, S=S, Q=Q, theta=theta, res=res)
             inside = (theta >= s) & (theta <= e)
             if not np.any(inside & (res > tol)):
                 ok = True
                 break
             Vk, m = Z, 1
-        if judge and count_miss(est, se, theta, res, c, R, Q.shape[1], tol):
-            if depth < max_resplit and e > s:
-                work[0:0] = [(ch, depth + 1) for ch in resplit(theta, c, R, s, e, kde_w)]
-                resplits += 1
+        return dict(ct=ct, theta=theta, Z=Z, res=res, inside=inside, est=est, se=se, rank=Q.shape[1],
+                    iters=it + 1, ok=ok, trace=tr)
+
+    # the contours of a level are solved side by side (each with its share of the host cores), then
+    # judged in order; a contour that fails the check is replaced in place by its halves, which the
+    # next level solves, so the final contours keep the order of the depth-first splits
+    slots = [dict(ct=tuple(ct), depth=0, out=None) for ct in contours]
+    resplits = 0
+    while True:
+        pend = [sl for sl in slots if sl["out"] is None]
+        if not pend:
+            break
+        per = max(1, cores // len(pend))
+        outs = node_map(lambda sl: one_contour(sl["ct"], per), pend, min(cores, len(pend)))
+        new_slots = []
+        for sl in slots:
+            if sl["out"] is not None:
+                new_slots.append(sl)
                 continue
-            ok = False
-        leaves.append((c, R, s, e))
-        ests.append(est)
-        iters.append(it + 1)
-        status.append(0 if ok else 1)
-        sel = inside & (res <= tol)
-        all_t.append(theta[sel]); all_z.append(Z[:, sel]); all_r.append(res[sel])
+            o = outs[pend.index(sl)]
+            c, R, s, e = sl["ct"]
+            if trace is not None and sl["depth"] == 0:
+                trace.setdefault("contours", []).append(o["trace"])
+            if judge and count_miss(o["est"], o["se"], o["theta"], o["res"], c, R, o["rank"], tol):
+                if sl["depth"] < max_resplit and e > s:
+                    new_slots.extend(dict(ct=tuple(ch), depth=sl["depth"] + 1, out=None)
+                                     for ch in resplit(o["theta"], c, R, s, e, kde_w))
+                    resplits += 1
+                    continue
+                o["ok"] = False
+            sl["out"] = o
+            new_slots.append(sl)
+        slots = new_slots
+    leaves = [sl["ct"] for sl in slots]
+    outs = [sl["out"] for sl in slots]
+    ests = [o["est"] for o in outs]
+    iters = [o["iters"] for o in outs]
+    status = [0 if o["ok"] else 1 for o in outs]
+    sels = [o["inside"] & (o["res"] <= tol) for o in outs]
+    all_t = [o["theta"][sel] for o, sel in zip(outs, sels)]
+    all_z = [o["Z"][:, sel] for o, sel in zip(outs, sels)]
+    all_r = [o["res"][sel] for o, sel in zip(outs, sels)]
     cid = [np.full(t.size, k, dtype=np.int32) for k, t in enumerate(all_t)]
     theta = np.concatenate(all_t)
     Z = np.concatenate(all_z, axis=1) if all_z else np.zeros((Ks.shape[0], 0))

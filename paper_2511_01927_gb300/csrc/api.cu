@@ -862,10 +862,11 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                     nn += nn & 1;
                     // per contour: COCG blocks (7 with a preconditioner), the FP64 iterate, moments and
                     // basis blocks, and FP32 band factors of its nodes
-                    const bool band = o->precision == GCIE_MIXED && o->precond != GCIE_PREC_NONE &&
-                                      o->precond != GCIE_PREC_AMG && band_feasible(c, p->bw);
-                    const size_t per = (size_t)half * n * nn * (7 * esz + 16) + (size_t)n * nn * 8 * 4 +
-                                       (band ? (size_t)half * band_elems(n, p->bw) * 8 : 0);
+                    const bool band = o->precond != GCIE_PREC_NONE && o->precond != GCIE_PREC_AMG &&
+                                      band_feasible(c, p->bw);
+                    // (FP64 with band factors: two more FP32 blocks for the sweeps' input and output)
+                    const size_t per = (size_t)half * n * nn * (7 * esz + 16 + (band && esz == 16 ? 16 : 0)) +
+                                       (size_t)n * nn * 8 * 4 + (band ? (size_t)half * band_elems(n, p->bw) * 8 : 0);
                     if (b1 > b0 && per * (b1 - b0 + 1) > budget) break;
                     ncol = nn;
                     ++b1;
@@ -1293,7 +1294,7 @@ int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const g
     for (int k = 0; k < o.ncontours; ++k)
         if (!(o.contours[k].r > 0) || !(o.contours[k].lo <= o.contours[k].hi)) { set_error("solve: bad contour"); return GCIE_EINVAL; }
     cudaSetDevice(c->device);
-    if (o.profile) c->profile = true;
+    c->profile = o.profile != 0;
     int rc = solve_driver(c, p, lo, hi, &o, out);
     cudaStreamSynchronize(c->stream);
     if (c->profile) flush_timing(c);

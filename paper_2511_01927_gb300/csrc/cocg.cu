@@ -501,6 +501,42 @@ __global__ void k_scale_rows(int64_t n, int ncol, int64_t nblk, int ncomp, const
     }
 }
 
+// ------------------------------------------------------------------ FP32 band factors in the FP64 solver
+// In FP64 mode the band preconditioner keeps its FP32 factors: the residual is rounded to FP32 for the
+// sweeps and their result widened back, with the partial sums of r^T z formed in FP64.
+__global__ void k_demote(int64_t n, int ncol, const int *__restrict__ mask, const double2 *__restrict__ R,
+                         float2 *__restrict__ Rf)
+{
+    const int s = blockIdx.y;
+    if (!mask[s]) return;
+    const int64_t per = n * ncol, base = (int64_t)s * per;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < per; e += (int64_t)gridDim.x * blockDim.x) {
+        const double2 r = R[base + e];
+        Rf[base + e] = make_float2((float)r.x, (float)r.y);
+    }
+}
+
+__global__ void k_promote_rz(int64_t n, int ncol, int64_t rows_per_chunk, int chunks, const int *__restrict__ mask,
+                             const double2 *__restrict__ R, const float2 *__restrict__ Zf, double2 *__restrict__ Z,
+                             double2 *__restrict__ part)
+{
+    const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
+    if (!mask[s]) return;
+    const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double re = 0.0, im = 0.0;
+        const int64_t off = (int64_t)s * n * ncol + c;
+        for (int64_t i = r0; i < r1; ++i) {
+            const float2 zf = Zf[off + i * ncol];
+            const double2 z = make_double2((double)zf.x, (double)zf.y), r = R[off + i * ncol];
+            Z[off + i * ncol] = z;
+            re = fma(r.x, z.x, fma(-r.y, z.y, re));
+            im = fma(r.x, z.y, fma(r.y, z.x, im));
+        }
+        part[((int64_t)s * chunks + ch) * ncol + c] = make_double2(re, im);
+    }
+}
+
 // ------------------------------------------------------------------ host driver
 template <typename T>
 static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const int *h_rhs_of, int nrhs, int ncol,
@@ -529,7 +565,10 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                             nshift * sizeof(int),
                             // preconditioned iteration: z, two fine-level cycle blocks, r^T z partials
                             prec ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0, amg ? blk * sizeof(C) : 0,
-                            prec ? (size_t)nshift * maxch * ncol * sizeof(double2) : 0};
+                            prec ? (size_t)nshift * maxch * ncol * sizeof(double2) : 0,
+                            // FP64 solver with the FP32 band factors: the residual and the sweeps' output in FP32
+                            (bandAB && sizeof(T) == 8) ? blk * sizeof(float2) : 0,
+                            (bandAB && sizeof(T) == 8) ? blk * sizeof(float2) : 0};
     size_t bytes = 0;
     for (size_t b : sizes) bytes += (b + 255) & ~(size_t)255;
     char *base = nullptr;
@@ -569,6 +608,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
     C *R1 = (C *)take();
     C *XF = (C *)take();
     double2 *partC = (double2 *)take();
+    float2 *Rf = (float2 *)take();
+    float2 *Zf = (float2 *)take();
     AmgWork<T> aw;
     // the direction sweep reads the preconditioned residual z (= r without preconditioner)
     C *Zdir = prec ? Zp : R;
@@ -580,9 +621,20 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
             GCIE_TRY(band_apply(c, p, nshift, ncol, mask, bandAB, (const float2 *)R, (float2 *)Zp, nact));
             return rz_partials(c, n, nshift, ncol, g.rows_per_chunk, g.chunks, mask, (const float2 *)R, (const float2 *)Zp,
                                partC, nact);
+        } else {
+            {
+                LaunchScope ls(c, GCIE_K_OTHER, (double)nact * n * ncol * 24.0, 0);
+                k_demote<<<dim3(std::max(1, std::min(64, (int)((n * ncol + 255) / 256))), nshift), 256, 0, c->stream>>>(
+                    n, ncol, mask, (const double2 *)R, Rf);
+                GCIE_CUDA_TRY(cudaGetLastError());
+            }
+            GCIE_TRY(band_apply(c, p, nshift, ncol, mask, bandAB, Rf, Zf, nact));
+            LaunchScope ls(c, GCIE_K_OTHER, (double)nact * n * ncol * 40.0, (double)nact * n * ncol * 8.0);
+            k_promote_rz<<<nshift * g.chunks, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(
+                n, ncol, g.rows_per_chunk, g.chunks, mask, (const double2 *)R, Zf, (double2 *)Zp, partC);
+            GCIE_CUDA_TRY(cudaGetLastError());
+            return GCIE_OK;
         }
-        set_error("band preconditioner needs the mixed-precision solver");
-        return GCIE_EINVAL;
     };
 
     int rc = GCIE_OK;
@@ -763,8 +815,7 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
     const Amg *amg = nullptr;
     float2 **bandAB = nullptr;
     BandCache local;
-    const bool use_band = precision == GCIE_MIXED && (precond == GCIE_PREC_BAND || precond == GCIE_PREC_AUTO) &&
-                          band_feasible(c, p->bw);
+    const bool use_band = (precond == GCIE_PREC_BAND || precond == GCIE_PREC_AUTO) && band_feasible(c, p->bw);
     if (rc == GCIE_OK && use_band) {
         rc = (cache ? cache : &local)->get(c, p, nshift, h_z, &bandAB);
     } else if (rc == GCIE_OK && (precond == GCIE_PREC_AMG || precond == GCIE_PREC_AUTO)) {
@@ -776,13 +827,13 @@ int cocg_solve(Ctx *c, Pencil *p, int nshift, const double *h_z, const int *h_rh
         }
         amg = p->amg;
     } else if (rc == GCIE_OK && precond == GCIE_PREC_BAND) {
-        set_error("band preconditioner: bandwidth too large or FP64 mode");
+        set_error("band preconditioner: bandwidth too large for the shared-memory kernels");
         rc = GCIE_EINVAL;
     }
     if (rc == GCIE_OK)
         rc = precision == GCIE_FP64
                  ? solve_t<double>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
-                                   nullptr, info)
+                                   bandAB, info)
                  : solve_t<float>(c, p, nshift, h_z, h_rhs_of, nrhs, ncol, Bs, d_X, x0, lin_tol, max_iters, amg,
                                   bandAB, info);
     if (bandAB) {

@@ -248,6 +248,10 @@ WORKLOADS = {
     # Smaller members of the same 2D family (parity sizes the oracle finishes in seconds).
     "fem2d-p1-40": dict(kind="fem2d", nc=40, seeds=(2, 3), first=11, last=60, contours=2, nodes=16,
                         L=32, moments=2, golden="fem2d_p1_40.json"),
+    # A reduced member of the 500 x 500 workload (160 x 160 cells, n = 25281, bandwidth 160) with the same
+    # solver configuration (8 contours x 16 nodes, L = 64, 2 moments): the oracle's timed whole solve.
+    "fem2d-p1-160": dict(kind="fem2d", nc=160, seeds=(2, 3), first=11, last=40, contours=8, nodes=16,
+                         L=64, moments=2, golden="fem2d_p1_160.json"),
     # A strip of the 500 x 500 family (12 x 500 cells, n = 11 x 499 = 5489) with the bench workload's
     # bandwidth (500): parity of the band kernels at full bandwidth, eigenvalues 21..60.
     "fem2d-p1-strip": dict(kind="fem2d_strip", nci=12, ncj=500, seeds=(2, 3), first=21, last=60, contours=2,

@@ -94,7 +94,7 @@ def test_shifted_spmm_f64(G, ctx, small2d, ncol):
 
 # --------------------------------------------------------------------------- a4-a6: shifted solves
 
-@pytest.mark.parametrize("precision,precond", [(0, 3), (0, 2), (1, 2), (0, 0), (1, 0)])
+@pytest.mark.parametrize("precision,precond", [(0, 3), (1, 3), (0, 2), (1, 2), (0, 0), (1, 0)])
 def test_shifted_solve_matches_lu(G, ctx, small2d, precision, precond):
     K, M, spec, pen = small2d
     lo, hi = spec["lo"], spec["hi"]
