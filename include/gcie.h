@@ -306,6 +306,25 @@ int gcie_rayleigh_ritz(gcie_ctx *ctx, gcie_pencil *p, int32_t q, const double *d
  * d_V: p x p row-major, column j = eigenvector j. */
 int gcie_jacobi_eig(gcie_ctx *ctx, int32_t p, double *d_A, double *d_w, double *d_V);
 
+/* ------------------------------------------------------------------ tensor-core products (tcgen05)
+ * D = A B^T on the fifth-generation tensor cores, A row-major M x K (leading dimension lda), B row-major
+ * N x K (ldb), D row-major M x N (ldd), all device memory on the context's device, caller-owned; the
+ * call returns when D is written (synchronous on the context's stream).  M, N, K >= 1 (0 does nothing).
+ * Errors: GCIE_EINVAL (sizes, leading dimensions, null pointers), GCIE_ETIMEOUT (a bounded wait for the
+ * tensor cores expired), GCIE_ECUDA.
+ *
+ * gcie_gemm_tf32x3: FP32 operands; each is split into a TF32 head and tail (x = hi + lo) and
+ *   D = Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T is accumulated in FP32, close to an FP32 product (per element
+ *   within a few 2^-22 of sum_k |A_ik| |B_jk|).  The dense contractions of the shifted solves' band
+ *   factors (Algorithm 1, "solve (z_j B - A) X_j = B V"; Eq. quadrature_appendix) are of this kind.
+ * gcie_gemm_bf16: BF16 operands (uint16 bit patterns), FP32 accumulation, epilogue
+ *   D = act(A B^T + bias), bias (N, FP32, may be NULL) and act = ReLU when relu != 0, else identity: the
+ *   layers of the density predictor that stands in for the paper's spectrum predictor (Section 4.1). */
+int gcie_gemm_tf32x3(gcie_ctx *ctx, int32_t M, int32_t N, int32_t K, const float *d_A, int32_t lda,
+                     const float *d_B, int32_t ldb, float *d_D, int32_t ldd);
+int gcie_gemm_bf16(gcie_ctx *ctx, int32_t M, int32_t N, int32_t K, const uint16_t *d_A, int32_t lda,
+                   const uint16_t *d_B, int32_t ldb, const float *d_bias, int32_t relu, float *d_D, int32_t ldd);
+
 /* The same eigensolve for callers that must not allocate device memory.  (The paper has no
  * counterpart; this entry point exists for integration only.)  Some callers cannot call cudaMalloc:
  * a process that reserves all device memory for its own pool up front has none left to give, and a

@@ -20,7 +20,7 @@ EXPORTED_SYMBOLS = [
     "gcie_reset_stats", "gcie_set_profile", "gcie_pencil_create", "gcie_pencil_destroy", "gcie_pencil_n", "gcie_pencil_nnz",
     "gcie_solve", "gcie_solve_pencil", "gcie_solve_batch", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_plan_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
-    "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc",
+    "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc", "gcie_gemm_tf32x3", "gcie_gemm_bf16",
 ]
 
 
@@ -113,6 +113,8 @@ def lib():
         "gcie_rayleigh_ritz": (C.c_int, [vp, vp, i32, vp, vp, vp, vp]),
         "gcie_jacobi_eig": (C.c_int, [vp, i32, vp, vp, vp]),
         "gcie_jacobi_eig_noalloc": (C.c_int, [vp, i32, vp, vp, vp]),
+        "gcie_gemm_tf32x3": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32]),
+        "gcie_gemm_bf16": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, i32]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -421,3 +423,15 @@ def gcie_jacobi_eig_noalloc(stream, p: int, d_A, d_w, d_V):
     """Allocation-free variant (stream: a cudaStream_t handle as int, or None)."""
     _check(lib().gcie_jacobi_eig_noalloc(C.c_void_p(stream) if stream else None, int(p), _ptr(d_A), _ptr(d_w),
                                          _ptr(d_V)), "gcie_jacobi_eig_noalloc")
+
+
+def gcie_gemm_tf32x3(ctx, M: int, N: int, K: int, d_A, lda: int, d_B, ldb: int, d_D, ldd: int):
+    """D = A B^T on the tensor cores, FP32 operands split into TF32 head and tail (device pointers)."""
+    _check(lib().gcie_gemm_tf32x3(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_D),
+                                  int(ldd)), "gcie_gemm_tf32x3")
+
+
+def gcie_gemm_bf16(ctx, M: int, N: int, K: int, d_A, lda: int, d_B, ldb: int, d_bias, relu: bool, d_D, ldd: int):
+    """D = act(A B^T + bias) on the tensor cores, BF16 operands (device tensors of dtype bfloat16)."""
+    _check(lib().gcie_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_bias),
+                                int(bool(relu)), _ptr(d_D), int(ldd)), "gcie_gemm_bf16")

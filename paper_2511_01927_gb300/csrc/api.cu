@@ -586,6 +586,45 @@ int gcie_rayleigh_ritz(gcie_ctx *c, gcie_pencil *p, int32_t q, const double *d_Q
     return rayleigh_ritz(c, p, q, d_Q, d_Z, h_theta, h_res);
 }
 
+// the tensor-core products: launch, then wait for the stream and read the timeout count
+static int gemm_finish(gcie_ctx *c, int rc)
+{
+    if (rc != GCIE_OK) return rc;
+    unsigned int to = 0;
+    GCIE_CUDA_TRY(cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream));
+    GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (to) {
+        cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(to), c->stream);
+        set_error("gemm: a wait for the tensor cores did not complete in time");
+        return GCIE_ETIMEOUT;
+    }
+    return GCIE_OK;
+}
+
+int gcie_gemm_tf32x3(gcie_ctx *c, int32_t M, int32_t N, int32_t K, const float *d_A, int32_t lda, const float *d_B,
+                     int32_t ldb, float *d_D, int32_t ldd)
+{
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
+    if (!c || M < 0 || N < 0 || K < 0 || (M && N && K && (!d_A || !d_B || !d_D || lda < K || ldb < K || ldd < N))) {
+        set_error("gemm_tf32x3: bad argument");
+        return GCIE_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    return gemm_finish(c, gemm_tf32x3(c, M, N, K, d_A, lda, d_B, ldb, d_D, ldd));
+}
+
+int gcie_gemm_bf16(gcie_ctx *c, int32_t M, int32_t N, int32_t K, const uint16_t *d_A, int32_t lda, const uint16_t *d_B,
+                   int32_t ldb, const float *d_bias, int32_t relu, float *d_D, int32_t ldd)
+{
+    if (c && c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
+    if (!c || M < 0 || N < 0 || K < 0 || (M && N && K && (!d_A || !d_B || !d_D || lda < K || ldb < K || ldd < N))) {
+        set_error("gemm_bf16: bad argument");
+        return GCIE_EINVAL;
+    }
+    cudaSetDevice(c->device);
+    return gemm_finish(c, gemm_bf16(c, M, N, K, d_A, lda, d_B, ldb, d_bias, relu, d_D, ldd));
+}
+
 int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, double *d_V)
 {
     return jacobi_noalloc((cudaStream_t)stream, p, d_A, d_w, d_V);

@@ -58,6 +58,11 @@ int jacobi_noalloc(cudaStream_t stream, int p, double *A, double *w, double *V);
 int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, const double *Z,
                 const double *d_theta, double *d_r2, double *d_z2);
 
+// tensor-core products D = A B^T (gemm.cu): FP32-faithful split TF32, and BF16 with bias and ReLU
+int gemm_tf32x3(Ctx *c, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *D, int ldd);
+int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, int relu,
+              float *D, int ldd);
+
 // a8: two-pass M-orthonormalisation; Q has *rank valid columns (row-major n x ldQ).
 int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q,
                      int *rank);

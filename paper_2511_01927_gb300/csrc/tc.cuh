@@ -1,0 +1,145 @@
+// Fifth-generation tensor cores (tcgen05) of sm_100-family GPUs: the pieces the library's tensor-core
+// kernels share, as inline PTX.
+//
+//   - Tensor memory (TMEM): 128 lanes x 512 columns of 32-bit cells per SM.  A CTA allocates a power-of-two
+//     number of columns (>= 32) with one warp, passes the base address through shared memory, and frees it
+//     with the same warp before it exits.  An address is (lane << 16) | column.
+//   - tcgen05.mma (cta_group::1): D[M x N] (+)= A[M x K] B[N x K]^T with A and B in shared memory, described
+//     by 64-bit matrix descriptors, and D (FP32) in TMEM; one thread issues it.  With M = 128, row m of D is
+//     TMEM lane m and column n is TMEM column base + n.
+//   - tcgen05.commit: an mbarrier arrival once every MMA the thread issued before it has completed.
+//   - tcgen05.ld (32x32b): each thread of a warp reads consecutive columns of one lane; warp w may read
+//     lanes 32 (w % 4) .. 32 (w % 4) + 31.
+//
+// Operands use the canonical K-major layout without swizzle: "core matrices" of 8 rows x 16 bytes, each
+// stored as 128 contiguous bytes (row r of the core matrix at byte 16 r).  Element (row, k) of a tile
+// whose rows hold KB bytes sits at
+//     (row / 8) * SBO + (k_byte / 16) * LBO + (row % 8) * 16 + k_byte % 16,
+// with LBO = 128 (core matrices adjacent along K) and SBO = 8 * KB (the next group of 8 rows).
+// One MMA consumes 32 bytes of K (8 TF32 or 16 BF16 values), i.e. two core matrices; the next K step
+// starts 2 * LBO bytes further.
+#pragma once
+
+#include <cstdint>
+
+namespace gcie {
+namespace tc {
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// ---------------------------------------------------------------- descriptors
+// Shared-memory matrix descriptor (no swizzle): start address, LBO and SBO in 16-byte units, version 1.
+__device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo_bytes, uint32_t sbo_bytes)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo_bytes >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo_bytes >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;                 // descriptor version of the sm_100 family
+    // base offset 0, LBO mode 0, layout type 0 (no swizzle)
+    return d;
+}
+
+// Instruction descriptor of kind::f16 / kind::tf32 MMAs: D in FP32, A and B K-major.
+//   fmt: 0 = F16, 1 = BF16 (kind::f16), 2 = TF32 (kind::tf32); neg_a / neg_b negate an operand.
+__host__ __device__ constexpr uint32_t make_idesc(int fmt, int M, int N, int neg_a = 0, int neg_b = 0)
+{
+    return (1u << 4)                              // D format: F32
+           | ((uint32_t)fmt << 7)                 // A format
+           | ((uint32_t)fmt << 10)                // B format
+           | ((uint32_t)neg_a << 13) | ((uint32_t)neg_b << 14)
+           | ((uint32_t)(N >> 3) << 17)           // N / 8
+           | ((uint32_t)(M >> 4) << 24);          // M / 16
+}
+
+// ---------------------------------------------------------------- TMEM
+// (whole warp) allocate ncols columns (power of two, 32..512); the base address lands in *slot
+__device__ __forceinline__ void tmem_alloc(uint32_t *slot, uint32_t ncols)
+{
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// (whole warp, the allocating one)
+__device__ __forceinline__ void tmem_free(uint32_t taddr, uint32_t ncols)
+{
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// generic-proxy writes to shared memory made visible to the tensor cores' (async proxy) reads
+__device__ __forceinline__ void fence_smem_for_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// ---------------------------------------------------------------- MMA
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, int accumulate)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc, int accumulate)
+{
+    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+                 ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate) : "memory");
+}
+// arrival on the mbarrier once the MMAs this thread issued so far have completed
+__device__ __forceinline__ void commit(uint64_t *bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+// ---------------------------------------------------------------- mbarrier (count 1)
+__device__ __forceinline__ void mbar_init(uint64_t *bar)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(ok) : "r"(smem_addr(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+// waits for the phase of the given parity; false after about 2^31 SM clock cycles (a second at 2 GHz)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+{
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > (1ll << 31)) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------- TMEM -> registers
+// 16 consecutive 32-bit columns of the calling thread's lane
+__device__ __forceinline__ void ld16(uint32_t taddr, float (&v)[16])
+{
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ---------------------------------------------------------------- operand values
+// FP32 -> TF32 (round to nearest, ties away; low 13 bits zero)
+__device__ __forceinline__ float to_tf32(float x)
+{
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
+// byte offset of element (row, kbyte) in the canonical no-swizzle K-major layout with rows of kb bytes
+__host__ __device__ constexpr uint32_t kmajor_offset(uint32_t row, uint32_t kbyte, uint32_t kb)
+{
+    return (row >> 3) * (8u * kb) + (kbyte >> 4) * 128u + (row & 7u) * 16u + (kbyte & 15u);
+}
+
+}  // namespace tc
+}  // namespace gcie
