@@ -769,18 +769,35 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
     int *d_status = nullptr;
     GCIE_CUDA_TRY(ctx_malloc(c, (void **)&d_status, sizeof(int)));
     GCIE_CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), c->stream));
-    const size_t smem = band_smem_factor(b);
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // the trailing update on the tensor cores when the band fits its operand tiles (b <= 512); GCIE_FACTOR_TC=0
+    // selects the CUDA-core kernel (comparison runs and tests of both)
+    const char *tc_env = std::getenv("GCIE_FACTOR_TC");
+    const bool use_tc = b <= 512 && band_smem_factor_tc() <= c->smem_optin && !(tc_env && std::atoi(tc_env) == 0);
+    const size_t smem = use_tc ? band_smem_factor_tc() : band_smem_factor(b);
     {
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
         LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
-        k_band_ldlt<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
+        if (use_tc) {
+            GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_band_ldlt_tc<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status,
+                                                                 &c->dbg->wait_timeouts);
+        } else {
+            GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            k_band_ldlt<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
+        }
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     int hs = 0;
+    unsigned int to = 0;
     GCIE_CUDA_TRY(cudaMemcpyAsync(&hs, d_status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    GCIE_CUDA_TRY(cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream));
     ctx_free(c, d_status);
     GCIE_CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (to) {
+        cudaMemsetAsync(&c->dbg->wait_timeouts, 0, sizeof(to), c->stream);
+        set_error("band LDL^T: a wait for the tensor cores did not complete in time");
+        return GCIE_ETIMEOUT;
+    }
     if (hs) { set_error("band LDL^T: zero or non-finite pivot"); return GCIE_EBREAKDOWN; }
     return GCIE_OK;
 }

@@ -25,6 +25,9 @@ struct BandCache {
 bool band_feasible(const Ctx *c, int b);
 size_t band_elems(int64_t n, int b);        // complex values of one shift's factor storage
 size_t band_smem_factor(int b);
+// the factorization with the trailing update on the tensor cores (ldlt_tc.cu), bandwidths <= 512
+size_t band_smem_factor_tc();
+__global__ void k_band_ldlt_tc(int64_t n, int b, float2 *const *ABp, size_t ab_off, int *status, unsigned int *timeouts);
 size_t band_smem_solve(int b, int sc);
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
                 const std::vector<float2 *> &h_ABp);
