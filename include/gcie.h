@@ -325,6 +325,46 @@ int gcie_gemm_tf32x3(gcie_ctx *ctx, int32_t M, int32_t N, int32_t K, const float
 int gcie_gemm_bf16(gcie_ctx *ctx, int32_t M, int32_t N, int32_t K, const uint16_t *d_A, int32_t lda,
                    const uint16_t *d_B, int32_t ldb, const float *d_bias, int32_t relu, float *d_D, int32_t ldd);
 
+/* ------------------------------------------------------------------ density predictor (learned contours)
+ * A small network that predicts the eigenvalue density of a pencil of the 2D log-normal family from its
+ * coefficient fields: the stand-in for the paper's spectrum predictor (Section 4.1: a neural operator
+ * maps the PDE coefficients to the spectrum) whose prediction places the contours (Section 4.2,
+ * Algorithm 3: predict, construct contours, solve).  Inference runs on the GPU: BF16 weights and
+ * activations, FP32 accumulation on the tensor cores (gcie_gemm_bf16's kernel).
+ *
+ * Input: kappa and rho (the coefficients in K and M) on a G x G cell grid, G a multiple of 64; channel
+ * c of the 64 x 64 input is the mean of log(kappa) (c = 0) or log(rho) (c = 1) over (G/64)^2 cells.
+ * Bounds: the target interval [lo, hi] (0 < lo < hi) enters as u = (log lo - 6.5, log hi - 6.5).
+ * Network (NHWC activations): four 3 x 3 convolutions, stride 2, zero padding 1, ReLU, channels
+ * 2 -> 16 -> 32 -> 64 -> 64 (64 x 64 -> 4 x 4); the 4 x 4 x 64 features flattened in (y, x, channel)
+ * order and followed by u (1026 values); fc1 1026 -> 512, ReLU; fc2 512 -> 256, softplus.  Output: the
+ * expected number of eigenvalues in each of 256 equal bins of [lo, hi].
+ * Weights: one FP32 array, in this order, each weight tensor followed by its bias:
+ *   conv l (l = 1..4): W[Cout][3][3][Cin] (ky, kx, input channel), b[Cout];
+ *   fc1: W[512][1026], b[512];  fc2: W[256][512], b[256]   (GCIE_DENSITY_NWEIGHTS values in all).
+ * The weights are rounded to BF16 on upload; each layer's input is rounded to BF16. */
+#define GCIE_DENSITY_NWEIGHTS 717520
+#define GCIE_DENSITY_BINS 256
+typedef struct gcie_density_net gcie_density_net;
+/* Upload the weights (host, nweights == GCIE_DENSITY_NWEIGHTS, finite) to the context's device.
+ * Errors: GCIE_EINVAL, GCIE_ENOMEM, GCIE_ECUDA. */
+int gcie_density_net_create(gcie_ctx *ctx, const float *h_weights, int64_t nweights, gcie_density_net **out);
+void gcie_density_net_destroy(gcie_density_net *net);
+/* Predict the histograms of `batch` pencils.  h_kappa, h_rho: host, batch x G x G FP32 (cell (y, x) of
+ * member i at i G^2 + y G + x), positive; h_bounds: host, batch x 2 (lo, hi); h_hist: host, batch x 256,
+ * written.  Errors: GCIE_EINVAL (G not a positive multiple of 64, batch < 1, bad bounds), GCIE_ENOMEM,
+ * GCIE_ETIMEOUT, GCIE_ECUDA. */
+int gcie_density_predict(gcie_ctx *ctx, gcie_density_net *net, int32_t batch, int32_t grid, const float *h_kappa,
+                         const float *h_rho, const double *h_bounds, double *h_hist);
+/* Pseudo-eigenvalues from a predicted histogram: with N = round(sum of the counts) (at most cap), the
+ * k-th value (k = 1..N) is where the piecewise-linear cumulative count of the histogram over
+ * [lo, hi] (counts spread evenly inside each bin) reaches k - 1/2; the spectrum the contour planners
+ * (gcie_plan_contours, gcie_kde_contours) take as their prediction (Algorithm 3).  Host only.
+ * hist: host, nbins >= 1 non-negative counts; out: host, cap values, ascending; *nout = N.
+ * Errors: GCIE_EINVAL (bad arguments, or N > cap: nothing written then). */
+int gcie_hist_quantiles(const double *hist, int32_t nbins, double lo, double hi, double *out, int32_t cap,
+                        int32_t *nout);
+
 /* The same eigensolve for callers that must not allocate device memory.  (The paper has no
  * counterpart; this entry point exists for integration only.)  Some callers cannot call cudaMalloc:
  * a process that reserves all device memory for its own pool up front has none left to give, and a

@@ -641,3 +641,101 @@ def kde_contours(pred, nmin: int = 10, nmax: int = 50, w: float = 10.0, alpha: f
         final = final[:lo_i] + new + final[hi_i + 1:]
     out = final
     return [(a, b, 0.5 * (a + b), (1.0 + alpha) * 0.5 * (b - a), int(members(a, b).size)) for a, b in out]
+
+
+# --------------------------------------------------------------------------- density predictor (reference forward)
+# The learned-contour path (Section 4.1's spectrum predictor stand-in, Algorithm 3 "predict, construct
+# contours, solve") runs a small network on the GPU.  This is its plain NumPy forward pass, written from
+# the layout the C ABI states: the 64 x 64 x 2 input of block means of log(kappa), log(rho); four 3 x 3
+# convolutions with stride 2, zero padding 1 and ReLU (2 -> 16 -> 32 -> 64 -> 64 channels, NHWC); the
+# 4 x 4 x 64 features flattened as (y, x, channel) followed by (log lo - 6.5, log hi - 6.5); fc1 1026 -> 512
+# with ReLU; fc2 512 -> 256 with softplus.  Weights: one float32 array, W[Cout][3][3][Cin] then b[Cout] per
+# convolution, then W1[512][1026], b1, W2[256][512], b2.  With `bf16`, weights and every layer's input are
+# rounded to BF16 (round to nearest even), as the GPU path does; sums are formed in FP64.
+
+DENSITY_CONV = ((2, 16), (16, 32), (32, 64), (64, 64))
+DENSITY_FEAT = 64 * 4 * 4 + 2
+DENSITY_HID = 512
+DENSITY_BINS = 256
+
+
+def bf16_round(x):
+    """Round float32 values to the nearest BF16 value (ties to even), returned as float64."""
+    u = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def density_unpack(w):
+    """The flat weight array as [(W, b), ...] per layer (W of the convolutions as [Cout][3][3][Cin])."""
+    w = np.asarray(w, dtype=np.float32).ravel()
+    out, pos = [], 0
+    shapes = [((co, 3, 3, ci), co) for ci, co in DENSITY_CONV]
+    shapes += [((DENSITY_HID, DENSITY_FEAT), DENSITY_HID), ((DENSITY_BINS, DENSITY_HID), DENSITY_BINS)]
+    for shp, nb in shapes:
+        nw = int(np.prod(shp))
+        out.append((w[pos:pos + nw].reshape(shp), w[pos + nw:pos + nw + nb]))
+        pos += nw + nb
+    if pos != w.size:
+        raise ValueError(f"expected {pos} weights, got {w.size}")
+    return out
+
+
+def density_input(kappa, rho):
+    """64 x 64 x 2 network input of one member: block means of log(kappa), log(rho) (G x G cell grids)."""
+    G = kappa.shape[0]
+    s = G // 64
+    lk = np.log(np.asarray(kappa, dtype=np.float64)).reshape(64, s, 64, s).mean(axis=(1, 3))
+    lr = np.log(np.asarray(rho, dtype=np.float64)).reshape(64, s, 64, s).mean(axis=(1, 3))
+    return np.stack([lk, lr], axis=-1)
+
+
+def density_forward(w, kappa, rho, bounds, bf16: bool = True):
+    """Predicted histograms (batch x 256): kappa, rho batch x G x G; bounds batch x 2 (lo, hi)."""
+    layers = density_unpack(w)
+    rnd = bf16_round if bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+    kappa = np.asarray(kappa)
+    rho = np.asarray(rho)
+    if kappa.ndim == 2:
+        kappa, rho = kappa[None], rho[None]
+    bounds = np.asarray(bounds, dtype=np.float64).reshape(-1, 2)
+    out = []
+    for b in range(kappa.shape[0]):
+        x = density_input(kappa[b], rho[b]).astype(np.float32)
+        for (W, bias), (ci, co) in zip(layers[:4], DENSITY_CONV):
+            H = x.shape[0]
+            Ho = H // 2
+            xp = np.zeros((H + 2, H + 2, ci))
+            xp[1:H + 1, 1:H + 1] = rnd(x)
+            Wr = rnd(W)
+            y = np.zeros((Ho, Ho, co))
+            for ky in range(3):
+                for kx in range(3):
+                    patch = xp[ky:ky + 2 * Ho:2, kx:kx + 2 * Ho:2, :]      # (Ho, Ho, ci): rows 2 oy + ky - 1
+                    y += patch @ Wr[:, ky, kx, :].T
+            x = np.maximum(y + bias.astype(np.float64), 0.0).astype(np.float32)
+        f = np.concatenate([x.reshape(-1), (np.log(bounds[b]) - 6.5).astype(np.float32)])
+        (W1, b1), (W2, b2) = layers[4], layers[5]
+        h = np.maximum(rnd(W1) @ rnd(f) + b1, 0.0).astype(np.float32)
+        z = rnd(W2) @ rnd(h) + b2
+        out.append(np.where(z > 20.0, z, np.log1p(np.exp(np.minimum(z, 20.0)))))
+    return np.array(out)
+
+
+def hist_quantiles(hist, lo: float, hi: float):
+    """Pseudo-eigenvalues of a histogram over [lo, hi] (counts spread evenly inside each bin): with
+    N = round(total), value k (k = 1..N) is where the cumulative count reaches k - 1/2."""
+    h = np.asarray(hist, dtype=np.float64)
+    N = int(np.floor(h.sum() + 0.5))
+    edges = np.linspace(lo, hi, h.size + 1)
+    cum = np.concatenate([[0.0], np.cumsum(h)])
+    out = []
+    for k in range(1, N + 1):
+        t = min(k - 0.5, cum[-1])
+        j = int(np.searchsorted(cum, t, side="left")) - 1
+        j = min(max(j, 0), h.size - 1)
+        while h[j] == 0.0 and j < h.size - 1 and cum[j + 1] < t:
+            j += 1
+        frac = min(1.0, max(0.0, (t - cum[j]) / h[j])) if h[j] > 0 else 1.0
+        out.append(edges[j] + frac * (edges[j + 1] - edges[j]))
+    return np.array(out)

@@ -21,7 +21,10 @@ EXPORTED_SYMBOLS = [
     "gcie_solve", "gcie_solve_pencil", "gcie_solve_batch", "gcie_result_free", "gcie_buffer_free", "gcie_kde_contours", "gcie_plan_contours", "gcie_count_miss", "gcie_resplit", "gcie_trapezoid_nodes", "gcie_shifted_spmm_f32",
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc", "gcie_gemm_tf32x3", "gcie_gemm_bf16",
+    "gcie_density_net_create", "gcie_density_net_destroy", "gcie_density_predict", "gcie_hist_quantiles",
 ]
+DENSITY_NWEIGHTS = 717520
+DENSITY_BINS = 256
 
 
 class GcieError(RuntimeError):
@@ -115,6 +118,10 @@ def lib():
         "gcie_jacobi_eig_noalloc": (C.c_int, [vp, i32, vp, vp, vp]),
         "gcie_gemm_tf32x3": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32]),
         "gcie_gemm_bf16": (C.c_int, [vp, i32, i32, i32, vp, i32, vp, i32, vp, i32, vp, i32]),
+        "gcie_density_net_create": (C.c_int, [vp, vp, i64, C.POINTER(vp)]),
+        "gcie_density_net_destroy": (None, [vp]),
+        "gcie_density_predict": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
+        "gcie_hist_quantiles": (C.c_int, [vp, i32, d, d, vp, i32, C.POINTER(i32)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -435,3 +442,41 @@ def gcie_gemm_bf16(ctx, M: int, N: int, K: int, d_A, lda: int, d_B, ldb: int, d_
     """D = act(A B^T + bias) on the tensor cores, BF16 operands (device tensors of dtype bfloat16)."""
     _check(lib().gcie_gemm_bf16(ctx, int(M), int(N), int(K), _ptr(d_A), int(lda), _ptr(d_B), int(ldb), _ptr(d_bias),
                                 int(bool(relu)), _ptr(d_D), int(ldd)), "gcie_gemm_bf16")
+
+
+def gcie_density_net_create(ctx, weights):
+    """Upload the density predictor's weights (float32, the gcie.h order); returns the net handle."""
+    w = np.ascontiguousarray(weights, dtype=np.float32).ravel()
+    out = C.c_void_p()
+    _check(lib().gcie_density_net_create(ctx, w.ctypes.data, int(w.size), C.byref(out)), "gcie_density_net_create")
+    return out
+
+
+def gcie_density_net_destroy(net):
+    lib().gcie_density_net_destroy(net)
+
+
+def gcie_density_predict(ctx, net, kappa, rho, bounds) -> np.ndarray:
+    """Predicted eigenvalue histograms (batch x 256) from fields kappa, rho (batch x G x G) and bounds
+    (batch x 2: lo, hi)."""
+    k = np.ascontiguousarray(kappa, dtype=np.float32)
+    r = np.ascontiguousarray(rho, dtype=np.float32)
+    if k.ndim == 2:
+        k, r = k[None], r[None]
+    b = np.ascontiguousarray(bounds, dtype=np.float64).reshape(-1, 2)
+    B, G = k.shape[0], k.shape[1]
+    hist = np.zeros((B, DENSITY_BINS))
+    _check(lib().gcie_density_predict(ctx, net, B, G, k.ctypes.data, r.ctypes.data, b.ctypes.data, hist.ctypes.data),
+           "gcie_density_predict")
+    return hist
+
+
+def gcie_hist_quantiles(hist, lo: float, hi: float) -> np.ndarray:
+    """Pseudo-eigenvalues of a predicted histogram over [lo, hi]."""
+    h = np.ascontiguousarray(hist, dtype=np.float64)
+    cap = int(np.floor(h.sum() + 0.5)) + 1
+    out = np.zeros(cap)
+    nout = C.c_int32(0)
+    _check(lib().gcie_hist_quantiles(h.ctypes.data, int(h.size), float(lo), float(hi), out.ctypes.data, cap,
+                                     C.byref(nout)), "gcie_hist_quantiles")
+    return out[:nout.value].copy()

@@ -622,7 +622,7 @@ int gcie_gemm_bf16(gcie_ctx *c, int32_t M, int32_t N, int32_t K, const uint16_t 
         return GCIE_EINVAL;
     }
     cudaSetDevice(c->device);
-    return gemm_finish(c, gemm_bf16(c, M, N, K, d_A, lda, d_B, ldb, d_bias, relu, d_D, ldd));
+    return gemm_finish(c, gemm_bf16(c, M, N, K, d_A, lda, d_B, ldb, d_bias, relu ? 1 : 0, d_D, ldd));
 }
 
 int gcie_jacobi_eig_noalloc(void *stream, int32_t p, double *d_A, double *d_w, double *d_V)

@@ -3,8 +3,8 @@
 //   k_gemm_tf32x3  FP32 operands, FP32-faithful: each operand is split into a TF32 head and a TF32 tail
 //                  (x = hi + lo, hi = tf32(x), lo = tf32(x - hi)) and D = Ahi Bhi^T + Ahi Blo^T + Alo Bhi^T,
 //                  accumulated in FP32 in tensor memory (the dropped Alo Blo^T term is 2^-22 relative);
-//   k_gemm_bf16    BF16 operands, FP32 accumulation, epilogue D = act(A B^T + bias) (the inference layers of
-//                  the density predictor).
+//   k_gemm_bf16    BF16 operands, FP32 accumulation, epilogue D = act(A B^T + bias), act = identity, ReLU or
+//                  softplus, written in FP32 and/or BF16 (the inference layers of the density predictor).
 //
 // One CTA of 128 threads per 128 x BN tile of D.  Per K block (128 bytes of every row: 32 FP32 or 64 BF16
 // values) the threads copy the A and B tiles into shared memory in the canonical K-major layout (see
@@ -119,8 +119,8 @@ __global__ void __launch_bounds__(GT) k_gemm_tf32x3(int M, int N, int K, const f
 template <int BN>
 __global__ void __launch_bounds__(GT) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda,
                                                   const __nv_bfloat16 *__restrict__ B, int ldb,
-                                                  const float *__restrict__ bias, int relu, float *__restrict__ D, int ldd,
-                                                  unsigned int *status)
+                                                  const float *__restrict__ bias, int act, float *__restrict__ D, int ldd,
+                                                  __nv_bfloat16 *__restrict__ Dh, unsigned int *status)
 {
     constexpr int KB = KBYTES / 2;                       // 64 BF16 values per K block
     constexpr uint32_t TCOLS = BN < 32 ? 32 : BN;
@@ -185,8 +185,10 @@ __global__ void __launch_bounds__(GT) k_gemm_bf16(int M, int N, int K, const __n
                     const int col = n0 + cb + e;
                     if (col < N) {
                         float y = v[e] + (bias ? bias[col] : 0.f);
-                        if (relu) y = fmaxf(y, 0.f);
-                        D[(size_t)row * ldd + col] = y;
+                        if (act == 1) y = fmaxf(y, 0.f);
+                        else if (act == 2) y = y > 20.f ? y : log1pf(expf(y));   // softplus
+                        if (D) D[(size_t)row * ldd + col] = y;
+                        if (Dh) Dh[(size_t)row * ldd + col] = __float2bfloat16(y);
                     }
                 }
         }
@@ -215,8 +217,8 @@ int gemm_tf32x3(Ctx *c, int M, int N, int K, const float *A, int lda, const floa
     return GCIE_OK;
 }
 
-int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, int relu,
-              float *D, int ldd)
+int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, int act,
+              float *D, int ldd, void *Dh)
 {
     if (M <= 0 || N <= 0 || K <= 0) return GCIE_OK;
     const dim3 grid((M + GM - 1) / GM, (N + 63) / 64);
@@ -224,7 +226,7 @@ int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B
     GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     LaunchScope ls(c, GCIE_K_DENSE, 2.0 * ((double)M * K + (double)N * K) + 4.0 * M * N, 2.0 * M * N * K);
     k_gemm_bf16<64><<<grid, GT, smem, c->stream>>>(M, N, K, (const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb,
-                                                   bias, relu, D, ldd, &c->dbg->wait_timeouts);
+                                                   bias, act, D, ldd, (__nv_bfloat16 *)Dh, &c->dbg->wait_timeouts);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }

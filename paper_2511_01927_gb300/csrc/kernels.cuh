@@ -60,8 +60,9 @@ int resid_norms(Ctx *c, int64_t n, int q, const double *KZ, const double *MZ, co
 
 // tensor-core products D = A B^T (gemm.cu): FP32-faithful split TF32, and BF16 with bias and ReLU
 int gemm_tf32x3(Ctx *c, int M, int N, int K, const float *A, int lda, const float *B, int ldb, float *D, int ldd);
-int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, int relu,
-              float *D, int ldd);
+// act: 0 identity, 1 ReLU, 2 softplus; D (FP32) and Dh (BF16) outputs, either may be null
+int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B, int ldb, const float *bias, int act,
+              float *D, int ldd, void *Dh = nullptr);
 
 // a8: two-pass M-orthonormalisation; Q has *rank valid columns (row-major n x ldQ).
 int m_orthonormalize(Ctx *c, const Pencil *p, int64_t n, int ncol, const double *Y, double drop, double *Q,

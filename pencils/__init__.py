@@ -21,7 +21,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "Csr", "fem1d", "fem2d_p1", "fem2d_p1_rect", "fem2d_p1_strip", "grf_lognormal", "fem2d_p1_lognormal", "fem_q1",
-    "octant_coefficients", "gaussian_block", "fem1d_eigenvalue", "workload", "WORKLOADS",
+    "octant_coefficients", "gaussian_block", "fem1d_eigenvalue", "workload", "WORKLOADS", "family_member",
 ]
 
 
@@ -160,6 +160,16 @@ def fem2d_p1_lognormal(nc: int, seeds=(2, 3), sigma: float = 1.0, ell: float = 0
     kappa = grf_lognormal(nc, ell, sigma, seeds[0])
     rho = grf_lognormal(nc, ell, sigma, seeds[1])
     return fem2d_p1(nc, kappa, rho)
+
+
+def family_member(seed: int, nc: int = 256):
+    """Member `seed` of the learned-contour family: the 2D log-normal P1 pencil on nc x nc cells with the
+    fields of seeds (2 seed + 10, 2 seed + 11).  Returns (K, M, kappa, rho), the fields on the cell grid
+    (the density predictor's input)."""
+    kappa = grf_lognormal(nc, 0.1, 1.0, 2 * seed + 10)
+    rho = grf_lognormal(nc, 0.1, 1.0, 2 * seed + 11)
+    K, M = fem2d_p1(nc, kappa, rho)
+    return K, M, kappa, rho
 
 
 # --------------------------------------------------------------------------- Q1 (2D/3D)
