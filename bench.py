@@ -51,7 +51,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="fem2d-p1-500")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--contours", default="uniform", choices=["uniform", "kde", "planned"])
+    ap.add_argument("--contours", default="uniform", choices=["uniform", "kde", "planned", "learned"])
+    ap.add_argument("--seeds", type=int, default=200,
+                    help="with --contours learned: held-out members of the 256 x 256 family to solve")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="shifted solves: FP32 COCG with FP64 refinement (mixed) or FP64 COCG (fp64); both "
                          "with the FP32 band factors as preconditioner")
@@ -292,6 +294,160 @@ def e2e_measure(G, ctx, K, M, spec, opts, steps):
     return {"value": cnt / sec, "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
 
+# ----------------------------------------------------------------------------- batched serving
+def run_serving(args):
+    """64 independent pencils of uneven size (pencils.serving_batch: alternating 2D P1, n 10k-200k, and 3D
+    Q1, n 10k-27k, intervals of about 20-200 eigenvalues), solved by one gcie_solve_batch call from host
+    CSR buffers (ingest, solve, eigenpairs out): `--steps` timed calls with 4 pencils in flight
+    (batch_streams = 4, the library's scheduler), then one call with the pencils one after another
+    (batch_streams = 1) on the same inputs; counts must agree pencil by pencil.  4 uniform contours x 16
+    nodes, L = 64, 2 moments."""
+    import torch
+    import paper_2511_01927_gb300 as G
+
+    batch = P.serving_batch(64, 6)
+    items = [(K, M, lo, hi) for K, M, lo, hi, _ in batch]
+    ctx = G.gcie_create(0)
+    opts = dict(nuniform=4, nodes=16, L=64, moments=2, tol=1e-10, lin_tol=1e-11)
+
+    def run(streams):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        outs = G.gcie_solve_batch(ctx, items, allow_noconv=True, batch_streams=streams, **opts)
+        torch.cuda.synchronize()
+        return outs, time.perf_counter() - t0
+
+    for _ in range(max(1, args.warmup)):
+        run(4)
+    G.gcie_reset_stats(ctx)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    secs, pairs, outs = 0.0, 0, None
+    for _ in range(args.steps):
+        outs, s = run(4)
+        secs += s
+        pairs += sum(len(o["evals"]) for o in outs)
+    clk = clocks.stop()
+    launches = int(G.gcie_get_stats(ctx)["total_launches"])
+    seq, s1 = run(1)
+    counts = [len(o["evals"]) for o in outs]
+    agree = all(len(a["evals"]) == c for a, c in zip(seq, counts))
+    worst = max(float(np.max(o["resid"])) for o in outs if len(o["resid"]))
+    G.gcie_destroy(ctx)
+    value = pairs / secs
+    out = {"metric": "converged eigenpairs/s at residual<=1e-10, batched serving", "value": value, "unit": UNIT,
+           "n_gpus": 1, "steps": args.steps, "warmup": max(1, args.warmup), "ms_per_step": 1e3 * secs / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
+           "config": {"workload": "serving: 64 pencils, 2D P1 n 10k-200k / 3D Q1 n 10k-27k, 20-200 eigenvalues each",
+                      "n_total": int(sum(K.n for K, _, _, _ in items)), "pairs_per_step": int(sum(counts)),
+                      "contours": 4, "nodes": 16, "L": 64, "moments": 2, "batch_streams": 4, "max_resid": worst,
+                      "status_not_ok": int(sum(1 for o in outs if o["rc"] != 0))},
+           "sequential": {"value": sum(counts) / s1, "seconds": s1, "counts_agree": agree},
+           "speedup_over_sequential": value / (sum(counts) / s1),
+           "gpu_launches": launches, "clocks": clk,
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": int(sum(K.val.nbytes + K.col.nbytes + K.rowptr.nbytes
+                                                                              + M.val.nbytes + M.col.nbytes + M.rowptr.nbytes
+                                                                              for K, M, _, _ in items)),
+                   "d2h_bytes_per_step": int(sum(o["evecs"].nbytes + o["evals"].nbytes for o in outs))}}
+    print(json.dumps(out))
+
+
+# ----------------------------------------------------------------------------- learned contours
+LEARNED_LO, LEARNED_HI = 300.0, 900.0      # target interval of the learned-contour comparison
+LEARNED_FIRST = 100000                     # held-out members (training used seeds 0..1999)
+
+
+def run_learned(args):
+    """Learned vs uniform contours on held-out members of the 256 x 256 log-normal family (the density
+    predictor's family), target interval [300, 900], 8 contours x 16 nodes, L = 64, 2 moments.  Per member:
+      uniform: 8 equal-width contours;
+      learned: GPU prediction of the interval's eigenvalue histogram from the coefficient fields, its
+               quantiles as the predicted spectrum, 8 contours cut in its gaps (gcie_plan_contours), the
+               judged solve (count check on);
+      kde:     the same prediction through Algorithm 2 (N_min 10, N_max 50, w 10), judged solve.
+    Each arm is timed wall-clock around its calls (prediction and planning included), the stream drained
+    on both sides; the ingested pencil and V are shared.  Counts of the arms must agree on every member."""
+    import torch
+    import paper_2511_01927_gb300 as G
+
+    w = np.load(os.path.join(ROOT, "paper_2511_01927_gb300", "density_net.npz"))["w"]
+    ctx = G.gcie_create(0, torch.cuda.current_stream().cuda_stream)
+    net = G.gcie_density_net_create(ctx, w)
+    lo, hi = LEARNED_LO, LEARNED_HI
+    common = dict(nodes=16, L=64, moments=2, tol=1e-10, lin_tol=1e-11)
+    arms = ("uniform", "learned", "kde")
+    tot = {a: 0.0 for a in arms}
+    pairs = {a: 0 for a in arms}
+    passes = {a: [] for a in arms}
+    resplits = {a: 0 for a in arms}
+    agree, pred_err, ncont = 0, [], {"learned": [], "kde": []}
+
+    def solve(arm, pen, K, kappa, rho, V):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if arm == "uniform":
+            r = G.gcie_solve_pencil(ctx, pen, lo, hi, nuniform=8, V0=V, allow_noconv=True, **common)
+            pc = None
+        else:
+            hist = G.gcie_density_predict(ctx, net, kappa[None], rho[None], [[lo, hi]])[0]
+            pred = G.gcie_hist_quantiles(hist, lo, hi)
+            if arm == "learned":
+                cts = G.gcie_plan_contours(pred, lo, hi, 8)
+            else:
+                cts = G.gcie_kde_contours(pred, nmin=10, nmax=50, w=10.0)
+            edges = [lo] + [c[1] for c in cts[:-1]] + [hi]
+            contours = [(0.5 * (a + b), 0.5 * (b - a), a, b) for a, b in zip(edges[:-1], edges[1:])]
+            r = G.gcie_solve_pencil(ctx, pen, lo, hi, contours=contours, judge=1, V0=V, allow_noconv=True, **common)
+            pc = (float(hist.sum()), len(contours))
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0, pc
+
+    members = list(range(LEARNED_FIRST, LEARNED_FIRST + args.seeds))
+    # warm-up: every arm once on the first member (not counted)
+    K, M, kappa, rho = P.family_member(members[0])
+    pen = G.gcie_pencil_create(ctx, K, M)
+    for arm in arms:
+        solve(arm, pen, K, kappa, rho, P.gaussian_block(K.n, 64, 1))
+    G.gcie_pencil_destroy(pen)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    for seed in members:
+        K, M, kappa, rho = P.family_member(seed)
+        pen = G.gcie_pencil_create(ctx, K, M)
+        V = P.gaussian_block(K.n, 64, seed)
+        counts = {}
+        for arm in arms:
+            r, sec, pc = solve(arm, pen, K, kappa, rho, V)
+            tot[arm] += sec
+            pairs[arm] += len(r["evals"])
+            counts[arm] = len(r["evals"])
+            passes[arm].append(max(r["iters"]))
+            resplits[arm] += r["resplits"]
+            if pc is not None:
+                ncont[arm].append(pc[1])
+                if arm == "learned":
+                    pred_err.append(abs(pc[0] - len(r["evals"])) / max(1, len(r["evals"])))
+        agree += len(set(counts.values())) == 1
+        G.gcie_pencil_destroy(pen)
+    clk = clocks.stop()
+    G.gcie_density_net_destroy(net)
+    G.gcie_destroy(ctx)
+    val = {a: pairs[a] / tot[a] for a in arms}
+    out = {"metric": "converged eigenpairs/s at residual<=1e-10, learned vs uniform contours", "value": val["learned"],
+           "unit": UNIT, "n_gpus": 1, "steps": len(members), "warmup": 1, "ms_per_step": 1e3 * tot["learned"] / len(members),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
+           "config": {"workload": "fem2d-p1-256 family, held-out members " + f"{members[0]}..{members[-1]}",
+                      "n": 65025, "interval": [lo, hi], "contours": 8, "nodes": 16, "L": 64, "moments": 2, "tol": 1e-10,
+                      "predictor": "density net (BF16, tcgen05), trained on members 0..1999 solved by this library"},
+           "arms": {a: {"value": val[a], "seconds": tot[a], "pairs": pairs[a],
+                        "mean_feast_passes": float(np.mean(passes[a])), "resplits": resplits[a]} for a in arms},
+           "learned_over_uniform": val["learned"] / val["uniform"], "kde_over_uniform": val["kde"] / val["uniform"],
+           "count_agreement": agree / len(members),
+           "predicted_count_rel_error": float(np.mean(pred_err)),
+           "kde_contours_mean": float(np.mean(ncont["kde"])), "clocks": clk}
+    print(json.dumps(out))
+
+
 # ----------------------------------------------------------------------------- CPU oracle baseline
 REDUCED = "fem2d-p1-160"   # the reduced member of the 500 x 500 workload the oracle solves whole
 
@@ -334,6 +490,12 @@ def main():
     args = parse()
     if args.profile_case:
         profile_case(args)
+        return
+    if args.contours == "learned":
+        run_learned(args)
+        return
+    if args.workload == "serving":
+        run_serving(args)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -101,6 +101,8 @@ typedef struct {
     int32_t max_resplit;    /* levels of re-splitting below an input contour, 0..16 (default 4); a
                                contour that still fails at the last level keeps its pairs and
                                reports GCIE_ENOCONV */
+    int32_t batch_streams;  /* gcie_solve_batch: pencils solved at the same time, each by its own host
+                               thread on its own stream (1..16; default 4) */
 } gcie_opts;
 
 /* Results: library-allocated host arrays, released by gcie_result_free. */
@@ -179,12 +181,16 @@ int gcie_solve(gcie_ctx *ctx, const gcie_csr *K, const gcie_csr *M, double lo, d
                const gcie_opts *opts, gcie_result *out);
 int gcie_solve_pencil(gcie_ctx *ctx, gcie_pencil *p, double lo, double hi, const gcie_opts *opts,
                       gcie_result *out);
-/* Independent pencils (the serving case): pencil i is K[i], M[i] with the interval [lo[i], hi[i]],
- * solved into out[i] with the same options, one after another on the context's stream (the pencils
- * share nothing, so they can also go to different contexts or GPUs).  K, M, lo, hi, out: host
- * arrays of npencils >= 1; each out[i] is released with gcie_result_free.  A pencil that ends with
- * GCIE_ENOCONV does not stop the batch; any other error does, leaving the later results zeroed.
- * Returns GCIE_OK when every solve did, else the first status other than GCIE_OK. */
+/* Independent pencils (the serving case; Algorithm 1 treats contours, and so pencils, as independent):
+ * pencil i is K[i], M[i] with the interval [lo[i], hi[i]], solved into out[i] with the same options.
+ * opts.batch_streams pencils are solved at the same time: a scheduler hands the pencils, largest first,
+ * to that many host threads, each driving its own context (stream, memory pool) on the context's device
+ * (the first one is ctx itself), so the small pencils' latency-bound kernels overlap on the GPU.  Each
+ * solve may use 1/batch_streams of the device-memory budget.  K, M, lo, hi, out: host arrays of
+ * npencils >= 1; each out[i] is released with gcie_result_free.  A pencil that ends with GCIE_ENOCONV
+ * does not stop the batch; any other error stops the scheduler from starting further pencils (those
+ * results stay zeroed).  Kernel statistics of all workers are added to ctx's.
+ * Returns GCIE_OK when every solve did, else the status of the lowest-numbered pencil that failed. */
 int gcie_solve_batch(gcie_ctx *ctx, int32_t npencils, const gcie_csr *K, const gcie_csr *M, const double *lo,
                      const double *hi, const gcie_opts *opts, gcie_result *out);
 void gcie_result_free(gcie_result *r);

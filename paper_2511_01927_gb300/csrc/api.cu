@@ -2,6 +2,7 @@
 // (Algorithm 1 with the moment method and subspace iteration of Appendix A.3.3), and the
 // per-step device-pointer entry points.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -242,6 +243,7 @@ void gcie_default_opts(gcie_opts *o)
     o->precond = 1;
     o->judge = 0;
     o->max_resplit = 4;
+    o->batch_streams = 4;
 }
 
 int gcie_create(gcie_ctx **out, int device, void *stream)
@@ -299,6 +301,8 @@ int gcie_create(gcie_ctx **out, int device, void *stream)
 void gcie_destroy(gcie_ctx *c)
 {
     if (!c) return;
+    for (gcie_ctx *w : c->workers) gcie_destroy(w);
+    c->workers.clear();
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     flush_timing(c);
@@ -1325,7 +1329,7 @@ int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const g
         o.max_iters < 1 || !(o.tol > 0) || !(o.lin_tol > 0) || (o.precision != GCIE_MIXED && o.precision != GCIE_FP64) ||
         o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0 ||
         o.precond < GCIE_PREC_NONE || o.precond > GCIE_PREC_BAND || o.judge < 0 || o.judge > 1 || o.max_resplit < 0 ||
-        o.max_resplit > 16) {
+        o.max_resplit > 16 || o.batch_streams < 1 || o.batch_streams > 16) {
         set_error("solve: option out of range");
         return GCIE_EINVAL;
     }
@@ -1356,17 +1360,79 @@ int gcie_solve_batch(gcie_ctx *c, int32_t npencils, const gcie_csr *K, const gci
                      const double *hi, const gcie_opts *opts, gcie_result *out)
 {
     if (!c || !K || !M || !lo || !hi || !out || npencils < 1) { set_error("solve_batch: null argument or no pencil"); return GCIE_EINVAL; }
+    if (c->unusable) { set_error("context unusable after an unconfirmed device copy: destroy and recreate it"); return GCIE_ECONTEXT; }
     for (int32_t i = 0; i < npencils; ++i) std::memset(&out[i], 0, sizeof(out[i]));
-    int first = GCIE_OK;
-    for (int32_t i = 0; i < npencils; ++i) {
-        const int rc = gcie_solve(c, &K[i], &M[i], lo[i], hi[i], opts, &out[i]);
-        if (rc != GCIE_OK && first == GCIE_OK) first = rc;
-        if (rc != GCIE_OK && rc != GCIE_ENOCONV) {
-            set_error("solve_batch: pencil " + std::to_string(i) + ": " + gcie_last_error());
-            break;
-        }
+    gcie_opts o;
+    if (opts) o = *opts; else gcie_default_opts(&o);
+    if (o.batch_streams < 1 || o.batch_streams > 16) { set_error("solve_batch: batch_streams must be 1..16"); return GCIE_EINVAL; }
+    const int W = std::min<int>(o.batch_streams, npencils);
+    // each concurrent solve gets its share of the device memory
+    if (W > 1 && !o.hbm_budget_bytes) {
+        size_t free_b = 0, total_b = 0;
+        cudaSetDevice(c->device);
+        cudaMemGetInfo(&free_b, &total_b);
+        o.hbm_budget_bytes = (size_t)(0.85 * (double)(free_b + ctx_pool_idle(c)) / W);
+    } else if (W > 1) {
+        o.hbm_budget_bytes /= W;
     }
-    return first;
+    // largest pencils first, so that the tail of the batch is short
+    std::vector<int32_t> order(npencils);
+    for (int32_t i = 0; i < npencils; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return K[a].n > K[b].n; });
+    std::vector<int> rcs(npencils, GCIE_OK);
+    std::vector<std::string> msgs(npencils);
+    std::atomic<int32_t> next{0};
+    std::atomic<bool> stop{false};
+    // worker contexts (created on first use, kept in ctx for later batches)
+    while ((int)c->workers.size() < W - 1) {
+        gcie_ctx *wc = nullptr;
+        const int rcw = gcie_create(&wc, c->device, nullptr);
+        if (rcw != GCIE_OK) return rcw;
+        c->workers.push_back(wc);
+    }
+    std::vector<gcie_ctx *> wctx(W, nullptr);
+    wctx[0] = c;
+    for (int w = 1; w < W; ++w) {
+        wctx[w] = c->workers[w - 1];
+        gcie_reset_stats(wctx[w]);
+    }
+    auto work = [&](int w) {
+        for (;;) {
+            if (stop.load()) return;
+            const int32_t k = next.fetch_add(1);
+            if (k >= npencils) return;
+            const int32_t i = order[k];
+            const int rc = gcie_solve(wctx[w], &K[i], &M[i], lo[i], hi[i], &o, &out[i]);
+            rcs[i] = rc;
+            if (rc != GCIE_OK) msgs[i] = gcie_last_error();
+            if (rc != GCIE_OK && rc != GCIE_ENOCONV) stop.store(true);
+        }
+    };
+    if (W == 1) {
+        work(0);
+    } else {
+        std::vector<std::thread> th;
+        for (int w = 1; w < W; ++w) th.emplace_back(work, w);
+        work(0);
+        for (auto &t : th) t.join();
+    }
+    for (int w = 1; w < W; ++w) {
+        gcie_stats st{};
+        gcie_get_stats(wctx[w], &st);
+        for (int k = 0; k < GCIE_K_NCLASS; ++k) {
+            c->stats.launches[k] += st.launches[k];
+            c->stats.ms[k] += st.ms[k];
+            c->stats.bytes[k] += st.bytes[k];
+            c->stats.flops[k] += st.flops[k];
+        }
+        c->stats.total_launches += st.total_launches;
+    }
+    for (int32_t i = 0; i < npencils; ++i)
+        if (rcs[i] != GCIE_OK) {
+            set_error("solve_batch: pencil " + std::to_string(i) + ": " + msgs[i]);
+            return rcs[i];
+        }
+    return GCIE_OK;
 }
 
 void gcie_buffer_free(void *p) { std::free(p); }

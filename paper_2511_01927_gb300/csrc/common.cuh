@@ -4,10 +4,14 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <array>
+#include <map>
 #include <string>
 #include <vector>
 
 #include "gcie.h"
+
+struct gcie_ctx;
 
 namespace gcie {
 
@@ -93,6 +97,9 @@ struct Ctx {
     void *h_stage = nullptr;         // pinned host staging for results copied out (grown on demand)
     size_t h_stage_bytes = 0;
     bool unusable = false;           // set after a drain timeout (GCIE_ECONTEXT): every later call fails
+    std::vector<gcie_ctx *> workers; // extra contexts of gcie_solve_batch (own streams and pools), kept for reuse
+    // band-sweep autotuner: fastest columns-per-CTA for (bandwidth, columns, active shifts), timed on first use
+    std::map<std::array<int, 3>, int> band_sc;
 };
 
 // Stream-ordered allocation from the context's pool.  The pool keeps what it has reserved between

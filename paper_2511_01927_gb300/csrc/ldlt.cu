@@ -831,10 +831,51 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
         if (!best || cost < best_cost) { best = sc; best_cost = cost; }
     }
     if (!best) { set_error("band sweep: bandwidth too large for shared memory"); return GCIE_EINVAL; }
-    // GCIE_BAND_SC = 8 | 16 | 32 forces the column count per CTA (tuning and tests of every variant)
+    // GCIE_BAND_SC = 8 | 16 | 32 forces the column count per CTA (tests of every variant); otherwise the
+    // autotuner times every variant on the first application for this (bandwidth, columns, active
+    // shifts) and keeps the fastest for the context (GCIE_BAND_TUNE=0: the cost model's choice above)
+    bool forced = false;
     if (const char *e = std::getenv("GCIE_BAND_SC")) {
         const int v = std::atoi(e);
-        if ((v == 8 || v == 16 || v == 32) && band_smem_solve(b, v) <= c->smem_optin) best = v;
+        if ((v == 8 || v == 16 || v == 32) && band_smem_solve(b, v) <= c->smem_optin) { best = v; forced = true; }
+    }
+    const char *tune_env = std::getenv("GCIE_BAND_TUNE");
+    const bool tune = !forced && !(tune_env && std::atoi(tune_env) == 0) && !std::getenv("GCIE_TEST_STOP_COPY");
+    const std::array<int, 3> key{b, ncol, nact};
+    if (tune) {
+        auto it = c->band_sc.find(key);
+        if (it != c->band_sc.end()) {
+            best = it->second;
+        } else {
+            // every feasible variant once (each writes the same Z), the fastest kept
+            float best_ms = 0.f;
+            int pick = best;
+            for (int sc : {32, 16, 8}) {
+                if (band_smem_solve(b, sc) > c->smem_optin) continue;
+                cudaEvent_t e0, e1;
+                GCIE_CUDA_TRY(cudaEventCreate(&e0));
+                GCIE_CUDA_TRY(cudaEventCreate(&e1));
+                const int ng = (ncol + sc - 1) / sc;
+                const double mac = 2.0 * nact * n * b * ncol;
+                int rc;
+                {
+                    LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4), 8.0 * mac);
+                    cudaEventRecord(e0, c->stream);
+                    rc = sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX)
+                         : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX)
+                                    : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX);
+                    cudaEventRecord(e1, c->stream);
+                }
+                float ms = 0.f;
+                if (rc == GCIE_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                if (rc != GCIE_OK) return rc;
+                if (pick == 0 || best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = sc; }
+            }
+            c->band_sc[key] = pick;
+            return GCIE_OK;
+        }
     }
     const int ngrp = (ncol + best - 1) / best;
     const double macs = 2.0 * nact * n * b * ncol;

@@ -21,7 +21,7 @@ import scipy.sparse as sp
 
 __all__ = [
     "Csr", "fem1d", "fem2d_p1", "fem2d_p1_rect", "fem2d_p1_strip", "grf_lognormal", "fem2d_p1_lognormal", "fem_q1",
-    "octant_coefficients", "gaussian_block", "fem1d_eigenvalue", "workload", "WORKLOADS", "family_member",
+    "octant_coefficients", "gaussian_block", "fem1d_eigenvalue", "workload", "WORKLOADS", "family_member", "serving_batch",
 ]
 
 
@@ -160,6 +160,37 @@ def fem2d_p1_lognormal(nc: int, seeds=(2, 3), sigma: float = 1.0, ell: float = 0
     kappa = grf_lognormal(nc, ell, sigma, seeds[0])
     rho = grf_lognormal(nc, ell, sigma, seeds[1])
     return fem2d_p1(nc, kappa, rho)
+
+
+def serving_batch(count: int = 64, seed: int = 6):
+    """The serving workload: `count` independent pencils of uneven size, alternating a 2D P1 pencil with
+    log-normal fields (n = (nc - 1)^2 drawn from U[10k, 200k]) and a 3D Q1 pencil with octant coefficients
+    (n = (nc - 1)^3 from U[10k, 27k], where its band stays within the shared-memory sweeps).  Each gets an
+    interval meant to hold k ~ U[20, 200] eigenvalues, placed with Weyl's law for -div(kappa grad u) =
+    lambda rho u (2D: N(lambda) ~ lambda mean(rho / kappa) / (4 pi); 3D: N(lambda) ~ lambda^(3/2)
+    mean((rho / kappa)^(3/2)) / (6 pi^2)), from N = 4.5 to N = 4.5 + k.  Returns a list of
+    (K, M, lo, hi, kind)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        k = int(rng.integers(20, 201))
+        if i % 2 == 0:
+            nc = int(round(np.sqrt(rng.uniform(10_000, 200_000)))) + 1
+            kappa = grf_lognormal(nc, 0.1, 1.0, 1000 + 2 * i)
+            rho = grf_lognormal(nc, 0.1, 1.0, 1001 + 2 * i)
+            K, M = fem2d_p1(nc, kappa, rho)
+            c = float(np.mean(rho / kappa)) / (4.0 * np.pi)
+            lam = lambda N: N / c
+            kind = "2d-p1"
+        else:
+            nc = int(round(rng.uniform(10_000, 27_000) ** (1.0 / 3.0))) + 1
+            ck, cm = octant_coefficients(3, 2000 + 2 * i), octant_coefficients(3, 2001 + 2 * i)
+            K, M = fem_q1(nc, 3, ck, cm)
+            c = float(np.mean((cm / ck) ** 1.5)) / (6.0 * np.pi ** 2)
+            lam = lambda N: (N / c) ** (2.0 / 3.0)
+            kind = "3d-q1"
+        out.append((K, M, lam(4.5), lam(4.5 + k), kind))
+    return out
 
 
 def family_member(seed: int, nc: int = 256):

@@ -403,3 +403,21 @@ def test_solve_batch_of_uneven_pencils(G, ctx, small2d):
         assert np.max(o["resid"]) <= 1e-10
     with pytest.raises(G.GcieError):
         G.gcie_solve_batch(ctx, [(K2, M2, 1.0, 0.5)])
+
+
+def test_solve_batch_concurrent_equals_sequential(G, ctx):
+    """The batch scheduler (several pencils in flight on their own streams) returns, pencil by pencil, the
+    result of solving them one after another, and each set is the definition's (inertia count)."""
+    import pencils as PP
+    batch = PP.serving_batch(5, 17)
+    items = []
+    for K, M, lo, hi, kind in batch:
+        if K.n > 60000:                              # keep the oracle inertia counts quick
+            continue
+        items.append((K, M, lo, hi))
+    a = G.gcie_solve_batch(ctx, items, L=32, nuniform=4, batch_streams=1, seed=3, allow_noconv=True)
+    b = G.gcie_solve_batch(ctx, items, L=32, nuniform=4, batch_streams=4, seed=3, allow_noconv=True)
+    for (K, M, lo, hi), x, y in zip(items, a, b):
+        assert len(x["evals"]) == len(y["evals"]) == O.count_in(K, M, lo, hi)
+        assert np.array_equal(x["evals"], y["evals"])
+        assert np.max(y["resid"]) <= 1e-10
