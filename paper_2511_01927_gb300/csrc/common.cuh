@@ -119,6 +119,17 @@ struct LaunchScope {
     ~LaunchScope();
 };
 
+// Let a kernel use the largest dynamic shared memory the device offers (the opt-in limit minus its static
+// shared memory).  Every caller sets the same value, so host threads that launch the same kernel with
+// different sizes (concurrent solves) cannot race on the attribute; a launch asks only for what it needs.
+inline cudaError_t allow_max_smem(const void *kernel, size_t optin)
+{
+    cudaFuncAttributes a;
+    cudaError_t e = cudaFuncGetAttributes(&a, kernel);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(optin - a.sharedSizeBytes));
+}
+
 // device scratch of at least `bytes` (reused; contents undefined)
 int ctx_scratch(Ctx *c, size_t bytes, void **out);
 

@@ -196,7 +196,7 @@ int gemm_tall(Ctx *c, int64_t n, int p, int q, const double *Y, int ldY, const d
     nchunk = (n + rpc - 1) / rpc;
     const size_t smem = sizeof(double) * (size_t)p * QB;
     if (smem > c->smem_optin) { set_error("gemm_tall: p too large"); return GCIE_EINVAL; }
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tall, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GCIE_CUDA_TRY(allow_max_smem((const void *)k_gemm_tall, c->smem_optin));
     LaunchScope ls(c, GCIE_K_DENSE, 8.0 * n * (p + q), 2.0 * n * p * q);
     k_gemm_tall<<<dim3((unsigned)nchunk, qblocks), threads, smem, c->stream>>>(n, p, q, QB, rpc, Y, ldY, T, Z, ldZ, c->dbg);
     GCIE_CUDA_TRY(cudaGetLastError());
@@ -560,7 +560,7 @@ int jacobi_batch(Ctx *c, int nmat, const int *h_p, double *const *h_A, double *c
     if (nmat <= 0) return GCIE_OK;
     const size_t smem = jacobi_cl_smem(pmax);
     if (smem > c->smem_optin) { set_error("jacobi_batch: shared memory"); return GCIE_EINVAL; }
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_jacobi_cl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GCIE_CUDA_TRY(allow_max_smem((const void *)k_jacobi_cl, c->smem_optin));
     LaunchScope ls(c, GCIE_K_DENSE, work, 0);
     for (int i0 = 0; i0 < nmat; i0 += JB) {
         const int cnt = std::min(JB, nmat - i0);

@@ -210,7 +210,7 @@ int gemm_tf32x3(Ctx *c, int M, int N, int K, const float *A, int lda, const floa
     if (M <= 0 || N <= 0 || K <= 0) return GCIE_OK;
     const dim3 grid((M + GM - 1) / GM, (N + 63) / 64);
     const size_t smem = gemm_smem_tf32x3(64);
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tf32x3<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GCIE_CUDA_TRY(allow_max_smem((const void *)k_gemm_tf32x3<64>, c->smem_optin));
     LaunchScope ls(c, GCIE_K_DENSE, 4.0 * ((double)M * K + (double)N * K + (double)M * N), 2.0 * M * N * K);
     k_gemm_tf32x3<64><<<grid, GT, smem, c->stream>>>(M, N, K, A, lda, B, ldb, D, ldd, &c->dbg->wait_timeouts);
     GCIE_CUDA_TRY(cudaGetLastError());
@@ -223,7 +223,7 @@ int gemm_bf16(Ctx *c, int M, int N, int K, const void *A, int lda, const void *B
     if (M <= 0 || N <= 0 || K <= 0) return GCIE_OK;
     const dim3 grid((M + GM - 1) / GM, (N + 63) / 64);
     const size_t smem = gemm_smem_bf16(64);
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_gemm_bf16<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GCIE_CUDA_TRY(allow_max_smem((const void *)k_gemm_bf16<64>, c->smem_optin));
     LaunchScope ls(c, GCIE_K_DENSE, 2.0 * ((double)M * K + (double)N * K) + 4.0 * M * N, 2.0 * M * N * K);
     k_gemm_bf16<64><<<grid, GT, smem, c->stream>>>(M, N, K, (const __nv_bfloat16 *)A, lda, (const __nv_bfloat16 *)B, ldb,
                                                    bias, act, D, ldd, (__nv_bfloat16 *)Dh, &c->dbg->wait_timeouts);

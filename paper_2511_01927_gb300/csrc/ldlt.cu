@@ -778,11 +778,11 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
         const double macs = (double)nshift * n * b * (b + 1) / 2.0;
         LaunchScope ls(c, GCIE_K_FACTOR, (double)nshift * n * (b + 1) * 16, 8.0 * macs);
         if (use_tc) {
-            GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            GCIE_CUDA_TRY(allow_max_smem((const void *)k_band_ldlt_tc, c->smem_optin));
             k_band_ldlt_tc<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status,
                                                                  &c->dbg->wait_timeouts);
         } else {
-            GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_ldlt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            GCIE_CUDA_TRY(allow_max_smem((const void *)k_band_ldlt, c->smem_optin));
             k_band_ldlt<<<nshift * KC, KT, smem, c->stream>>>(n, b, d_ABp, band_ab_offset(n, b), d_status);
         }
         GCIE_CUDA_TRY(cudaGetLastError());
@@ -807,7 +807,7 @@ static int launch_band_solve(Ctx *c, int64_t n, int b, int nshift, int ncol, con
                              const float2 *R, float2 *Z, int64_t stop_issue)
 {
     const size_t smem = band_smem_solve(b, SC);
-    GCIE_CUDA_TRY(cudaFuncSetAttribute(k_band_solve<SC>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    GCIE_CUDA_TRY(allow_max_smem((const void *)k_band_solve<SC>, c->smem_optin));
     const int ngrp = (ncol + SC - 1) / SC;
     k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z, c->dbg, stop_issue);
     GCIE_CUDA_TRY(cudaGetLastError());
@@ -839,6 +839,18 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
         const int v = std::atoi(e);
         if ((v == 8 || v == 16 || v == 32) && band_smem_solve(b, v) <= c->smem_optin) { best = v; forced = true; }
     }
+    // GCIE_SWEEP_TC=1: the block updates on the tensor cores (b <= 504; window in tensor memory).  Correct but,
+    // as measured on the 500 x 500 workload, slower than the CUDA-core sweeps (181 against 107 ms per
+    // launch: the per-step chain of TMEM reads, barriers, operand splits and 24 small MMAs), so not the default.
+    const char *tc_env = std::getenv("GCIE_SWEEP_TC");
+    const bool use_tc = b <= 504 && tc_env && std::atoi(tc_env) == 1 && band_smem_solve_tc(b, 32) <= c->smem_optin;
+    auto variant = [&](int sc, int64_t stop) -> int {
+        if (use_tc) return launch_band_solve_tc(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
+        return sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
+               : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
+                          : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop);
+    };
+    auto feasible = [&](int sc) { return use_tc ? band_smem_solve_tc(b, sc) <= c->smem_optin : band_smem_solve(b, sc) <= c->smem_optin; };
     const char *tune_env = std::getenv("GCIE_BAND_TUNE");
     const bool tune = !forced && !(tune_env && std::atoi(tune_env) == 0) && !std::getenv("GCIE_TEST_STOP_COPY");
     const std::array<int, 3> key{b, ncol, nact};
@@ -851,7 +863,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
             float best_ms = 0.f;
             int pick = best;
             for (int sc : {32, 16, 8}) {
-                if (band_smem_solve(b, sc) > c->smem_optin) continue;
+                if (!feasible(sc)) continue;
                 cudaEvent_t e0, e1;
                 GCIE_CUDA_TRY(cudaEventCreate(&e0));
                 GCIE_CUDA_TRY(cudaEventCreate(&e1));
@@ -861,9 +873,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
                 {
                     LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4), 8.0 * mac);
                     cudaEventRecord(e0, c->stream);
-                    rc = sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX)
-                         : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX)
-                                    : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, INT64_MAX);
+                    rc = variant(sc, INT64_MAX);
                     cudaEventRecord(e1, c->stream);
                 }
                 float ms = 0.f;
@@ -871,7 +881,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
                 cudaEventDestroy(e0);
                 cudaEventDestroy(e1);
                 if (rc != GCIE_OK) return rc;
-                if (pick == 0 || best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = sc; }
+                if (best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = sc; }
             }
             c->band_sc[key] = pick;
             return GCIE_OK;
@@ -885,9 +895,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     // (checked here, right after the launch, only in this test mode)
     int64_t stop_issue = INT64_MAX;
     if (const char *e = std::getenv("GCIE_TEST_STOP_COPY")) stop_issue = std::max<int64_t>(1, std::atoll(e));
-    int rc = best == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue)
-             : best == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue)
-                          : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop_issue);
+    int rc = variant(best, stop_issue);
     if (rc == GCIE_OK && stop_issue != INT64_MAX) {
         unsigned int to = 0;
         GCIE_CUDA_TRY(cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream));

@@ -31,6 +31,10 @@ __global__ void k_band_ldlt_tc(int64_t n, int b, float2 *const *ABp, size_t ab_o
 size_t band_smem_solve(int b, int sc);
 int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 *const *d_ABp,
                 const std::vector<float2 *> &h_ABp);
+// the sweeps with the block updates on the tensor cores (sweep_tc.cu), bandwidths <= 504
+size_t band_smem_solve_tc(int b, int sc);
+int launch_band_solve_tc(Ctx *c, int64_t n, int b, int nshift, int ncol, int sc, const int *mask,
+                         const float2 *const *d_ABp, const float2 *R, float2 *Z, int64_t stop_issue);
 int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
                const float2 *R, float2 *Z, int nact);
 int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,

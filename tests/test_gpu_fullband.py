@@ -9,7 +9,8 @@ reach the code paths that smaller parity pencils do not:
   * the COCG sweeps' band-sized row chunks (taken once (n / b) x shifts >= 2 x SMs, here with 32 shifts);
   * every column-per-CTA variant (8, 16, 32) of the band sweeps on 64 columns;
   * the factorization with its trailing update on the tensor cores (4 x 128-row tiles at b = 500, split
-    TF32) and on CUDA cores.
+    TF32) and on CUDA cores;
+  * the sweeps with the window in tensor memory and the block updates as MMAs, and on CUDA cores.
 
 Tolerances are those of tests/test_gpu_parity.py: the stopping test's scaled residual <= 2 lin_tol on
 every column of every shift, forward error < 1e-7 against the oracle's banded LU, eigenpairs within
@@ -57,12 +58,14 @@ def strip(G):
     G.gcie_destroy(ctx)
 
 
-@pytest.mark.parametrize("sc,factor_tc", [(8, 1), (16, 1), (32, 1), (8, 0), (32, 0)])
-def test_strip_band_solves_match_lu(G, strip, sc, factor_tc, monkeypatch):
-    """factor_tc: the factorization's trailing update on the tensor cores (1, split TF32) or on CUDA cores
-    (0); both give FP32-quality factors, so the iteration bound and the parity are the same."""
+@pytest.mark.parametrize("sc,factor_tc,sweep_tc", [(8, 1, 1), (16, 1, 1), (32, 1, 1), (8, 0, 0), (32, 0, 0), (32, 1, 0)])
+def test_strip_band_solves_match_lu(G, strip, sc, factor_tc, sweep_tc, monkeypatch):
+    """factor_tc / sweep_tc: the factorization's trailing update and the sweeps' block updates on the
+    tensor cores (1, split TF32) or on CUDA cores (0); all give FP32-quality preconditioners, so the
+    iteration bound and the parity are the same."""
     monkeypatch.setenv("GCIE_BAND_SC", str(sc))
     monkeypatch.setenv("GCIE_FACTOR_TC", str(factor_tc))
+    monkeypatch.setenv("GCIE_SWEEP_TC", str(sweep_tc))
     K, M, spec, ctx, pen, z, B, ref = strip
     dX = torch.zeros((len(z), K.n, NCOL), dtype=torch.complex128, device="cuda")
     iters, rc = G.gcie_shifted_solve(ctx, pen, z, NCOL, torch.from_numpy(B).cuda(), dX, lin_tol=LIN_TOL,

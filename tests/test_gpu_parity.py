@@ -125,11 +125,13 @@ def test_shifted_solve_matches_lu(G, ctx, small2d, precision, precond):
         assert np.max(err) < 1e-7, (s, err)
 
 
-@pytest.mark.parametrize("sc", [8, 16, 32])
-def test_band_sweep_variants(G, ctx, small2d, sc, monkeypatch):
+@pytest.mark.parametrize("sc,sweep_tc", [(8, 0), (16, 0), (32, 0), (8, 1), (16, 1), (32, 1)])
+def test_band_sweep_variants(G, ctx, small2d, sc, sweep_tc, monkeypatch):
     """Every column-per-CTA variant of the band sweeps gives the same converged solves (ragged
-    column groups: 38 columns do not fill the last group of 8, 16 or 32)."""
+    column groups: 38 columns do not fill the last group of 8, 16 or 32), on CUDA cores and with the
+    block updates on the tensor cores (sweep_tc = 1, forced at this narrow band: b = 40)."""
     monkeypatch.setenv("GCIE_BAND_SC", str(sc))
+    monkeypatch.setenv("GCIE_SWEEP_TC", str(sweep_tc))
     K, M, spec, pen = small2d
     lo, hi = spec["lo"], spec["hi"]
     z, _ = O.trapezoid_nodes(0.5 * (lo + hi), 0.5 * (hi - lo), 16)
