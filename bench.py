@@ -163,6 +163,7 @@ def run_ours(args, rank, world):
 
     for _ in range(args.warmup):
         step(False)
+    fp64 = G.gcie_fp64_rates(ctx)          # FP64 peaks of this GPU (CUDA-core FMA, FP64 MMA), measured
     # timed region: device events on the library's stream (torch's current stream), max over ranks
     G.gcie_reset_stats(ctx)
     if world > 1:
@@ -199,7 +200,7 @@ def run_ours(args, rank, world):
     G.gcie_destroy(ctx)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     return dict(ms=ms, count=count, stats=stats, clocks=clk, last=last, resid_max=resid_max, spec=spec, K=K, e2e=e2e,
-                kde=kde, launches=launches, sms=sms)
+                kde=kde, launches=launches, sms=sms, fp64=fp64)
 
 
 def predicted_opts(G, ctx, pen, spec, opts, noise, kind):
@@ -579,6 +580,10 @@ def main():
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
                         "nameplate_frac": spmm_gbs / 8000.0},
            "kernel_ms": {k: round(v["ms"], 2) for k, v in classes.items()},
+           "fp64": {"fma_tflops": r["fp64"][0], "mma_tflops": r["fp64"][1],
+                    "refine_tflops": stats["refine"]["flops"] / max(stats["refine"]["ms"], 1e-9) / 1e9,
+                    "refine_frac_of_fma": stats["refine"]["flops"] / max(stats["refine"]["ms"], 1e-9) / 1e9
+                    / max(r["fp64"][0], 1e-9)},
            "gpu_launches": r["launches"],
            "clocks": r["clocks"], "e2e": r["e2e"]}
     if r["kde"] is not None:

@@ -371,6 +371,13 @@ int gcie_density_predict(gcie_ctx *ctx, gcie_density_net *net, int32_t batch, in
 int gcie_hist_quantiles(const double *hist, int32_t nbins, double lo, double hi, double *out, int32_t cap,
                         int32_t *nout);
 
+/* FP64 throughput of the context's GPU on its two FP64 paths, measured by two short kernels (about a
+ * millisecond each): CUDA-core FMAs and FP64 tensor MMAs (mma.sync m8n8k4; tcgen05 has no FP64 kind), in
+ * TFLOP/s.  The dense products of the basis and of the projection (Algorithm 1, "orth", "project") and the
+ * refinement residual run in FP64; the probe shows which path is faster on this part and is the FP64 peak
+ * of their roofline.  Errors: GCIE_EINVAL, GCIE_ECUDA. */
+int gcie_fp64_rates(gcie_ctx *ctx, double *h_fma_tflops, double *h_mma_tflops);
+
 /* The same eigensolve for callers that must not allocate device memory.  (The paper has no
  * counterpart; this entry point exists for integration only.)  Some callers cannot call cudaMalloc:
  * a process that reserves all device memory for its own pool up front has none left to give, and a

@@ -11,6 +11,6 @@ from ._binding import (  # noqa: F401
     gcie_kde_contours, gcie_plan_contours, gcie_count_miss, gcie_resplit, gcie_trapezoid_nodes, gcie_shifted_spmm_f32, gcie_shifted_spmm_f64, gcie_shifted_solve, gcie_moments,
     gcie_m_orthonormalize, gcie_rayleigh_ritz, gcie_jacobi_eig, gcie_jacobi_eig_noalloc, gcie_get_stats, gcie_reset_stats, gcie_set_profile,
     gcie_gemm_tf32x3, gcie_gemm_bf16, gcie_density_net_create, gcie_density_net_destroy, gcie_density_predict,
-    gcie_hist_quantiles, DENSITY_NWEIGHTS, DENSITY_BINS,
+    gcie_hist_quantiles, DENSITY_NWEIGHTS, DENSITY_BINS, gcie_fp64_rates,
     EXPORTED_SYMBOLS,
 )

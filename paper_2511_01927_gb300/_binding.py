@@ -22,6 +22,7 @@ EXPORTED_SYMBOLS = [
     "gcie_shifted_spmm_f64", "gcie_shifted_solve", "gcie_moments", "gcie_m_orthonormalize",
     "gcie_rayleigh_ritz", "gcie_jacobi_eig", "gcie_jacobi_eig_noalloc", "gcie_gemm_tf32x3", "gcie_gemm_bf16",
     "gcie_density_net_create", "gcie_density_net_destroy", "gcie_density_predict", "gcie_hist_quantiles",
+    "gcie_fp64_rates",
 ]
 DENSITY_NWEIGHTS = 717520
 DENSITY_BINS = 256
@@ -122,6 +123,7 @@ def lib():
         "gcie_density_net_destroy": (None, [vp]),
         "gcie_density_predict": (C.c_int, [vp, vp, i32, i32, vp, vp, vp, vp]),
         "gcie_hist_quantiles": (C.c_int, [vp, i32, d, d, vp, i32, C.POINTER(i32)]),
+        "gcie_fp64_rates": (C.c_int, [vp, C.POINTER(d), C.POINTER(d)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -480,3 +482,10 @@ def gcie_hist_quantiles(hist, lo: float, hi: float) -> np.ndarray:
     _check(lib().gcie_hist_quantiles(h.ctypes.data, int(h.size), float(lo), float(hi), out.ctypes.data, cap,
                                      C.byref(nout)), "gcie_hist_quantiles")
     return out[:nout.value].copy()
+
+
+def gcie_fp64_rates(ctx) -> tuple:
+    """Measured FP64 TFLOP/s of the GPU: (CUDA-core FMA, FP64 MMA)."""
+    a, b = C.c_double(0.0), C.c_double(0.0)
+    _check(lib().gcie_fp64_rates(ctx, C.byref(a), C.byref(b)), "gcie_fp64_rates")
+    return float(a.value), float(b.value)

@@ -152,27 +152,29 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve_tc(int64_t n, int b, int n
         *reinterpret_cast<float *>(Bh + off) = h;
         *reinterpret_cast<float *>(Bl + off) = tc::to_tf32(x - h);
     };
+    // operand descriptors at the start of each buffer; an offset of o bytes adds o / 16 to the start field
+    // (every operand lies below 256 KB of shared memory, so the 14-bit field does not overflow)
+    const uint64_t dAh[2] = {tc::make_sdesc(tc::smem_addr(Ah[0]), 128, 8 * OPB), tc::make_sdesc(tc::smem_addr(Ah[1]), 128, 8 * OPB)};
+    const uint64_t dAl[2] = {tc::make_sdesc(tc::smem_addr(Al[0]), 128, 8 * OPB), tc::make_sdesc(tc::smem_addr(Al[1]), 128, 8 * OPB)};
+    const uint64_t dBh = tc::make_sdesc(tc::smem_addr(Bh), 128, 8 * OPB), dBl = tc::make_sdesc(tc::smem_addr(Bl), 128, 8 * OPB);
     auto issue_mma = [&](int abuf) {
         tc::fence_after_sync();
+        const uint64_t ah0 = abuf ? dAh[1] : dAh[0], al0 = abuf ? dAl[1] : dAl[0];
 #pragma unroll
         for (int t = 0; t < NTILE; ++t)
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-                const uint32_t ao = 8192u * t + 256u * kk, bo = 256u * kk;
-                const uint64_t ah = tc::make_sdesc(tc::smem_addr(Ah[abuf]) + ao, 128, 8 * OPB);
-                const uint64_t al = tc::make_sdesc(tc::smem_addr(Al[abuf]) + ao, 128, 8 * OPB);
-                const uint64_t bh = tc::make_sdesc(tc::smem_addr(Bh) + bo, 128, 8 * OPB);
-                const uint64_t bl = tc::make_sdesc(tc::smem_addr(Bl) + bo, 128, 8 * OPB);
+                const uint64_t ao = (8192u * t + 256u * kk) >> 4, bo = (256u * kk) >> 4;
                 const uint32_t d = tmem + (uint32_t)(t * N);
-                tc::mma_tf32(d, ah, bh, idesc, 1);
-                tc::mma_tf32(d, ah, bl, idesc, 1);
-                tc::mma_tf32(d, al, bh, idesc, 1);
+                tc::mma_tf32(d, ah0 + ao, dBh + bo, idesc, 1);
+                tc::mma_tf32(d, ah0 + ao, dBl + bo, idesc, 1);
+                tc::mma_tf32(d, al0 + ao, dBh + bo, idesc, 1);
             }
         tc::commit(&bar_mma);
     };
     // the step's MMAs done (every thread; false if the wait gave up in any thread)
     auto wait_mma = [&]() -> bool {
-        const bool w = __syncthreads_and(tc::mbar_wait(&bar_mma, mma_uses & 1));
+        const bool w = __syncthreads_and(warp != 0 || tc::mbar_wait(&bar_mma, mma_uses & 1));
         if (w) { ++mma_uses; mma_pend = false; }
         return w;
     };
@@ -231,16 +233,19 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve_tc(int64_t n, int b, int n
         st_pend[buf] = true;
     };
     auto st_wait = [&](int buf) -> bool {
-        const bool w = __syncthreads_and(tc::mbar_wait(&bar_st[buf], st_uses[buf] & 1));
+        const bool w = __syncthreads_and(warp != 0 || tc::mbar_wait(&bar_st[buf], st_uses[buf] & 1));
         if (w) { ++st_uses[buf]; st_pend[buf] = false; }
         return w;
     };
     // rows 8 .. b + 7 of factor block kb (in stage[sbuf]) -> A[abuf] at the slots of rows kb SB + il
     auto fwd_split = [&](int64_t kb, int abuf, int sbuf) {
         const float4 *src = reinterpret_cast<const float4 *>(stage[sbuf]);
-        for (int e = tid; e < b * 4; e += ST) {
-            const int il = SB + (e >> 2), q = e & 3;
-            split4(src[il * 4 + q], Ah[abuf], Al[abuf], opoff((int)((kb * SB + il) & (WT - 1)), q));
+        const int base_slot = (int)((kb * SB + SB) & (WT - 1));
+        for (int e = tid; e < ((b + 7) / 8) * 32; e += ST) {
+            // 32 consecutive e: rows 8 (e / 32) .. + 7 (e % 8), chunk (e / 8) % 4
+            const int r = ((e >> 5) << 3) + (e & 7), q = (e >> 3) & 3;
+            if (r >= b) continue;
+            split4(src[(SB + r) * 4 + q], Ah[abuf], Al[abuf], opoff((base_slot + r) & (WT - 1), q));
         }
     };
     {
@@ -332,9 +337,10 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve_tc(int64_t n, int b, int n
         const int64_t kbs = klo / SB;
         const float2 *L = stage[sbuf];
         const int rows = (int)(blk - klo);
-        for (int e = tid; e < rows * 4; e += ST) {
-            const int64_t k = klo + (e >> 2);
-            const int q = e & 3;
+        for (int e = tid; e < ((rows + 7) / 8) * 32; e += ST) {
+            const int r = ((e >> 5) << 3) + (e & 7), q = (e >> 3) & 3;   // as in fwd_split
+            if (r >= rows) continue;
+            const int64_t k = klo + r;
             const int i = (int)(k / SB - kbs), cp = (int)(k % SB);
             const float2 x0 = L[(i * SB + 2 * q) * SB + cp], x1 = L[(i * SB + 2 * q + 1) * SB + cp];
             split4(make_float4(x0.x, x0.y, x1.x, x1.y), Ah[abuf], Al[abuf], opoff((int)(k & (WT - 1)), q));

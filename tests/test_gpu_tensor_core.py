@@ -74,3 +74,9 @@ def test_gemm_rejects_bad_leading_dimension(G, ctx):
     with pytest.raises(G.GcieError) as e:
         G.gcie_gemm_tf32x3(ctx, 8, 8, 8, d, 4, d, 8, d, 8)
     assert e.value.code == 1
+
+
+def test_fp64_rate_probe(G, ctx):
+    """The FP64 probe returns positive rates below the nominal FP64 ceiling of the part (a few TFLOP/s)."""
+    fma, mma = G.gcie_fp64_rates(ctx)
+    assert 0.05 < fma < 100.0 and 0.05 < mma < 100.0
