@@ -291,7 +291,18 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
             for (int q = 0; q < np && q < 2; ++q) pend[q & 1] = 1;
             for (int q = 0; q < np; ++q) {
                 const int buf = q & 1;
-                const bool ok = __syncthreads_and(tc::mbar_wait(&bars[buf], uses[buf] & 1));
+                // the band values this pair updates do not depend on its MMAs: load them first, so that their
+                // latency overlaps the wait (warp w: lanes 32 (w % 4) .. of I tile pi[q], complex columns 32 (w / 4) ..)
+                const int lb = 32 * (warp & 3), grp = warp >> 2;
+                const int I = TILE * pi[q] + lb + lane;
+                const int J0 = TILE * pj[q] + 32 * grp;
+                float2 old[16], old2[16];
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int J = J0 + e;
+                    old[e] = (I < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                }
+                const bool ok = __syncthreads_and(warp != 0 || tc::mbar_wait(&bars[buf], uses[buf] & 1));
                 if (!ok) {
                     dead = true;
                     if (tid == 0) atomicAdd(timeouts, 1u);
@@ -300,26 +311,28 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
                 ++uses[buf];
                 pend[buf] = 0;
                 tc::fence_after_sync();
-                // epilogue: warp w reads lanes 32 (w % 4) .. of I tile pi[q], complex columns 32 (w / 4) ..
-                const int lb = 32 * (warp & 3), grp = warp >> 2;
-                const int I = TILE * pi[q] + lb + lane;
-#pragma unroll 1
-                for (int half = 0; half < 2; ++half) {
-                    const uint32_t col = 256u * buf + 32u * grp + 16u * half;
+                // epilogue: the accumulator's real and imaginary parts, subtracted from the band
+                {
+                    const uint32_t col = 256u * buf + 32u * grp;
                     float vr[16], vi[16];
                     tc::ld16(tmem + ((uint32_t)lb << 16) + col, vr);
                     tc::ld16(tmem + ((uint32_t)lb << 16) + col + 128u, vi);
-                    const int J0 = TILE * pj[q] + 32 * grp + 16 * half;
-                    float2 old[16];
-#pragma unroll
-                    for (int e = 0; e < 16; ++e) {
-                        const int J = J0 + e;
-                        old[e] = (I < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
-                    }
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int J = J0 + e;
                         if (I < tr && J <= I) AB[(p0 + NB + J) * B1 + (I - J)] = make_float2(old[e].x - vr[e], old[e].y - vi[e]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {           // the second half's band values
+                        const int J = J0 + 16 + e;
+                        old2[e] = (I < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                    }
+                    tc::ld16(tmem + ((uint32_t)lb << 16) + col + 16u, vr);
+                    tc::ld16(tmem + ((uint32_t)lb << 16) + col + 144u, vi);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) {
+                        const int J = J0 + 16 + e;
+                        if (I < tr && J <= I) AB[(p0 + NB + J) * B1 + (I - J)] = make_float2(old2[e].x - vr[e], old2[e].y - vi[e]);
                     }
                 }
                 if (q + 2 < np) {
