@@ -45,6 +45,18 @@ void flush_timing(Ctx *c)
     cudaGetLastError();
 }
 
+int live_shifts(Ctx *c, const int *d_mask, int nshift, int fallback)
+{
+    if (!c->profile || nshift <= 0 || !d_mask) return fallback;
+    std::vector<int> h(nshift);
+    if (cudaMemcpyAsync(h.data(), d_mask, nshift * sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return fallback;
+    int k = 0;
+    for (int v : h) k += v != 0;
+    return k;
+}
+
 LaunchScope::LaunchScope(Ctx *ctx, int klass, double b, double f) : c(ctx), cls(klass), bytes(b), flops(f)
 {
     if (c->profile) {

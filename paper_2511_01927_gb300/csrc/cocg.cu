@@ -239,20 +239,30 @@ __global__ void k_refine_x(int64_t n, int ncol, int64_t rows_per_chunk, int chun
     }
 }
 
-// r64 = b - (z M - K) x64 in FP64; r = (T)(r64 / scale_next) unless norm_only; partials of r^T r
-// (from the rounded, scaled r) and |r64|^2 (absolute).  x_zero: x64 is known to be zero (the first
-// residual of a solve without initial guess), so r64 = b without the FP64 products.
+// r64 = b - (z M - K) x64 in FP64 and r = (T)(r64 / scale_next), with per-CTA partials of |r64|^2 in
+// partB.  Modes (flags):
+//   RF_NORM_ONLY  only |r64|^2 (the scale of the first update of a warm-started solve), in FP64;
+//   RF_X_ZERO     x64 is known to be zero (a solve without initial guess): r64 = b, no products and no
+//                 |r64|^2 (the caller takes ||b||^2, known from the start);
+//   RF_RTR        also the partials of r^T r of the rounded, scaled r (the next rho of an
+//                 unpreconditioned solve; with a preconditioner rho = r^T z comes from the sweeps).
+// In FP32 mode |r64|^2 is summed from the rounded, scaled r in FP32 per thread and rescaled by
+// scale_next^2: the norm decides convergence and the next scale, for which FP32 accuracy is ample, and
+// the scaled values are near unit size, so nothing underflows.  The FP64 work is then the products and
+// the forming of r64, not the norms.
+enum : int { RF_NORM_ONLY = 1, RF_X_ZERO = 2, RF_RTR = 4 };
 template <typename T, int CPT>
 __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
         const double *__restrict__ kv, const double *__restrict__ mv, const double2 *__restrict__ z, int ncol,
         int64_t rows_per_chunk, int chunks, const int *__restrict__ shift_refine, const int *__restrict__ rhs_of,
         const double *__restrict__ B, const double2 *__restrict__ X, const double *__restrict__ scale_next,
-        int norm_only, int x_zero, typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA,
-        double *__restrict__ partB)
+        int flags, typename cplx<T>::t *__restrict__ R, double2 *__restrict__ partA, double *__restrict__ partB)
 {
     using C = typename cplx<T>::t;
     const int s = blockIdx.x / chunks, ch = blockIdx.x % chunks;
     if (!shift_refine[s]) return;
+    const bool norm_only = flags & RF_NORM_ONLY, x_zero = flags & RF_X_ZERO, rtr = flags & RF_RTR;
+    constexpr bool f32 = sizeof(T) == 4;
     const int tpr = ncol / CPT;
     const int t = threadIdx.x % tpr, rsub = threadIdx.x / tpr, rpb = blockDim.x / tpr;
     const int64_t r0 = (int64_t)ch * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
@@ -265,40 +275,61 @@ __global__ void __launch_bounds__(256) k_refine_r(int64_t n, const int *__restri
 #pragma unroll
     for (int q = 0; q < CPT; ++q) inv[q] = 1.0 / scale_next[(int64_t)s * ncol + t * CPT + q];
     double pa[CPT][2] = {}, pb[CPT] = {};
-    for (int64_t i = r0 + rsub; i < r1; i += rpb) {
-        double am[CPT][2] = {}, ak[CPT][2] = {};
-        const int e1 = x_zero ? rowptr[i] : rowptr[i + 1];
-        for (int k = rowptr[i]; k < e1; ++k) {
-            const int j = __ldg(col + k);
-            const double a = __ldg(kv + k), b = __ldg(mv + k);
-            const double2 *xj = Xs + (int64_t)j * ncol;
+    float pf[CPT] = {};
+    if (x_zero) {
+        for (int64_t i = r0 + rsub; i < r1; i += rpb) {
 #pragma unroll
             for (int q = 0; q < CPT; ++q) {
-                double2 x = __ldg(xj + q);
-                am[q][0] = fma(b, x.x, am[q][0]); am[q][1] = fma(b, x.y, am[q][1]);
-                ak[q][0] = fma(a, x.x, ak[q][0]); ak[q][1] = fma(a, x.y, ak[q][1]);
+                C rt;
+                rt.x = (T)(__ldg(Bs + i * ncol + q) * inv[q]);
+                rt.y = 0;
+                Rs[i * ncol + q] = rt;
+                if (rtr) { const double tr = (double)rt.x; pa[q][0] += tr * tr; }
             }
         }
+    } else {
+        for (int64_t i = r0 + rsub; i < r1; i += rpb) {
+            double am[CPT][2] = {}, ak[CPT][2] = {};
+            for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+                const int j = __ldg(col + k);
+                const double a = __ldg(kv + k), b = __ldg(mv + k);
+                const double2 *xj = Xs + (int64_t)j * ncol;
 #pragma unroll
-        for (int q = 0; q < CPT; ++q) {
-            double apr = zr * am[q][0] - zi * am[q][1] - ak[q][0];
-            double api = zr * am[q][1] + zi * am[q][0] - ak[q][1];
-            double rr = __ldg(Bs + i * ncol + q) - apr, ri = -api;
-            pb[q] += rr * rr + ri * ri;
-            if (!norm_only) {
-                C rt;
-                rt.x = (T)(rr * inv[q]); rt.y = (T)(ri * inv[q]);
-                Rs[i * ncol + q] = rt;
-                double tr = (double)rt.x, ti = (double)rt.y;
-                pa[q][0] += tr * tr - ti * ti;
-                pa[q][1] += 2 * tr * ti;
+                for (int q = 0; q < CPT; ++q) {
+                    double2 x = __ldg(xj + q);
+                    am[q][0] = fma(b, x.x, am[q][0]); am[q][1] = fma(b, x.y, am[q][1]);
+                    ak[q][0] = fma(a, x.x, ak[q][0]); ak[q][1] = fma(a, x.y, ak[q][1]);
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const double rr = __ldg(Bs + i * ncol + q) - (fma(zr, am[q][0], -zi * am[q][1]) - ak[q][0]);
+                const double ri = ak[q][1] - fma(zr, am[q][1], zi * am[q][0]);
+                if (norm_only || !f32) pb[q] = fma(rr, rr, fma(ri, ri, pb[q]));
+                if (!norm_only) {
+                    C rt;
+                    rt.x = (T)(rr * inv[q]); rt.y = (T)(ri * inv[q]);
+                    Rs[i * ncol + q] = rt;
+                    if (f32) pf[q] = fmaf((float)rt.x, (float)rt.x, fmaf((float)rt.y, (float)rt.y, pf[q]));
+                    if (rtr) {
+                        const double tr = (double)rt.x, ti = (double)rt.y;
+                        pa[q][0] += tr * tr - ti * ti;
+                        pa[q][1] += 2 * tr * ti;
+                    }
+                }
+            }
+        }
+        if (f32 && !norm_only) {
+#pragma unroll
+            for (int q = 0; q < CPT; ++q) {
+                const double sc = scale_next[(int64_t)s * ncol + t * CPT + q];
+                pb[q] = (double)pf[q] * sc * sc;
             }
         }
     }
     const int64_t tile = (int64_t)s * chunks + ch;
     cta_partials<CPT, double>(pa, pb, ncol, tpr, t, rsub, rpb, partA + tile * ncol, partB + tile * ncol);
 }
-
 // ------------------------------------------------------------------ per-column scalar kernels
 // One CTA per shift, one thread per column (ncol <= 1024).  Units: rho, sigma, alpha, beta, eta,
 // eta_ref are in the scaled FP32 system; eta_abs and bnorm2 are absolute FP64 squared norms.
@@ -398,7 +429,8 @@ __global__ void k_scal_beta(int ncol, int chunks, Scal S, const double2 *__restr
 
 // After an update: absolute residual norms decide convergence (or stagnation); the scaled system
 // restarts at eta = eta_abs / scale^2 with the new scale, and the ratio of the scales is kept for beta.
-__global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
+// x_zero: the residual was b itself (no initial guess), eta_abs = ||b||^2.
+__global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2, int x_zero)
 {
     __shared__ int any_active;
     const int s = blockIdx.x, l = threadIdx.x;
@@ -408,7 +440,9 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
     if (l < ncol) {
         const int64_t sc = (int64_t)s * ncol + l;
         double eta_abs = 0;
-        for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
+        if (x_zero) eta_abs = S.bnorm2[sc];
+        else
+            for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
         int f = S.flag[sc];
         const double sn = S.scale_next[sc];
         S.sratio[sc] = sn / S.scale[sc];
@@ -440,13 +474,15 @@ __global__ void k_scal_refine(int ncol, int chunks, Scal S, double tol2)
     }
 }
 
-// First update of a solve: scale_next = ||b - A x0|| from a norm-only residual pass.
-__global__ void k_scale_from_norm(int ncol, int chunks, Scal S)
+// First update of a solve: scale_next = ||b - A x0|| from a norm-only residual pass (x_zero: ||b||).
+__global__ void k_scale_from_norm(int ncol, int chunks, Scal S, int x_zero)
 {
     const int s = blockIdx.x, l = threadIdx.x;
     if (l >= ncol) return;
     double eta_abs = 0;
-    for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
+    if (x_zero) eta_abs = S.bnorm2[(int64_t)s * ncol + l];
+    else
+        for (int c = 0; c < chunks; ++c) eta_abs += S.partB[((int64_t)s * chunks + c) * ncol + l];
     const double nrm = sqrt(eta_abs);
     S.scale_next[(int64_t)s * ncol + l] = (nrm > 0 && isfinite(nrm)) ? nrm : 1.0;
 }
@@ -673,25 +709,31 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         k_bnorm_init<<<nshift, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(ncol, bch, d_rhs, S.partB, S);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
-    auto refine_r = [&](int nact, int norm_only, int x_zero) -> int {
-        LaunchScope ls(c, GCIE_K_REFINE, (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
-                       x_zero ? 0.0 : (double)nact * p->nnz * ncol * 8.0);
+    // r^T r partials only where they are the next rho (no preconditioner)
+    const int rf_rtr = prec ? 0 : RF_RTR;
+    auto refine_r = [&](int nact, int flags) -> int {
+        const bool xz = flags & RF_X_ZERO;
+        nact = live_shifts(c, S.shift_refine, nshift, nact);
+        LaunchScope ls(c, GCIE_K_REFINE,
+                       xz ? (double)nact * n * ncol * esz + (double)n * ncol * 8
+                          : (double)nact * (n * ncol * (16.0 + esz) + mat) + (double)n * ncol * 8,
+                       xz ? 0.0 : (double)nact * p->nnz * ncol * 8.0);
         k_refine_r<T, CPT><<<ntiles_r, gr.threads, smem_r, c->stream>>>(n, p->rowptr, p->col, p->k64s, p->m64s, d_z,
-            ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, norm_only, x_zero, R,
+            ncol, gr.rows_per_chunk, gr.chunks, S.shift_refine, d_rhs, d_B, d_X, S.scale_next, flags | rf_rtr, R,
             S.partA, S.partB);
         GCIE_CUDA_TRY(cudaGetLastError());
         return GCIE_OK;
     };
     auto refine = [&](int nact, int x_zero = 0) -> int {
-        {
-            LaunchScope ls(c, GCIE_K_REFINE, (double)nact * n * ncol * (2 * esz + 32), 0);
+        if (!x_zero) {   // with x64 = 0 and D = 0 there is nothing to fold
+            LaunchScope ls(c, GCIE_K_REFINE, (double)live_shifts(c, S.shift_refine, nshift, nact) * n * ncol * (2 * esz + 32), 0);
             k_refine_x<T><<<ntiles, 256, 0, c->stream>>>(n, ncol, g.rows_per_chunk, g.chunks, S.shift_refine, S.scale, D, d_X);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
-        GCIE_TRY(refine_r(nact, 0, x_zero));
+        GCIE_TRY(refine_r(nact, x_zero ? RF_X_ZERO : 0));
         {
             LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2);
+            k_scal_refine<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, tol2, x_zero);
             GCIE_CUDA_TRY(cudaGetLastError());
         }
         return GCIE_OK;
@@ -704,13 +746,15 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
         GCIE_CUDA_TRY(cudaGetLastError());
         return GCIE_OK;
     };
-    // first update: exact scale from a norm-only residual pass, then the scaled residual
-    // without an initial guess x64 = 0 (and D = 0), so the first two residuals are b itself
-    rc = refine_r(nshift, 1, !x0);
-    if (rc) goto done;
+    // first update: exact scale from a norm-only residual pass (without an initial guess, x64 = 0 and
+    // D = 0, the residual is b and its norm is known), then the scaled residual
+    if (x0) {
+        rc = refine_r(nshift, RF_NORM_ONLY);
+        if (rc) goto done;
+    }
     {
         LaunchScope ls(c, GCIE_K_OTHER, 0, 0);
-        k_scale_from_norm<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S);
+        k_scale_from_norm<<<nshift, sthreads, 0, c->stream>>>(ncol, gr.chunks, S, !x0);
         GCIE_CUDA_TRY(cudaGetLastError());
     }
     rc = refine(nshift, !x0);
@@ -728,9 +772,11 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
             if (active_shifts == 0 || it >= max_iters) break;
             for (int k = 0; k < check_every && it < max_iters; ++k, ++it) {
                 C *Pold = P[it & 1], *Pnew = P[(it + 1) & 1];
+                // shifts the sweeps work on (active_shifts is refreshed only every check_every iterations)
+                const int live = live_shifts(c, S.shift_active, nshift, active_shifts);
                 {
-                    LaunchScope ls(c, GCIE_K_SPMM_DIR, (double)active_shifts * (n * ncol * 3 * esz + mat),
-                                   (double)active_shifts * p->nnz * ncol * 12.0);
+                    LaunchScope ls(c, GCIE_K_SPMM_DIR, (double)live * (n * ncol * 3 * esz + mat),
+                                   (double)live * p->nnz * ncol * 12.0);
                     k_dir<T, CPT><<<ntiles, g.threads, smem, c->stream>>>(n, p->rowptr, p->col, kv, mv, d_z, ncol,
                         g.rows_per_chunk, g.chunks, S.shift_active, S.beta, Zdir, Pold, Pnew, S.partA);
                     GCIE_CUDA_TRY(cudaGetLastError());
@@ -741,8 +787,8 @@ static int solve_t(Ctx *c, const Pencil *p, int nshift, const double *h_z, const
                     GCIE_CUDA_TRY(cudaGetLastError());
                 }
                 {
-                    LaunchScope ls(c, GCIE_K_SPMM_UPD, (double)active_shifts * (n * ncol * 5 * esz + mat),
-                                   (double)active_shifts * p->nnz * ncol * 8.0);
+                    LaunchScope ls(c, GCIE_K_SPMM_UPD, (double)live * (n * ncol * 5 * esz + mat),
+                                   (double)live * p->nnz * ncol * 8.0);
                     k_upd<T, CPT><<<ntiles, g.threads, smem, c->stream>>>(n, p->rowptr, p->col, kv, mv, d_z, ncol,
                         g.rows_per_chunk, g.chunks, S.shift_active, S.alpha, Pnew, D, R, S.partA, S.partB);
                     GCIE_CUDA_TRY(cudaGetLastError());

@@ -130,6 +130,11 @@ inline cudaError_t allow_max_smem(const void *kernel, size_t optin)
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(optin - a.sharedSizeBytes));
 }
 
+// Profiled runs: the number of nonzero entries of the device mask of nshift shifts (one synchronous
+// read), so that the work recorded for a launch counts only the shifts it processes; otherwise (or
+// if the read fails) `fallback`, the caller's host-side count.
+int live_shifts(Ctx *c, const int *d_mask, int nshift, int fallback);
+
 // device scratch of at least `bytes` (reused; contents undefined)
 int ctx_scratch(Ctx *c, size_t bytes, void **out);
 

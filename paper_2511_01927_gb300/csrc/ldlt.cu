@@ -854,6 +854,9 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     const char *tune_env = std::getenv("GCIE_BAND_TUNE");
     const bool tune = !forced && !(tune_env && std::atoi(tune_env) == 0) && !std::getenv("GCIE_TEST_STOP_COPY");
     const std::array<int, 3> key{b, ncol, nact};
+    // the work recorded per launch: the shifts the mask really selects (profiled runs; nact is the caller's
+    // host-side count and keys the autotuner)
+    const int acct = live_shifts(c, mask, nshift, nact);
     if (tune) {
         auto it = c->band_sc.find(key);
         if (it != c->band_sc.end()) {
@@ -868,10 +871,10 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
                 GCIE_CUDA_TRY(cudaEventCreate(&e0));
                 GCIE_CUDA_TRY(cudaEventCreate(&e1));
                 const int ng = (ncol + sc - 1) / sc;
-                const double mac = 2.0 * nact * n * b * ncol;
+                const double mac = 2.0 * acct * n * b * ncol;
                 int rc;
                 {
-                    LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4), 8.0 * mac);
+                    LaunchScope ls(c, GCIE_K_PREC, (double)acct * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4), 8.0 * mac);
                     cudaEventRecord(e0, c->stream);
                     rc = variant(sc, INT64_MAX);
                     cudaEventRecord(e1, c->stream);
@@ -888,8 +891,8 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
         }
     }
     const int ngrp = (ncol + best - 1) / best;
-    const double macs = 2.0 * nact * n * b * ncol;
-    LaunchScope ls(c, GCIE_K_PREC, (double)nact * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
+    const double macs = 2.0 * acct * n * b * ncol;
+    LaunchScope ls(c, GCIE_K_PREC, (double)acct * (n * (b + 1) * 8.0 * 2 * ngrp + n * ncol * 8.0 * 4), 8.0 * macs);
     // GCIE_TEST_STOP_COPY = k: test of the bounded wait: the forward sweep never issues the copy of
     // factor block k, its wait gives up after about a second, and the call reports GCIE_ETIMEOUT
     // (checked here, right after the launch, only in this test mode)
@@ -911,7 +914,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
 int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,
                 const float2 *R, const float2 *Z, double2 *part, int nact)
 {
-    LaunchScope ls(c, GCIE_K_OTHER, (double)nact * n * ncol * 16.0, 0);
+    LaunchScope ls(c, GCIE_K_OTHER, (double)live_shifts(c, mask, nshift, nact) * n * ncol * 16.0, 0);
     k_rz_partials<<<nshift * chunks, std::min(256, ((ncol + 31) / 32) * 32), 0, c->stream>>>(n, ncol, rows_per_chunk,
                                                                                             chunks, mask, R, Z, part);
     GCIE_CUDA_TRY(cudaGetLastError());
