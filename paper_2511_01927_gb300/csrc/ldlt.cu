@@ -384,9 +384,9 @@ __device__ __forceinline__ void row_update(const float2 *__restrict__ l, float2 
 }
 
 // Row stride of the window: SC columns padded so that the rows a quarter warp touches in one
-// 16-byte access fall on distinct banks (8 columns: 4 rows of 32 bytes -> stride 96 bytes; 16
-// columns: 2 rows of 64 bytes -> stride 192 bytes).
-__host__ __device__ constexpr int band_window_stride(int sc) { return sc == 8 ? 12 : sc == 16 ? 24 : sc; }
+// 16-byte access fall on distinct banks (4 columns: 8 rows of 16 bytes -> stride 48 bytes; 8 columns:
+// 4 rows of 32 bytes -> stride 96 bytes; 16 columns: 2 rows of 64 bytes -> stride 192 bytes).
+__host__ __device__ constexpr int band_window_stride(int sc) { return sc == 4 ? 6 : sc == 8 ? 12 : sc == 16 ? 24 : sc; }
 
 // The block's SB rows, the thread's four columns, into registers (zero past the block's nb rows)
 template <int YS, int H>
@@ -819,73 +819,98 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
 {
     const int b = p->bw;
     const int64_t n = p->n;
-    // Columns per CTA: a CTA's block step costs about SC columns of work and one CTA runs per SM,
-    // so take the SC with the fewest (waves x SC) over the active shifts; ties go to the wider CTA,
-    // which reads each column of L once for more right-hand sides.
+    // Three kernel families: solve-then-apply (k_band_solve, kind 0), warp-specialised (k_band_solve_ws,
+    // kind 1: one warp solves the next block while the others apply the current one) and the block updates
+    // on the tensor cores (k_band_solve_tc, kind 2), each with SC = 8, 16 or 32 columns per CTA (kind 0 also
+    // SC = 4, which puts twice the CTAs of SC = 8 on a small batch of shifts, whose sweeps are bound by each
+    // step's latency rather than by the SM's arithmetic).
+    // GCIE_SWEEP_TC=1 selects kind 2 (b <= 504; correct but, as measured on the 500 x 500 workload, slower
+    // than the CUDA-core sweeps: the per-step chain of TMEM reads, barriers, operand splits and 24 small MMAs);
+    // GCIE_BAND_WS=0 / 1 restricts the choice to kind 0 / 1; otherwise kinds 0 and 1 are both candidates.
+    const char *tc_env = std::getenv("GCIE_SWEEP_TC");
+    const bool use_tc = b <= 504 && tc_env && std::atoi(tc_env) == 1 && band_smem_solve_tc(b, 32) <= c->smem_optin;
+    const char *ws_env = std::getenv("GCIE_BAND_WS");
+    std::vector<int> kinds;
+    if (use_tc) kinds = {2};
+    else if (ws_env) kinds = {std::atoi(ws_env) == 0 ? 0 : 1};
+    else kinds = {0, 1};
+    auto smem_of = [&](int kind, int sc) {
+        return kind == 2 ? band_smem_solve_tc(b, sc) : kind == 1 ? band_smem_solve_ws(b, sc) : band_smem_solve(b, sc);
+    };
+    auto feasible = [&](int kind, int sc) { return (sc != 4 || kind == 0) && smem_of(kind, sc) <= c->smem_optin; };
+    // Columns per CTA without tuning: a CTA's block step costs about SC columns of work and one CTA runs per
+    // SM, so take the SC with the fewest (waves x SC) over the active shifts; ties go to the wider CTA, which
+    // reads each column of L once for more right-hand sides.
+    auto ctas_of = [&](int sc) { return (int64_t)std::max(1, nact) * ((ncol + sc - 1) / sc); };
+    const int kind0 = kinds[0];
     int best = 0;
     int64_t best_cost = 0;
     for (int sc : {32, 16, 8}) {
-        if (band_smem_solve(b, sc) > c->smem_optin) continue;
-        const int64_t ctas = (int64_t)std::max(1, nact) * ((ncol + sc - 1) / sc);
-        const int64_t cost = ((ctas + c->num_sms - 1) / c->num_sms) * sc;
+        if (!feasible(kind0, sc)) continue;
+        const int64_t cost = ((ctas_of(sc) + c->num_sms - 1) / c->num_sms) * sc;
         if (!best || cost < best_cost) { best = sc; best_cost = cost; }
     }
     if (!best) { set_error("band sweep: bandwidth too large for shared memory"); return GCIE_EINVAL; }
-    // GCIE_BAND_SC = 8 | 16 | 32 forces the column count per CTA (tests of every variant); otherwise the
-    // autotuner times every variant on the first application for this (bandwidth, columns, active
-    // shifts) and keeps the fastest for the context (GCIE_BAND_TUNE=0: the cost model's choice above)
+    int best_kind = kind0;
+    // GCIE_BAND_SC = 4 | 8 | 16 | 32 forces the column count per CTA (tests of every variant; the first
+    // candidate kind); otherwise the autotuner times every feasible (kind, SC) on the first application for
+    // this (bandwidth, columns, active shifts, candidate kinds) and keeps the fastest for the context
+    // (GCIE_BAND_TUNE=0: the cost model's choice above)
     bool forced = false;
     if (const char *e = std::getenv("GCIE_BAND_SC")) {
         const int v = std::atoi(e);
-        if ((v == 8 || v == 16 || v == 32) && band_smem_solve(b, v) <= c->smem_optin) { best = v; forced = true; }
+        if ((v == 4 || v == 8 || v == 16 || v == 32) && feasible(kind0, v)) { best = v; forced = true; }
     }
-    // GCIE_SWEEP_TC=1: the block updates on the tensor cores (b <= 504; window in tensor memory).  Correct but,
-    // as measured on the 500 x 500 workload, slower than the CUDA-core sweeps (181 against 107 ms per
-    // launch: the per-step chain of TMEM reads, barriers, operand splits and 24 small MMAs), so not the default.
-    const char *tc_env = std::getenv("GCIE_SWEEP_TC");
-    const bool use_tc = b <= 504 && tc_env && std::atoi(tc_env) == 1 && band_smem_solve_tc(b, 32) <= c->smem_optin;
-    auto variant = [&](int sc, int64_t stop) -> int {
-        if (use_tc) return launch_band_solve_tc(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
+    auto variant = [&](int kind, int sc, int64_t stop) -> int {
+        if (kind == 2) return launch_band_solve_tc(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
+        if (kind == 1) return launch_band_solve_ws(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
         return sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
                : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
-                          : launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop);
+               : sc == 8  ? launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
+                          : launch_band_solve<4>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop);
     };
-    auto feasible = [&](int sc) { return use_tc ? band_smem_solve_tc(b, sc) <= c->smem_optin : band_smem_solve(b, sc) <= c->smem_optin; };
     const char *tune_env = std::getenv("GCIE_BAND_TUNE");
     const bool tune = !forced && !(tune_env && std::atoi(tune_env) == 0) && !std::getenv("GCIE_TEST_STOP_COPY");
-    const std::array<int, 3> key{b, ncol, nact};
+    int kmask = 0;
+    for (int k : kinds) kmask |= 1 << k;
+    const std::array<int, 3> key{b, ncol, nact * 8 + kmask};
     // the work recorded per launch: the shifts the mask really selects (profiled runs; nact is the caller's
     // host-side count and keys the autotuner)
     const int acct = live_shifts(c, mask, nshift, nact);
     if (tune) {
         auto it = c->band_sc.find(key);
         if (it != c->band_sc.end()) {
-            best = it->second;
+            best = it->second % 64;
+            best_kind = it->second / 64;
         } else {
-            // every feasible variant once (each writes the same Z), the fastest kept
+            // every feasible variant once (each writes the same Z), the fastest kept; a variant that needs
+            // more than one wave of CTAs is skipped when a wider one fits in one
             float best_ms = 0.f;
-            int pick = best;
-            for (int sc : {32, 16, 8}) {
-                if (!feasible(sc)) continue;
-                cudaEvent_t e0, e1;
-                GCIE_CUDA_TRY(cudaEventCreate(&e0));
-                GCIE_CUDA_TRY(cudaEventCreate(&e1));
-                const int ng = (ncol + sc - 1) / sc;
-                const double mac = 2.0 * acct * n * b * ncol;
-                int rc;
-                {
-                    LaunchScope ls(c, GCIE_K_PREC, (double)acct * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4), 8.0 * mac);
-                    cudaEventRecord(e0, c->stream);
-                    rc = variant(sc, INT64_MAX);
-                    cudaEventRecord(e1, c->stream);
+            int pick = best_kind * 64 + best;
+            const bool one_wave = ctas_of(32) <= c->num_sms;
+            for (int kind : kinds)
+                for (int sc : {32, 16, 8, 4}) {
+                    if (!feasible(kind, sc) || (one_wave && ctas_of(sc) > c->num_sms)) continue;
+                    cudaEvent_t e0, e1;
+                    GCIE_CUDA_TRY(cudaEventCreate(&e0));
+                    GCIE_CUDA_TRY(cudaEventCreate(&e1));
+                    const int ng = (ncol + sc - 1) / sc;
+                    const double mac = 2.0 * acct * n * b * ncol;
+                    int rc;
+                    {
+                        LaunchScope ls(c, GCIE_K_PREC, (double)acct * (n * (b + 1) * 8.0 * 2 * ng + n * ncol * 8.0 * 4),
+                                       8.0 * mac);
+                        cudaEventRecord(e0, c->stream);
+                        rc = variant(kind, sc, INT64_MAX);
+                        cudaEventRecord(e1, c->stream);
+                    }
+                    float ms = 0.f;
+                    if (rc == GCIE_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    if (rc != GCIE_OK) return rc;
+                    if (best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = kind * 64 + sc; }
                 }
-                float ms = 0.f;
-                if (rc == GCIE_OK && cudaEventSynchronize(e1) == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                if (rc != GCIE_OK) return rc;
-                if (best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = sc; }
-            }
             c->band_sc[key] = pick;
             return GCIE_OK;
         }
@@ -898,7 +923,7 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     // (checked here, right after the launch, only in this test mode)
     int64_t stop_issue = INT64_MAX;
     if (const char *e = std::getenv("GCIE_TEST_STOP_COPY")) stop_issue = std::max<int64_t>(1, std::atoll(e));
-    int rc = variant(best, stop_issue);
+    int rc = variant(best_kind, best, stop_issue);
     if (rc == GCIE_OK && stop_issue != INT64_MAX) {
         unsigned int to = 0;
         GCIE_CUDA_TRY(cudaMemcpyAsync(&to, &c->dbg->wait_timeouts, sizeof(to), cudaMemcpyDeviceToHost, c->stream));

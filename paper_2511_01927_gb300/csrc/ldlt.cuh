@@ -35,6 +35,10 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
 size_t band_smem_solve_tc(int b, int sc);
 int launch_band_solve_tc(Ctx *c, int64_t n, int b, int nshift, int ncol, int sc, const int *mask,
                          const float2 *const *d_ABp, const float2 *R, float2 *Z, int64_t stop_issue);
+// the warp-specialised sweeps (sweep_ws.cu): one warp solves the next block while the others apply the current one
+size_t band_smem_solve_ws(int b, int sc);
+int launch_band_solve_ws(Ctx *c, int64_t n, int b, int nshift, int ncol, int sc, const int *mask,
+                         const float2 *const *d_ABp, const float2 *R, float2 *Z, int64_t stop_issue);
 int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
                const float2 *R, float2 *Z, int nact);
 int rz_partials(Ctx *c, int64_t n, int nshift, int ncol, int64_t rows_per_chunk, int chunks, const int *mask,

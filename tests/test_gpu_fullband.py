@@ -58,14 +58,18 @@ def strip(G):
     G.gcie_destroy(ctx)
 
 
-@pytest.mark.parametrize("sc,factor_tc,sweep_tc", [(8, 1, 1), (16, 1, 1), (32, 1, 1), (8, 0, 0), (32, 0, 0), (32, 1, 0)])
-def test_strip_band_solves_match_lu(G, strip, sc, factor_tc, sweep_tc, monkeypatch):
+@pytest.mark.parametrize("sc,factor_tc,sweep_tc,ws", [(8, 1, 1, 0), (16, 1, 1, 0), (32, 1, 1, 0), (8, 0, 0, 1),
+                                                      (32, 0, 0, 1), (8, 1, 0, 1), (16, 1, 0, 1), (32, 1, 0, 1),
+                                                      (32, 1, 0, 0), (8, 1, 0, 0), (4, 1, 0, 0)])
+def test_strip_band_solves_match_lu(G, strip, sc, factor_tc, sweep_tc, ws, monkeypatch):
     """factor_tc / sweep_tc: the factorization's trailing update and the sweeps' block updates on the
-    tensor cores (1, split TF32) or on CUDA cores (0); all give FP32-quality preconditioners, so the
-    iteration bound and the parity are the same."""
+    tensor cores (1, split TF32) or on CUDA cores (0); ws: the CUDA-core sweeps warp-specialised (1) or
+    solve-then-apply (0).  All give FP32-quality preconditioners, so the iteration bound and the parity
+    are the same."""
     monkeypatch.setenv("GCIE_BAND_SC", str(sc))
     monkeypatch.setenv("GCIE_FACTOR_TC", str(factor_tc))
     monkeypatch.setenv("GCIE_SWEEP_TC", str(sweep_tc))
+    monkeypatch.setenv("GCIE_BAND_WS", str(ws))
     K, M, spec, ctx, pen, z, B, ref = strip
     dX = torch.zeros((len(z), K.n, NCOL), dtype=torch.complex128, device="cuda")
     iters, rc = G.gcie_shifted_solve(ctx, pen, z, NCOL, torch.from_numpy(B).cuda(), dX, lin_tol=LIN_TOL,

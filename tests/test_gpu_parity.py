@@ -125,13 +125,15 @@ def test_shifted_solve_matches_lu(G, ctx, small2d, precision, precond):
         assert np.max(err) < 1e-7, (s, err)
 
 
-@pytest.mark.parametrize("sc,sweep_tc", [(8, 0), (16, 0), (32, 0), (8, 1), (16, 1), (32, 1)])
-def test_band_sweep_variants(G, ctx, small2d, sc, sweep_tc, monkeypatch):
+@pytest.mark.parametrize("sc,kind", [(sc, k) for k in ("ws", "plain", "tc") for sc in (8, 16, 32)] + [(4, "plain")])
+def test_band_sweep_variants(G, ctx, small2d, sc, kind, monkeypatch):
     """Every column-per-CTA variant of the band sweeps gives the same converged solves (ragged
-    column groups: 38 columns do not fill the last group of 8, 16 or 32), on CUDA cores and with the
-    block updates on the tensor cores (sweep_tc = 1, forced at this narrow band: b = 40)."""
+    column groups: 38 columns do not fill the last group of 4, 8, 16 or 32): warp-specialised (ws),
+    solve-then-apply (plain), and with the block updates on the tensor cores (tc, forced at this narrow
+    band: b = 40)."""
     monkeypatch.setenv("GCIE_BAND_SC", str(sc))
-    monkeypatch.setenv("GCIE_SWEEP_TC", str(sweep_tc))
+    monkeypatch.setenv("GCIE_SWEEP_TC", "1" if kind == "tc" else "0")
+    monkeypatch.setenv("GCIE_BAND_WS", "1" if kind == "ws" else "0")
     K, M, spec, pen = small2d
     lo, hi = spec["lo"], spec["hi"]
     z, _ = O.trapezoid_nodes(0.5 * (lo + hi), 0.5 * (hi - lo), 16)
@@ -149,10 +151,13 @@ def test_band_sweep_variants(G, ctx, small2d, sc, sweep_tc, monkeypatch):
         assert np.max(err) < 1e-7, (sc, s, err)
 
 
-def test_band_sweep_wait_timeout_reports_and_recovers(G, small2d, monkeypatch):
+@pytest.mark.parametrize("ws", [1, 0])
+def test_band_sweep_wait_timeout_reports_and_recovers(G, small2d, ws, monkeypatch):
     """The bounded wait of the band sweeps: with the copy of one factor block never issued (test
     switch), the waiting CTAs give up after about a second, the call returns GCIE_ETIMEOUT, and the
-    context stays usable for the next solve."""
+    context stays usable for the next solve (warp-specialised sweeps: the other warps' waits return at
+    once after the first gives up, so the CTA still finishes)."""
+    monkeypatch.setenv("GCIE_BAND_WS", str(ws))
     K, M, spec, _ = small2d
     ctx2 = G.gcie_create(0)
     try:
