@@ -26,7 +26,7 @@
 //                    rank-NB update L_p D_p L_p^T (4-column x 128-row items shared by the cluster);
 //   k_band_solve     z = L^-T D^-1 L^-1 r for a group of right-hand sides, with a sliding window of
 //                    b + 2 SB rows in shared memory for each sweep and the factor block of the
-//                    next block step copied in asynchronously (bulk copy forward, cp.async back).
+//                    next block step copied in asynchronously (cp.async).
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
@@ -301,10 +301,16 @@ k_band_ldlt(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off, in
 //             block's x to the b rows above through the strip l_{block, k}.
 // Everything a step reads from global memory (its columns of L, the rows entering the window) is
 // copied with cp.async during the previous step into a second buffer, so a step waits on no global
-// load and needs two barriers.  Both sweeps keep the factor entries a step needs row by row, SB
-// consecutive values per row of the window (row il: l_{blk+il, blk+c} forward, l_{blk+c, k}
-// backward), so every row update reads them as four 16-byte loads at fixed offsets.
+// load and needs two barriers; the threads outside the in-block solve issue those copies while it
+// runs.  Both sweeps keep the factor entries a step needs row by row, SB consecutive values per row
+// of the window (row il: l_{blk+il, blk+c} forward, l_{blk+c, k} backward): forward rows padded to
+// 80 bytes, so that the rows of a quarter warp fall on distinct banks and each row update reads them
+// as four 16-byte loads; backward, each row reads its SB values at a stride of SB.
 constexpr int ST = 512;       // threads per CTA of the sweeps
+constexpr int LP = SB + 2;    // padded row of the forward slab (80 bytes: a quarter warp's rows on distinct banks)
+// complex values of one slab buffer: the forward slab (b + SB) x LP or the backward strip with its diagonal
+// block, (b / SB + 2) SB x SB <= (b + 2 SB) x SB
+__host__ __device__ constexpr int band_slab_elems(int b) { return (b + SB) * LP > (b + 2 * SB) * SB ? (b + SB) * LP : (b + 2 * SB) * SB; }
 
 __device__ __forceinline__ void cp_async8(void *sdst, const void *gsrc)
 {
@@ -318,40 +324,6 @@ __device__ __forceinline__ void cp_async16(void *sdst, const void *gsrc)
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// bulk (TMA) copies global -> shared, completed on an mbarrier that expects their byte count
-__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(unsigned long long *bar)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect(unsigned long long *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_test(unsigned long long *bar, unsigned parity)
-{
-    unsigned ok;
-    asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-                 : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
-    return ok != 0;
-}
-// waits for the phase with the given parity; gives up (false) after about 2^31 SM clock cycles
-// (one second at 2 GHz), far beyond any copy's duration
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity)
-{
-    const long long t0 = clock64();
-    while (!mbar_test(bar, parity))
-        if (clock64() - t0 > (1ll << 31)) return false;
-    return true;
-}
-// orders this thread's earlier shared-memory accesses before later async-proxy (TMA) writes
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, unsigned bytes, unsigned long long *bar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
-}
 
 // One window row, the four columns of a thread: (2q, 2q + 1) and (2q + H, 2q + H + 1), H = SC / 2,
 // so that each 16-byte access of a quarter warp covers 128 contiguous bytes.
@@ -414,15 +386,16 @@ __device__ __forceinline__ void load_block(Quad (&yb)[SB], const float2 *Y, int 
 
 template <int SC>
 __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol, const int *__restrict__ mask,
-        const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall,
-        DbgRec *__restrict__ dbg, int64_t stop_issue)
+        const float2 *const *__restrict__ ABp, const float2 *__restrict__ Rall, float2 *__restrict__ Zall)
 {
     constexpr int H = SC / 2;
     constexpr int YS = band_window_stride(SC);        // window row stride (padded: no bank conflicts)
     constexpr int QT = SC / 4;                        // threads per row in the updates (four columns each)
     constexpr int RG = ST / QT;                       // row groups of the updates
-    static_assert(SB * SC <= ST, "in-block solve needs SB x SC threads");
-    extern __shared__ float4 sm4[];                   // 16-byte aligned: the backward strip is read as float4
+    constexpr int NS = SB * SC;                       // threads 0 .. NS - 1 solve the block's triangle,
+    constexpr int NC = ST - NS;                       // the others meanwhile issue the next step's copies
+    static_assert(NS < ST, "in-block solve needs SB x SC threads and some left to copy");
+    extern __shared__ float4 sm4[];                   // 16-byte aligned: the factor rows are read as float4
     float2 *sm2 = reinterpret_cast<float2 *>(sm4);
     const int ngrp = (ncol + SC - 1) / SC;
     const int s = blockIdx.x / ngrp, g = blockIdx.x % ngrp;
@@ -432,7 +405,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int WR = b + 2 * SB;
     const int GB = (b + SB) * SB;                     // elements of one block of G
     const int DOFF = (b / SB + 1) * SB * SB;          // backward: diagonal block after the strip pieces
-    const int LBS = (b + 2 * SB) * SB;                // one slab buffer (>= GB and >= DOFF + SB SB)
+    const int LBS = band_slab_elems(b);               // one slab buffer
     const float2 *Gf = ABp[s];
     const float2 *Rs = Rall + (int64_t)s * n * ncol + c0;
     float2 *Zs = Zall + (int64_t)s * n * ncol + c0;
@@ -444,40 +417,12 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     const int q4 = tid % QT, rg = tid / QT;
     const float2 zero = make_float2(0.f, 0.f);
     const int64_t nblk = (n + SB - 1) / SB;
-    __shared__ unsigned long long bars[2];            // completion of the bulk copies into slab buffer 0 / 1
-    int uses0 = 0, uses1 = 0;                         // completed phases of each barrier
-    bool pend0 = false, pend1 = false;                // a bulk copy into the buffer is in flight
-    if (tid == 0) {
-        mbar_init(&bars[0]);
-        mbar_init(&bars[1]);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    // wait for slab buffer `buf`; false (in every thread) if some thread's wait gave up
-    auto slab_wait = [&](int buf) -> bool {
-        const int par = (buf ? uses1 : uses0) & 1;
-        const bool ok = __syncthreads_and(mbar_wait(&bars[buf], par));
-        if (ok) {
-            if (buf) { ++uses1; pend1 = false; } else { ++uses0; pend0 = false; }
-        }
-        return ok;
-    };
-    // after a failed wait: record it, let the bulk copies still in flight land (bounded), leave
-    // (a copy that did not land within that second bound may still write this CTA's shared memory after
-    //  it exits: counted apart, the host then marks the context unusable)
-    auto give_up = [&]() {
-        if (tid == 0) atomicAdd(&dbg->wait_timeouts, 1u);
-        bool drained = true;
-        if (pend0) drained = mbar_wait(&bars[0], uses0 & 1) && drained;
-        if (pend1) drained = mbar_wait(&bars[1], uses1 & 1) && drained;
-        if (tid == 0 && !drained) atomicAdd(&dbg->drain_timeouts, 1u);
-        cp_async_wait_all();
-    };
 
     // rows [r0, r0 + SB) of src (zero outside [0, n) and past the CTA's columns) into the window,
-    // row r0 + c at slot slot0 + c (mod WR)
+    // row r0 + c at slot slot0 + c (mod WR); copy threads
     auto rows_async = [&](int64_t r0, int slot0, const float2 *src) {
-        for (int e = tid; e < SB * SC; e += ST) {
+        if (tid < NS) return;
+        for (int e = tid - NS; e < SB * SC; e += NC) {
             const int c = e / SC, qq = e % SC;
             const int64_t i = r0 + c;
             int sl = slot0 + c;
@@ -489,13 +434,15 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     };
 
     // ---------------- forward: L y = r, then y / d written to Z
-    // slab of block kb: block kb of G as it is, L[il * SB + c] = l_{blk+il, blk+c}; one bulk copy
-    // issued by thread 0
+    // slab of block kb: block kb of G with its rows padded to LP values, L[il * LP + c] = l_{blk+il, blk+c}
+    // (the rows a quarter warp reads then fall on distinct banks); 16-byte cp.async copies, copy threads
     auto fwd_slab = [&](int64_t kb, int buf) {
-        if (tid == 0) {
-            fence_proxy_async();
-            mbar_expect(&bars[buf], (unsigned)(GB * sizeof(float2)));
-            bulk_g2s(Lbuf + buf * LBS, Gf + kb * GB, (unsigned)(GB * sizeof(float2)), &bars[buf]);
+        if (tid < NS) return;
+        float4 *dst = reinterpret_cast<float4 *>(Lbuf + buf * LBS);
+        const float4 *src = reinterpret_cast<const float4 *>(Gf + kb * GB);
+        for (int e = tid - NS; e < (b + SB) * (SB / 2); e += NC) {
+            const int il = e / (SB / 2), h = e % (SB / 2);
+            cp_async16(dst + il * (LP / 2) + h, src + il * (SB / 2) + h);
         }
     };
     for (int e = tid; e < (b + SB) * SC; e += ST) {
@@ -504,7 +451,6 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         else Y[t * YS + qq] = zero;
     }
     fwd_slab(0, 0);
-    pend0 = true;
     cp_async_commit();
     int bs = 0;                                       // slot of row blk
     for (int64_t kb = 0; kb < nblk; ++kb) {
@@ -513,14 +459,9 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
         const float2 *Lb = Lbuf + (kb & 1) * LBS;
         auto bslot = [&](int c) { const int v = bs + c; return v >= WR ? v - WR : v; };
         cp_async_wait_all();
-        if (!slab_wait((int)(kb & 1))) { give_up(); return; }
+        __syncthreads();
         // next step's slab and the rows entering the window then (slots of the previous block)
-        // (stop_issue < nblk only in the test of the timeout path: the copy of block stop_issue is
-        //  never issued, so its wait runs out)
-        if (kb + 1 < nblk && kb + 1 < stop_issue) {
-            fwd_slab(kb + 1, (int)((kb + 1) & 1));
-            if ((kb + 1) & 1) pend1 = true; else pend0 = true;
-        }
+        if (kb + 1 < nblk) fwd_slab(kb + 1, (int)((kb + 1) & 1));
         {
             int s0 = bs + b + SB;
             while (s0 >= WR) s0 -= WR;
@@ -533,13 +474,13 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             for (int c = 0; c < SB - 1; ++c) {
                 const float yr = __shfl_sync(gmask, y.x, c, SB), yi = __shfl_sync(gmask, y.y, c, SB);
                 if (lg > c) {
-                    const float2 l = Lb[lg * SB + c];
+                    const float2 l = Lb[lg * LP + c];
                     cmsubf(y, l.x, l.y, make_float2(yr, yi));
                 }
             }
             if (lg < nb) {
                 Y[bslot(lg) * YS + cg] = y;
-                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmulf(y, Lb[lg * SB + lg]);   // y / d
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmulf(y, Lb[lg * LP + lg]);   // y / d
             }
         }
         __syncthreads();
@@ -550,7 +491,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             for (int il = nb + rg; il < rhi; il += RG) {
                 int sl = bs + il;                     // < 2 WR
                 sl -= sl >= WR ? WR : 0;
-                row_update<H, 1>(Lb + il * SB, Y + sl * YS, q4, yb);
+                row_update<H, 1>(Lb + il * LP, Y + sl * YS, q4, yb);
             }
         }
         bs += SB;
@@ -563,15 +504,15 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
     // slab of block kb (blk = kb SB): piece i (i < kb - kbs, kbs = max(0, blk - b) / SB) is rows
     // blk - (kbs + i) SB .. + SB of block kbs + i of G, so L[(i SB + c) SB + c'] = l_{blk+c, (kbs+i) SB + c'}
     // (rows past the block's b + SB are out of the band: zero); at DOFF the block's own first SB
-    // rows, L[DOFF + c SB + c'] = l_{blk+c, blk+c'}
-    // 16-byte cp.async copies (many small pieces: one bulk copy each would queue on the copy engine)
+    // rows, L[DOFF + c SB + c'] = l_{blk+c, blk+c'}; 16-byte cp.async copies, copy threads
     auto bwd_slab = [&](int64_t kb, int buf) {
+        if (tid < NS) return;
         float4 *dst = reinterpret_cast<float4 *>(Lbuf + buf * LBS);
         const int64_t blk = kb * SB;
         const int64_t kbs = max((int64_t)0, blk - b) / SB;
         const int npc = (int)(kb - kbs);
         constexpr int Q = SB / 2;                     // float4 per row of a piece
-        for (int e = tid; e < npc * SB * Q; e += ST) {
+        for (int e = tid - NS; e < npc * SB * Q; e += NC) {
             const int i = e / (SB * Q), r = e % (SB * Q);
             const int c = r / Q, h4 = r % Q;
             const int64_t kbp = kbs + i;
@@ -579,7 +520,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             if (il < b + SB) cp_async16(dst + e, reinterpret_cast<const float4 *>(Gf + kbp * GB + il * SB) + h4);
             else dst[e] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        for (int e = tid; e < SB * Q; e += ST)
+        for (int e = tid - NS; e < SB * Q; e += NC)
             cp_async16(dst + DOFF / 2 + e, reinterpret_cast<const float4 *>(Gf + kb * GB) + e);
     };
     const int64_t lastblk = (nblk - 1) * SB;
@@ -743,8 +684,8 @@ int BandCache::get(Ctx *c, const Pencil *p, int nshift, const double *h_z, float
 size_t band_smem_factor(int b) { return sizeof(float2) * ((size_t)NB * factor_rp(b) + (size_t)NB * factor_ws(b) + 2 * NB); }
 size_t band_smem_solve(int b, int sc)
 {
-    // window (b + 2 SB) x (sc padded) + two slabs (b + 2 SB) x SB
-    return sizeof(float2) * ((size_t)(b + 2 * SB) * band_window_stride(sc) + 2 * (size_t)SB * (b + 2 * SB));
+    // window (b + 2 SB) x (sc padded) + two slab buffers
+    return sizeof(float2) * ((size_t)(b + 2 * SB) * band_window_stride(sc) + 2 * (size_t)band_slab_elems(b));
 }
 
 bool band_feasible(const Ctx *c, int b)
@@ -804,12 +745,12 @@ int band_factor(Ctx *c, const Pencil *p, int nshift, const double2 *d_z, float2 
 
 template <int SC>
 static int launch_band_solve(Ctx *c, int64_t n, int b, int nshift, int ncol, const int *mask, const float2 *const *d_ABp,
-                             const float2 *R, float2 *Z, int64_t stop_issue)
+                             const float2 *R, float2 *Z)
 {
     const size_t smem = band_smem_solve(b, SC);
     GCIE_CUDA_TRY(allow_max_smem((const void *)k_band_solve<SC>, c->smem_optin));
     const int ngrp = (ncol + SC - 1) / SC;
-    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z, c->dbg, stop_issue);
+    k_band_solve<SC><<<nshift * ngrp, ST, smem, c->stream>>>(n, b, ncol, mask, d_ABp, R, Z);
     GCIE_CUDA_TRY(cudaGetLastError());
     return GCIE_OK;
 }
@@ -864,10 +805,10 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     auto variant = [&](int kind, int sc, int64_t stop) -> int {
         if (kind == 2) return launch_band_solve_tc(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
         if (kind == 1) return launch_band_solve_ws(c, n, b, nshift, ncol, sc, mask, d_ABp, R, Z, stop);
-        return sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
-               : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
-               : sc == 8  ? launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop)
-                          : launch_band_solve<4>(c, n, b, nshift, ncol, mask, d_ABp, R, Z, stop);
+        return sc == 32   ? launch_band_solve<32>(c, n, b, nshift, ncol, mask, d_ABp, R, Z)
+               : sc == 16 ? launch_band_solve<16>(c, n, b, nshift, ncol, mask, d_ABp, R, Z)
+               : sc == 8  ? launch_band_solve<8>(c, n, b, nshift, ncol, mask, d_ABp, R, Z)
+                          : launch_band_solve<4>(c, n, b, nshift, ncol, mask, d_ABp, R, Z);
     };
     const char *tune_env = std::getenv("GCIE_BAND_TUNE");
     const bool tune = !forced && !(tune_env && std::atoi(tune_env) == 0) && !std::getenv("GCIE_TEST_STOP_COPY");
