@@ -63,6 +63,12 @@ __device__ __forceinline__ void cmaddf(float2 &a, float2 l, float2 w)
 }
 
 __device__ __forceinline__ float2 cmulf(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// a b with a fixed rounding sequence (no contraction left to the compiler), so that every sweep kernel
+// forms y / d to the same bits
+__device__ __forceinline__ float2 cmul_rn(float2 a, float2 b)
+{
+    return make_float2(__fmaf_rn(a.x, b.x, __fmul_rn(-a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
 
 // ------------------------------------------------------------------ assembly
 __global__ void k_band_assemble(int64_t n, const int *__restrict__ rowptr, const int *__restrict__ col,
@@ -480,7 +486,7 @@ __global__ void __launch_bounds__(ST, 1) k_band_solve(int64_t n, int b, int ncol
             }
             if (lg < nb) {
                 Y[bslot(lg) * YS + cg] = y;
-                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmulf(y, Lb[lg * LP + lg]);   // y / d
+                if (cg < nrc) Zs[(blk + lg) * ncol + cg] = cmul_rn(y, Lb[lg * LP + lg]);   // y / d
             }
         }
         __syncthreads();
@@ -773,12 +779,17 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     const char *ws_env = std::getenv("GCIE_BAND_WS");
     std::vector<int> kinds;
     if (use_tc) kinds = {2};
-    else if (ws_env) kinds = {std::atoi(ws_env) == 0 ? 0 : 1};
-    else kinds = {0, 1};
+    else if (ws_env && std::atoi(ws_env) == 0) kinds = {0};
+    else if (ws_env && b >= SB) kinds = {1};
+    else if (b >= SB) kinds = {0, 1};
+    else kinds = {0};
     auto smem_of = [&](int kind, int sc) {
         return kind == 2 ? band_smem_solve_tc(b, sc) : kind == 1 ? band_smem_solve_ws(b, sc) : band_smem_solve(b, sc);
     };
-    auto feasible = [&](int kind, int sc) { return (sc != 4 || kind == 0) && smem_of(kind, sc) <= c->smem_optin; };
+    // (kind 1 needs b >= SB: see sweep_ws.cu)
+    auto feasible = [&](int kind, int sc) {
+        return (sc != 4 || kind == 0) && (kind != 1 || b >= SB) && smem_of(kind, sc) <= c->smem_optin;
+    };
     // Columns per CTA without tuning: a CTA's block step costs about SC columns of work and one CTA runs per
     // SM, so take the SC with the fewest (waves x SC) over the active shifts; ties go to the wider CTA, which
     // reads each column of L once for more right-hand sides.
@@ -825,10 +836,12 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
             best_kind = it->second / 64;
         } else {
             // every feasible variant once (each writes the same Z), the fastest kept; a variant that needs
-            // more than one wave of CTAs is skipped when a wider one fits in one
+            // more than one wave of CTAs is skipped when another feasible one fits in one
             float best_ms = 0.f;
             int pick = best_kind * 64 + best;
-            const bool one_wave = ctas_of(32) <= c->num_sms;
+            bool one_wave = false;
+            for (int kind : kinds)
+                for (int sc : {32, 16, 8, 4}) one_wave = one_wave || (feasible(kind, sc) && ctas_of(sc) <= c->num_sms);
             for (int kind : kinds)
                 for (int sc : {32, 16, 8, 4}) {
                     if (!feasible(kind, sc) || (one_wave && ctas_of(sc) > c->num_sms)) continue;
@@ -853,7 +866,9 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
                     if (best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = kind * 64 + sc; }
                 }
             c->band_sc[key] = pick;
-            return GCIE_OK;
+            if (best_ms > 0.f) return GCIE_OK;   // Z holds the last variant's (identical) result
+            best = pick % 64;                     // nothing timed: run the cost model's choice
+            best_kind = pick / 64;
         }
     }
     const int ngrp = (ncol + best - 1) / best;

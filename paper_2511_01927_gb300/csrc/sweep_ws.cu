@@ -18,6 +18,8 @@
 //     the strip pieces l_{blk+c, k} as 16-byte cp.async copies shared by the updaters, complete at the next
 //     barrier), and each row entering the update range in the next step is copied in by its own row group;
 //   - the solver reads the block's diagonal piece from a two-slot ring of bulk copies issued two blocks ahead.
+// The bandwidth must be at least SB: below it, rows of block k + 1 would be among the rows entering the window
+// during step k, while the solver reads them (the host does not select this kernel then).
 // The waits for bulk copies (mbarriers) give up after about a second: the thread counts it
 // (dbg->wait_timeouts) and sets a CTA flag, after which every such wait returns at once and no copy is
 // issued, so all warps run through their remaining steps (producing nothing of use) and still meet at every
@@ -286,9 +288,10 @@ __global__ void __launch_bounds__(NT, 1) k_band_solve_ws(int64_t n, int b, int n
                 Y[sl * YS + lane] = v[i];
                 if (lane < nrc) {
                     float2 z = v[i];
-                    if (fwd) {
+                    if (fwd) {                // y / d, rounded as in k_band_solve
                         const float2 dinv = Dg[i * SB + i];
-                        z = make_float2(v[i].x * dinv.x - v[i].y * dinv.y, v[i].x * dinv.y + v[i].y * dinv.x);
+                        z = make_float2(__fmaf_rn(v[i].x, dinv.x, __fmul_rn(-v[i].y, dinv.y)),
+                                        __fmaf_rn(v[i].x, dinv.y, __fmul_rn(v[i].y, dinv.x)));
                     }
                     Zs[(blk + i) * ncol + lane] = z;
                 }
@@ -524,6 +527,7 @@ size_t band_smem_solve_ws(int b, int sc)
 int launch_band_solve_ws(Ctx *c, int64_t n, int b, int nshift, int ncol, int sc, const int *mask,
                          const float2 *const *d_ABp, const float2 *R, float2 *Z, int64_t stop_issue)
 {
+    if (b < SB) { set_error("band sweep: the warp-specialised sweeps need a bandwidth of at least 8"); return GCIE_EINVAL; }
     const size_t smem = band_smem_solve_ws(b, sc);
     const int ngrp = (ncol + sc - 1) / sc;
     auto go = [&](auto kern) -> int {

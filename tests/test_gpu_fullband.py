@@ -122,3 +122,37 @@ def test_strip_solve_matches_oracle_ci(G, strip):
     Ms = M.to_scipy()
     dots = np.abs(np.einsum("ij,ij->j", r["evecs"], Ms @ ro["evecs"]))
     assert np.min(dots) > 1 - 1e-9
+
+
+@pytest.fixture(scope="module")
+def wide_strip(G):
+    """An 8 x 700 strip (n = 4893, bandwidth 700): above the tensor-core factorization's limit (512), so the
+    CUDA-core factorization runs; its sweep windows only fit the narrower column groups."""
+    K, M = P.fem2d_p1_strip(8, 700)
+    assert O.bandwidth(K, M) == 700
+    ctx = G.gcie_create(0)
+    pen = G.gcie_pencil_create(ctx, K, M)
+    import scipy.linalg as sla
+    lam = sla.eigh(O.as_scipy(K).toarray(), O.as_scipy(M).toarray(), eigvals_only=True, subset_by_index=[0, 59])
+    z = np.array(O.trapezoid_nodes(0.5 * (lam[10] + lam[40]), 0.5 * (lam[40] - lam[10]), 8)[0][[0, 2]])
+    B = M.to_scipy() @ P.gaussian_block(K.n, 16, 5)
+    ref = O.node_map(lambda zs: O.ShiftedSolver(K, M, zs, 700).solve(B), z)
+    yield K, M, ctx, pen, z, B, ref
+    G.gcie_pencil_destroy(pen)
+    G.gcie_destroy(ctx)
+
+
+@pytest.mark.parametrize("sc,ws", [(4, 0), (8, 0), (8, 1)])
+def test_wide_band_solves_match_lu(G, wide_strip, sc, ws, monkeypatch):
+    """Band solves at bandwidth 700 with every sweep variant whose window fits shared memory there."""
+    monkeypatch.setenv("GCIE_BAND_SC", str(sc))
+    monkeypatch.setenv("GCIE_BAND_WS", str(ws))
+    K, M, ctx, pen, z, B, ref = wide_strip
+    dX = torch.zeros((len(z), K.n, 16), dtype=torch.complex128, device="cuda")
+    iters, rc = G.gcie_shifted_solve(ctx, pen, z, 16, torch.from_numpy(B).cuda(), dX, lin_tol=LIN_TOL,
+                                     precision=0, precond=3)
+    X = dX.cpu().numpy()
+    assert rc == 0 and 0 < iters <= 12, iters
+    for s, Xr in enumerate(ref):
+        err = np.linalg.norm(X[s] - Xr, axis=0) / np.linalg.norm(Xr, axis=0)
+        assert np.max(err) < 1e-7, (sc, ws, s, np.max(err))
