@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"],
                     help="shifted solves: FP32 COCG with FP64 refinement (mixed) or FP64 COCG (fp64); both "
                          "with the FP32 band factors as preconditioner")
+    ap.add_argument("--lin-tol", type=float, default=1e-11,
+                    help="shifted-solve tolerance (scaled residual) of the FEAST iterations after the first")
+    ap.add_argument("--lin-tol-first", type=float, default=1e-6,
+                    help="looser shifted-solve tolerance of every contour's first FEAST iteration (0: --lin-tol); "
+                         "the eigenpair test ||Kx - lambda Mx|| / (||K||_1 ||x||) <= 1e-10 applies either way, and a "
+                         "contour whose pairs miss it is iterated again at --lin-tol")
     ap.add_argument("--pred-noise", type=float, default=0.1,
                     help="with --contours kde|planned: noise of the predicted spectrum in mean eigenvalue spacings")
     ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",
@@ -154,6 +160,9 @@ def run_ours(args, rank, world):
     ctx = G.gcie_create(dev, stream.cuda_stream)
     pen = G.gcie_pencil_create(ctx, K, M)
     opts = solver_opts(spec, V, args.precision)
+    opts["lin_tol"] = args.lin_tol
+    if args.lin_tol_first > 0:
+        opts["lin_tol_first"] = args.lin_tol_first
     kde = None
     if args.contours != "uniform":
         opts, kde = predicted_opts(G, ctx, pen, spec, opts, args.pred_noise, args.contours)
@@ -309,7 +318,8 @@ def run_serving(args):
     batch = P.serving_batch(64, 6)
     items = [(K, M, lo, hi) for K, M, lo, hi, _ in batch]
     ctx = G.gcie_create(0)
-    opts = dict(nuniform=4, nodes=16, L=64, moments=2, tol=1e-10, lin_tol=1e-11)
+    opts = dict(nuniform=4, nodes=16, L=64, moments=2, tol=1e-10, lin_tol=args.lin_tol,
+                lin_tol_first=args.lin_tol_first)
 
     def run(streams):
         torch.cuda.synchronize()
@@ -341,7 +351,9 @@ def run_serving(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
            "config": {"workload": "serving: 64 pencils, 2D P1 n 10k-200k / 3D Q1 n 10k-27k, 20-200 eigenvalues each",
                       "n_total": int(sum(K.n for K, _, _, _ in items)), "pairs_per_step": int(sum(counts)),
-                      "contours": 4, "nodes": 16, "L": 64, "moments": 2, "batch_streams": 4, "max_resid": worst,
+                      "contours": 4, "nodes": 16, "L": 64, "moments": 2, "batch_streams": 4, "lin_tol": args.lin_tol,
+                      "lin_tol_first": args.lin_tol_first,
+                      "max_resid": worst,
                       "status_not_ok": int(sum(1 for o in outs if o["rc"] != 0))},
            "sequential": {"value": sum(counts) / s1, "seconds": s1, "counts_agree": agree},
            "speedup_over_sequential": value / (sum(counts) / s1),
@@ -375,7 +387,7 @@ def run_learned(args):
     ctx = G.gcie_create(0, torch.cuda.current_stream().cuda_stream)
     net = G.gcie_density_net_create(ctx, w)
     lo, hi = LEARNED_LO, LEARNED_HI
-    common = dict(nodes=16, L=64, moments=2, tol=1e-10, lin_tol=1e-11)
+    common = dict(nodes=16, L=64, moments=2, tol=1e-10, lin_tol=args.lin_tol, lin_tol_first=args.lin_tol_first)
     arms = ("uniform", "learned", "kde")
     tot = {a: 0.0 for a in arms}
     pairs = {a: 0 for a in arms}
@@ -439,7 +451,8 @@ def run_learned(args):
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c32+f64", "data": "synthetic",
            "config": {"workload": "fem2d-p1-256 family, held-out members " + f"{members[0]}..{members[-1]}",
                       "n": 65025, "interval": [lo, hi], "contours": 8, "nodes": 16, "L": 64, "moments": 2, "tol": 1e-10,
-                      "predictor": "density net (BF16, tcgen05), trained on members 0..1999 solved by this library"},
+                      "predictor": "density net (BF16, tcgen05), trained on members 0..1999 solved by this library",
+                      "lin_tol": args.lin_tol, "lin_tol_first": args.lin_tol_first},
            "arms": {a: {"value": val[a], "seconds": tot[a], "pairs": pairs[a],
                         "mean_feast_passes": float(np.mean(passes[a])), "resplits": resplits[a]} for a in arms},
            "learned_over_uniform": val["learned"] / val["uniform"], "kde_over_uniform": val["kde"] / val["uniform"],
@@ -575,7 +588,8 @@ def main():
            "config": workload_config(args, spec, r["K"].n) | {
                       "max_resid": r["resid_max"], "outer_iters": r["last"]["outer_iters"],
                       "feast_iters_per_contour": r["last"]["iters"], "cocg_iters": r["last"]["cocg_iters"],
-                      "precision": args.precision},
+                      "precision": args.precision, "lin_tol": args.lin_tol}
+                      | ({"lin_tol_first": args.lin_tol_first} if args.lin_tol_first > 0 else {}),
            "roofline": roof,
            "spmm_hbm": {"achieved": spmm_gbs, "peak": hbm_peak, "frac": spmm_gbs / hbm_peak, "unit": "GB/s",
                         "nameplate_frac": spmm_gbs / 8000.0},

@@ -48,7 +48,8 @@ class Opts(C.Structure):
                 ("ncontours", C.c_int32), ("nuniform", C.c_int32), ("contours", C.c_void_p), ("alpha", C.c_double),
                 ("h_V0", C.c_void_p), ("seed", C.c_uint64), ("hbm_budget_bytes", C.c_size_t),
                 ("expected_count", C.c_int32), ("profile", C.c_int32), ("precond", C.c_int32),
-                ("judge", C.c_int32), ("max_resplit", C.c_int32), ("batch_streams", C.c_int32)]
+                ("judge", C.c_int32), ("max_resplit", C.c_int32), ("batch_streams", C.c_int32),
+                ("lin_tol_first", C.c_double)]
 
 
 class Result(C.Structure):

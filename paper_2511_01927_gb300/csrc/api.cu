@@ -256,6 +256,7 @@ void gcie_default_opts(gcie_opts *o)
     o->judge = 0;
     o->max_resplit = 4;
     o->batch_streams = 4;
+    o->lin_tol_first = 0.0;
 }
 
 int gcie_create(gcie_ctx **out, int device, void *stream)
@@ -990,7 +991,8 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 SolveInfo info;
                 mark("right-hand sides");
-                int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, o->lin_tol, o->max_iters,
+                const double ltol = (it == 0 && o->lin_tol_first > 0) ? o->lin_tol_first : o->lin_tol;
+                int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, ltol, o->max_iters,
                                      o->precision, o->precond, &bands, &info);
                 mark("shifted solves");
                 cocg_iters += info.iters;
@@ -1341,7 +1343,8 @@ int gcie_solve_pencil(gcie_ctx *c, gcie_pencil *p, double lo, double hi, const g
         o.max_iters < 1 || !(o.tol > 0) || !(o.lin_tol > 0) || (o.precision != GCIE_MIXED && o.precision != GCIE_FP64) ||
         o.ncontours < 0 || (o.ncontours > 0 && !o.contours) || (o.ncontours == 0 && o.nuniform < 1) || o.alpha < 0 ||
         o.precond < GCIE_PREC_NONE || o.precond > GCIE_PREC_BAND || o.judge < 0 || o.judge > 1 || o.max_resplit < 0 ||
-        o.max_resplit > 16 || o.batch_streams < 1 || o.batch_streams > 16) {
+        o.max_resplit > 16 || o.batch_streams < 1 || o.batch_streams > 16 ||
+        !(o.lin_tol_first == 0 || (std::isfinite(o.lin_tol_first) && o.lin_tol_first >= o.lin_tol))) {
         set_error("solve: option out of range");
         return GCIE_EINVAL;
     }

@@ -82,3 +82,25 @@ def test_golden_interval_counts_match_oracle_inertia():
     K, M, spec = P.workload("fem2d-p1-40")
     assert O.count_in(K, M, spec["lo"], spec["hi"]) == spec["count"] == spec["last"] - spec["first"] + 1
     assert O.inertia_count(K, M, spec["lo"]) == spec["first"] - 1
+
+
+def header_struct_fields(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/gcie.h."""
+    src = open(os.path.join(ROOT, "include", "gcie.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    m = re.search(r"typedef struct \{([^{}]*)\}\s*" + name + r"\s*;", src)
+    assert m, name
+    fields = []
+    for decl in m.group(1).split(";"):
+        decl = decl.strip()
+        for part in decl.split(","):          # "double c, r": one field per declarator
+            if part.strip():
+                fields.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", part)[-1])
+    return fields
+
+
+@pytest.mark.parametrize("cname,pyname", [("gcie_opts", "Opts"), ("gcie_contour", "Contour")])
+def test_binding_structs_follow_the_header(G, cname, pyname):
+    """The ctypes mirrors of the ABI structs list the header's fields in the header's order."""
+    from paper_2511_01927_gb300 import _binding as B
+    assert [f[0] for f in getattr(B, pyname)._fields_] == header_struct_fields(cname)
