@@ -60,9 +60,9 @@ def parse():
     ap.add_argument("--lin-tol", type=float, default=1e-11,
                     help="shifted-solve tolerance (scaled residual) of the FEAST iterations after the first")
     ap.add_argument("--lin-tol-first", type=float, default=1e-6,
-                    help="looser shifted-solve tolerance of every contour's first FEAST iteration (0: --lin-tol); "
-                         "the eigenpair test ||Kx - lambda Mx|| / (||K||_1 ||x||) <= 1e-10 applies either way, and a "
-                         "contour whose pairs miss it is iterated again at --lin-tol")
+                    help="looser shifted-solve tolerance of every contour's first FEAST iteration, --lin-tol in the "
+                         "later ones (0: --lin-tol throughout); the eigenpair test ||Kx - lambda Mx|| / (||K||_1 ||x||) "
+                         "<= 1e-10 applies either way, and a contour whose pairs miss it is iterated again")
     ap.add_argument("--pred-noise", type=float, default=0.1,
                     help="with --contours kde|planned: noise of the predicted spectrum in mean eigenvalue spacings")
     ap.add_argument("--profile-case", type=int, default=0, metavar="NODES",

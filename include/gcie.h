@@ -103,12 +103,12 @@ typedef struct {
                                reports GCIE_ENOCONV */
     int32_t batch_streams;  /* gcie_solve_batch: pencils solved at the same time, each by its own host
                                thread on its own stream (1..16; default 4) */
-    double lin_tol_first;   /* looser inner tolerance of the first FEAST iteration (Appendix A.3.3: the
-                               early iterations of the subspace iteration only need the filtered basis,
-                               not converged solves): 0 (default) = lin_tol in every iteration; otherwise
-                               >= lin_tol, the shifted-solve target of every contour's first iteration, the
-                               later ones using lin_tol.  A contour whose pairs do not meet tol after the
-                               first iteration is iterated again, so results keep tol either way. */
+    double lin_tol_first;   /* looser inner tolerance in the first FEAST iteration (Appendix A.3.3: the
+                               subspace iteration needs the filtered basis, not converged solves): 0
+                               (default) = lin_tol in every iteration; otherwise >= lin_tol, the
+                               shifted-solve target of every contour's first iteration, the later ones
+                               using lin_tol.  A contour whose pairs do not meet tol after the first
+                               iteration is iterated again, so results keep tol either way. */
 } gcie_opts;
 
 /* Results: library-allocated host arrays, released by gcie_result_free. */

@@ -991,6 +991,9 @@ static int solve_driver(Ctx *c, Pencil *p, double lo, double hi, const gcie_opts
                 }
                 SolveInfo info;
                 mark("right-hand sides");
+                // the first iteration's looser target (lin_tol_first), lin_tol in the later ones: a tightening
+                // schedule through intermediate targets was measured to trip the stall rule below (or, with
+                // the rule held back, to add iterations), the one-step switch to neither
                 const double ltol = (it == 0 && o->lin_tol_first > 0) ? o->lin_tol_first : o->lin_tol;
                 int src = cocg_solve(c, p, nshift, hz.data(), rhs_of.data(), nrhs, ncol, dB, dX, x0, ltol, o->max_iters,
                                      o->precision, o->precond, &bands, &info);

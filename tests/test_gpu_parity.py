@@ -327,7 +327,7 @@ def test_solve_fem2d_matches_oracle_ci(G, ctx, small2d):
 @pytest.mark.parametrize("lin_tol_first,lin_tol", [(1e-6, 1e-11), (1e-3, 1e-11), (1e-6, 1e-8)])
 def test_solve_loose_inner_tolerance(G, ctx, small2d, lin_tol_first, lin_tol):
     """Looser inner tolerance in the first FEAST iteration (Appendix A.3.3: the subspace iteration needs the
-    filtered basis, not exact solves), tight enough ones after it: the pairs still meet tol (a contour whose
+    filtered basis, not exact solves), lin_tol in the later ones: the pairs still meet tol (a contour whose
     pairs do not is iterated again), they match the oracle's CI solve; the contours never take fewer FEAST
     iterations than with the tight default."""
     K, M, spec, pen = small2d
