@@ -31,6 +31,8 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 
 #include <cooperative_groups.h>
 
@@ -829,7 +831,20 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
     // the work recorded per launch: the shifts the mask really selects (profiled runs; nact is the caller's
     // host-side count and keys the autotuner)
     const int acct = live_shifts(c, mask, nshift, nact);
-    if (tune) {
+    // Choices are shared by every context of the process for launch shapes of the same bandwidth bucket (32
+    // rows), columns, active nodes and candidates (the variants compute the same bits, so which one runs
+    // never changes a result); a choice that does not fit this bandwidth's shared memory is tuned again.
+    // Launches of little work (below 5e10 flops) are not tuned: the cost model's choice runs.
+    static std::mutex g_mu;
+    static std::map<std::array<int, 4>, int> g_pick;
+    const std::array<int, 4> gkey{(b + 31) / 32, ncol, nact, kmask};
+    const bool small = 16.0 * (double)n * b * std::max(1, nact) * ncol < 5e10;
+    if (tune && !small && c->band_sc.find(key) == c->band_sc.end()) {
+        std::lock_guard<std::mutex> lk(g_mu);
+        auto g = g_pick.find(gkey);
+        if (g != g_pick.end() && feasible(g->second / 64, g->second % 64)) c->band_sc[key] = g->second;
+    }
+    if (tune && !small) {
         auto it = c->band_sc.find(key);
         if (it != c->band_sc.end()) {
             best = it->second % 64;
@@ -866,6 +881,10 @@ int band_apply(Ctx *c, const Pencil *p, int nshift, int ncol, const int *mask, c
                     if (best_ms == 0.f || ms < best_ms) { best_ms = ms; pick = kind * 64 + sc; }
                 }
             c->band_sc[key] = pick;
+            {
+                std::lock_guard<std::mutex> lk(g_mu);
+                g_pick[gkey] = pick;
+            }
             if (best_ms > 0.f) return GCIE_OK;   // Z holds the last variant's (identical) result
             best = pick % 64;                     // nothing timed: run the cost model's choice
             best_kind = pick / 64;
