@@ -67,6 +67,26 @@ __device__ __forceinline__ float2 cinvf2(float2 d)
     const float r = 1.0f / (d.x * d.x + d.y * d.y);
     return make_float2(d.x * r, -d.y * r);
 }
+// Band values of the trailing triangle, read and written again at every panel: loads and stores with an L2
+// evict-last policy, so that the triangles of all nodes stay in L2 while the streaming accesses (the panel's
+// last reads of the band, the writes of G) are evicted first.
+__device__ __forceinline__ uint64_t l2_keep_policy()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ float2 ld_keep(const float2 *a, uint64_t pol)
+{
+    float2 v;
+    asm volatile("ld.global.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;" : "=f"(v.x), "=f"(v.y) : "l"(a), "l"(pol) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_keep(float2 *a, float2 v, uint64_t pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(a), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+}
+
 // v -= l y (four explicit FMAs)
 __device__ __forceinline__ void cmsub(float2 &v, float2 l, float2 y)
 {
@@ -137,20 +157,23 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
     uint32_t uses[2] = {0, 0};       // completed phases of each accumulator's barrier
     int pend[2] = {0, 0};            // a commit into the buffer is outstanding
     bool dead = false;               // a wait for the tensor cores gave up: no more MMAs from this CTA
+    const uint64_t keep = l2_keep_policy();
 
     for (int64_t p0 = 0; p0 < n; p0 += NB) {
         const int nc = (int)min((int64_t)NB, n - p0);
         const int rows = (int)min((int64_t)(NB + b), n - p0);
         const int tr = (int)max((int64_t)0, min((int64_t)b, n - p0 - NB));
-        // 1. panel reads: diagonal block to shared memory, the row of this thread to registers
+        // 1. panel reads: diagonal block to shared memory, the row of this thread to registers (the last reads
+        //    of these band values: streaming loads, evicted first, so that L2 keeps the trailing triangles
+        //    that the updates read and write again at every panel)
         if (tid < NB)
             for (int c = 0; c < NB; ++c)
-                Dg[c * NB + tid] = (c < nc && c <= tid && tid < rows && tid - c <= b) ? AB[(p0 + c) * B1 + (tid - c)] : zero;
+                Dg[c * NB + tid] = (c < nc && c <= tid && tid < rows && tid - c <= b) ? __ldcs(&AB[(p0 + c) * B1 + (tid - c)]) : zero;
         const int t = NB + tid;               // this thread's panel row (t < NB + b)
         float2 a[NB];
 #pragma unroll
         for (int c = 0; c < NB; ++c)
-            a[c] = (tid < b && t < rows && c < nc && t - c <= b) ? AB[(p0 + c) * B1 + (t - c)] : zero;
+            a[c] = (tid < b && t < rows && c < nc && t - c <= b) ? __ldcs(&AB[(p0 + c) * B1 + (t - c)]) : zero;
         __syncthreads();
         // 2. diagonal block (warp 0; lane r = row r)
         if (warp == 0) {
@@ -194,7 +217,7 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
 #pragma unroll
                         for (int cp = 0; cp < SB; ++cp) {
                             const int c = SB * h + cp;
-                            g[cp] = (r < rows && c < nc && r > c) ? v[c] : zero;   // diagonal: 1 / d below
+                            __stcs(&g[cp], (r < rows && c < nc && r > c) ? v[c] : zero);   // diagonal: 1 / d below
                         }
                     }
                 }
@@ -205,7 +228,7 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
         if (crank == 0 && tid < nc) {
             const int h = tid / SB;
             const int64_t kb = p0 / SB + h;
-            if (kb < nblk) Gf[kb * (int64_t)(b + SB) * SB + (int64_t)(tid - SB * h) * SB + (tid - SB * h)] = DI[tid];
+            if (kb < nblk) __stcs(&Gf[kb * (int64_t)(b + SB) * SB + (int64_t)(tid - SB * h) * SB + (tid - SB * h)], DI[tid]);
         }
         // 3. the rows below the diagonal block: l_tc, G, operands
         if (tid < b) {
@@ -232,7 +255,7 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
                             const int c0 = SB * h + 2 * q;
                             const float2 u0 = (live && c0 < nc && t - c0 <= b) ? a[c0] : zero;
                             const float2 u1 = (live && c0 + 1 < nc && t - c0 - 1 <= b) ? a[c0 + 1] : zero;
-                            g[q] = make_float4(u0.x, u0.y, u1.x, u1.y);
+                            __stcs(&g[q], make_float4(u0.x, u0.y, u1.x, u1.y));   // G: written once (streaming)
                         }
                     }
                 }
@@ -300,7 +323,7 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
 #pragma unroll
                 for (int e = 0; e < 16; ++e) {
                     const int J = J0 + e;
-                    old[e] = (I < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                    old[e] = (I < tr && J <= I) ? ld_keep(&AB[(p0 + NB + J) * B1 + (I - J)], keep) : zero;
                 }
                 const bool ok = __syncthreads_and(warp != 0 || tc::mbar_wait(&bars[buf], uses[buf] & 1));
                 if (!ok) {
@@ -320,19 +343,19 @@ k_band_ldlt_tc(int64_t n, int b, float2 *const *__restrict__ ABp, size_t ab_off,
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int J = J0 + e;
-                        if (I < tr && J <= I) AB[(p0 + NB + J) * B1 + (I - J)] = make_float2(old[e].x - vr[e], old[e].y - vi[e]);
+                        if (I < tr && J <= I) st_keep(&AB[(p0 + NB + J) * B1 + (I - J)], make_float2(old[e].x - vr[e], old[e].y - vi[e]), keep);
                     }
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {           // the second half's band values
                         const int J = J0 + 16 + e;
-                        old2[e] = (I < tr && J <= I) ? AB[(p0 + NB + J) * B1 + (I - J)] : zero;
+                        old2[e] = (I < tr && J <= I) ? ld_keep(&AB[(p0 + NB + J) * B1 + (I - J)], keep) : zero;
                     }
                     tc::ld16(tmem + ((uint32_t)lb << 16) + col + 16u, vr);
                     tc::ld16(tmem + ((uint32_t)lb << 16) + col + 144u, vi);
 #pragma unroll
                     for (int e = 0; e < 16; ++e) {
                         const int J = J0 + 16 + e;
-                        if (I < tr && J <= I) AB[(p0 + NB + J) * B1 + (I - J)] = make_float2(old2[e].x - vr[e], old2[e].y - vi[e]);
+                        if (I < tr && J <= I) st_keep(&AB[(p0 + NB + J) * B1 + (I - J)], make_float2(old2[e].x - vr[e], old2[e].y - vi[e]), keep);
                     }
                 }
                 if (q + 2 < np) {
