@@ -388,7 +388,9 @@ def run_learned(args):
     net = G.gcie_density_net_create(ctx, w)
     lo, hi = LEARNED_LO, LEARNED_HI
     common = dict(nodes=16, L=64, moments=2, tol=1e-10, lin_tol=args.lin_tol, lin_tol_first=args.lin_tol_first)
-    arms = ("uniform", "learned", "kde")
+    # uniform_fp64: the in-box comparator of the learned mixed-precision solve (FP64 COCG recurrences, SpMM and
+    # residuals, the same FP32 band factors, tight inner tolerance throughout)
+    arms = ("uniform", "learned", "kde", "uniform_fp64")
     tot = {a: 0.0 for a in arms}
     pairs = {a: 0 for a in arms}
     passes = {a: [] for a in arms}
@@ -400,6 +402,10 @@ def run_learned(args):
         t0 = time.perf_counter()
         if arm == "uniform":
             r = G.gcie_solve_pencil(ctx, pen, lo, hi, nuniform=8, V0=V, allow_noconv=True, **common)
+            pc = None
+        elif arm == "uniform_fp64":
+            r = G.gcie_solve_pencil(ctx, pen, lo, hi, nuniform=8, V0=V, allow_noconv=True,
+                                    **(common | dict(precision=1, lin_tol=1e-11, lin_tol_first=0.0)))
             pc = None
         else:
             hist = G.gcie_density_predict(ctx, net, kappa[None], rho[None], [[lo, hi]])[0]
@@ -456,6 +462,7 @@ def run_learned(args):
            "arms": {a: {"value": val[a], "seconds": tot[a], "pairs": pairs[a],
                         "mean_feast_passes": float(np.mean(passes[a])), "resplits": resplits[a]} for a in arms},
            "learned_over_uniform": val["learned"] / val["uniform"], "kde_over_uniform": val["kde"] / val["uniform"],
+           "learned_over_uniform_fp64": val["learned"] / val["uniform_fp64"],
            "count_agreement": agree / len(members),
            "predicted_count_rel_error": float(np.mean(pred_err)),
            "kde_contours_mean": float(np.mean(ncont["kde"])), "clocks": clk}
