@@ -526,8 +526,9 @@ __global__ void k_bnorm_init(int ncol, int chunks, const int *__restrict__ rhs_o
 
 // X[e] *= dsc[row]^pow for every element of nblk blocks of n x ncol (pow = +1 or -1); complex
 // or real (ncomp = 2 or 1 doubles per element).
+// (src and dst may be the same array: every element is read and written by one thread)
 __global__ void k_scale_rows(int64_t n, int ncol, int64_t nblk, int ncomp, const double *__restrict__ dsc, int inverse,
-                             const double *__restrict__ src, double *__restrict__ dst)
+                             const double *src, double *dst)
 {
     const int64_t total = nblk * n * ncol * ncomp;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
